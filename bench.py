@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the per-shading-point path: 1080p frames shaded by the
+tensor-core neural decoder, next to the supersampled reference integrator.
+
+One timed step = one 1920x1080 frame (2,073,600 shading points, eight weave
+materials) through the decoder: a single launch of the fused tcgen05 kernel
+on a G-buffer already resident in HBM (Sec. 4.4: only the decoder runs per
+frame; the latent fold and weight packing run once per material edit and are
+timed separately).  Four G-buffer copies rotate so that every step reads
+inputs that are not in L2 (4 x 79 MB > 129 MB).
+
+Also measured in the same run and reported on the JSON line: the reference
+integral of the same frame at 256 spp, the full neural call including the
+fold, a training step (batch 65536), the end-to-end path from pinned host
+memory, SM clocks during the timed region, and the FP64 oracle timed on the
+host cores.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank shades its own frame (independent frames, no
+collective on the data path: weak scaling); the elapsed time is the maximum
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as dt
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frame ms & shading pts/s: neural vs supersampled reference at RMSE≤0.01"
+UNIT = "shading pts/s"
+WIDTH, HEIGHT = 1920, 1080
+N_POINTS = WIDTH * HEIGHT
+FLOP_PER_POINT = 2 * (39 * 64 + 64 * 64 + 64 * 64 + 64 * 4)      # 21,888 (layer 1 with the latent folded)
+BYTES_PER_POINT = 38 + 12                                          # G-buffer record in, RGB out
+WORKLOAD = "1920x1080 G-buffer, 8 weave materials (one per 240-px band), random-init decoder"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "of measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+CLOCK_FIELDS = ["timestamp", "index", "clocks.sm", "clocks.max.sm", "power.draw",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + ",".join(CLOCK_FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, t0: float, t1: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "nvidia-smi unavailable"}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(CLOCK_FIELDS):
+                continue
+            try:
+                ts = dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        note = "samples inside the timed region"
+        if len(inside) < 3:
+            inside = [r for r in rows if t0 - 1.0 <= r[0] <= t1 + 1.0]
+            note = "timed region shorter than the 100 ms sampling period: samples within 1 s of it"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "no samples"}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "note": note}
+
+
+# ----------------------------------------------------------------------------
+# the FP64 oracle on the host cores (baseline leg)
+# ----------------------------------------------------------------------------
+def oracle_decoder_rate(points: int, reps: int = 3):
+    """FP64 numpy decoder (the oracle as it stands) on `points` points of the
+    1080p workload; returns (pts/s, cores, description)."""
+    import oracle
+    import workloads as W
+    g = W.frame_gbuffer()
+    idx = W.sample_indices(N_POINTS, points, stream="cpu-baseline")
+    sub = W.subset(g, idx)
+    mats = W.frame_materials()
+    P = oracle.mlp.unpack(W.decoder_init(), oracle.mlp.DEC_SHAPES)
+    z = W.random_latents(len(mats))
+    oracle.mlp.shade_neural(P, z, mats, sub)
+    t = time.perf_counter()
+    for _ in range(reps):
+        oracle.mlp.shade_neural(P, z, mats, sub)
+    dtime = (time.perf_counter() - t) / reps
+    return points / dtime, os.cpu_count(), f"FP64 numpy decoder on {points} sampled points of the 1080p G-buffer"
+
+
+def oracle_reference_rate(points: int, spp: int = 16):
+    """FP64 C reference integral (OpenMP, all host cores) at spp x spp."""
+    import oracle
+    import workloads as W
+    g = W.frame_gbuffer()
+    idx = W.sample_indices(N_POINTS, points, stream="cpu-baseline-ref")
+    sub = W.subset(g, idx)
+    mats = W.frame_materials()
+    t = time.perf_counter()
+    oracle.shade_reference(mats, sub, spp, spp, 7, nthreads=0, pixel_index=idx)
+    return points / (time.perf_counter() - t)
+
+
+def run_reference_arm(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    g = W.frame_gbuffer()
+    mats = W.frame_materials()
+    P = oracle.mlp.unpack(W.decoder_init(), oracle.mlp.DEC_SHAPES)
+    z = W.random_latents(len(mats))
+    total = args.steps + args.warmup
+    per_step = int(max(256, min(16384, 16384 * 60 // max(total, 1))))
+    idx = W.sample_indices(N_POINTS, per_step, stream="reference-arm")
+    sub = W.subset(g, idx)
+    for _ in range(args.warmup):
+        oracle.mlp.shade_neural(P, z, mats, sub)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mlp.shade_neural(P, z, mats, sub)
+    el = time.perf_counter() - t
+    value = per_step * args.steps / el
+    ms_frame = N_POINTS / value * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_points_per_step": per_step,
+                       "extrapolated_ms_per_1080p_frame": ms_frame},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} sampled points of the 1080p G-buffer per step, FP64 numpy"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--no-extras", action="store_true", help="only the timed neural frames")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        run_reference_arm(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_2406_17782_gb300 import build as B
+    B.build()
+    from paper_2406_17782_gb300.api import Fabric, GBuffer
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    fab = Fabric(local)
+    mats = W.frame_materials()
+    fab.set_materials(mats)
+    fab.set_params(W.decoder_init(), W.encoder_init())
+    latents = fab.encode_params(mats)
+    g_host = W.frame_gbuffer()
+    copies = 4
+    gbufs = [GBuffer.from_numpy(g_host) for _ in range(copies)]
+    rgbs = [torch.empty((N_POINTS, 3), dtype=torch.float32, device="cuda") for _ in range(copies)]
+    fab.prepare_neural(latents, args.precision)
+    stream = torch.cuda.current_stream()
+
+    sampler = ClockSampler(local, os.path.join(ROOT, f".bench_clocks_{rank}.csv"))
+    for k in range(args.warmup):
+        fab.shade_neural_prepared(gbufs[k % copies], args.precision, out_rgb=rgbs[k % copies])
+    fab.sync_status()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    ev0.record(stream)
+    for k in range(args.steps):
+        fab.shade_neural_prepared(gbufs[k % copies], args.precision, out_rgb=rgbs[k % copies])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    fab.sync_status()
+    ms_step = elapsed_ms / args.steps
+    value = world * N_POINTS * args.steps / (elapsed_ms * 1e-3)
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, args, stream)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    try:
+        os.remove(sampler.path)
+    except OSError:
+        pass
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    pk, which = peaks()
+    tflops = FLOP_PER_POINT * N_POINTS / (ms_step * 1e-3) / 1e12
+    gbs = BYTES_PER_POINT * N_POINTS / (ms_step * 1e-3) / 1e9
+    # FP16 and BF16 share the dense tensor rate (nominal 2.25 PFLOP/s each), so
+    # the measured BF16 burst figure is the FP16 peak too; FP32 runs on the
+    # SIMT pipes (nominal 1/16 of the dense 16-bit tensor rate)
+    peak_t = pk["bf16_tflops"] if args.precision in ("fp16", "bf16") else pk["bf16_tflops"] / 16.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "points_per_frame": N_POINTS,
+                   "l2": "4 rotating G-buffer copies, 4 x 79 MB > 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_t, "unit": "TFLOP/s",
+                     "frac": tflops / peak_t, "traffic": None,
+                     "note": f"fused decoder kernel, {FLOP_PER_POINT} FLOP/pt x {N_POINTS} pts per launch, "
+                             f"one launch per step, peak = bf16 burst {which}"},
+        "hbm_view": {"achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"],
+                     "bytes_per_point": BYTES_PER_POINT},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    if "reference" in extras:
+        line["speedup_vs_reference_256spp"] = extras["reference"]["ms_per_frame"] / ms_step
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def timed(torch, stream, fn, reps):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(reps):
+        fn(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, args, stream):
+    out = {}
+    copies = len(gbufs)
+    # neural frame including the latent fold / weight packing (two launches)
+    ms_full = timed(torch, stream, lambda k: fab.shade_neural(gbufs[k % copies], latents, args.precision,
+                                                              out_rgb=rgbs[k % copies]), 200)
+    # supersampled reference at 256 spp (16 x 16) on the same frame
+    for k in range(2):
+        fab.shade_reference(gbufs[k], 16, 16, 11, out_rgb=rgbs[k])
+    ms_ref = timed(torch, stream, lambda k: fab.shade_reference(gbufs[k % copies], 16, 16, 11,
+                                                                out_rgb=rgbs[k % copies]), 10)
+    fab.sync_status()
+    ms_neural = None
+    out["reference"] = {"ms_per_frame": ms_ref, "pts_per_s": N_POINTS / (ms_ref * 1e-3), "spp": 256,
+                        "sample_evals_per_s": N_POINTS * 256 / (ms_ref * 1e-3)}
+    out["neural_with_fold_ms_per_frame"] = ms_full
+    # end to end: pinned host G-buffer in, RGB back to pinned host memory
+    host = GBuffer.from_numpy(g_host, device="cpu", pin=True)
+    rgb_host = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
+    dev = gbufs[0]
+
+    def e2e(k):
+        dev.copy_(host, non_blocking=True)
+        fab.shade_neural_prepared(dev, args.precision, out_rgb=rgbs[0])
+        rgb_host.copy_(rgbs[0], non_blocking=True)
+
+    e2e(0)
+    reps = max(10, min(args.steps, 200))
+    ms_e2e = timed(torch, stream, e2e, reps)
+    out["e2e"] = {"value": N_POINTS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+                  "h2d_bytes_per_step": host.nbytes(), "d2h_bytes_per_step": rgb_host.numel() * 4}
+    # one training step, batch 65536, over 256 training materials
+    tm = W.training_materials(32)
+    fab.set_train_materials(tm)
+    q = W.training_queries(65536, len(tm), stream="bench-train")
+    gq = GBuffer.from_numpy(q)
+    target = torch.empty((65536, 4), dtype=torch.float32, device="cuda")
+    fab.set_materials(tm)
+    fab.shade_reference(gq, 4, 4, 3, out_rgb=torch.empty((65536, 3), device="cuda"), out_comps=target)
+    fab.set_materials(mats)
+    fab.set_params(W.decoder_init(), W.encoder_init())
+    for _ in range(3):
+        fab.train_step(gq, target, 1e-3)
+    ms_train = timed(torch, stream, lambda k: fab.train_step(gq, target, 1e-3), 20)
+    fab.sync_status()
+    out["train"] = {"ms_per_step": ms_train, "batch": 65536, "samples_per_s": 65536 / (ms_train * 1e-3),
+                    "materials": len(tm)}
+    # the FP64 oracle on the host cores, bounded sample
+    rate, cores, what = oracle_decoder_rate(16384)
+    pts = int(min(2_000_000, max(4096, rate * args.cpu_seconds / 4)))
+    rate, cores, what = oracle_decoder_rate(pts)
+    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": what}
+    ref_pts = 512
+    out["cpu_baseline_reference"] = {"value": oracle_reference_rate(ref_pts), "unit": "pts/s at 256 spp",
+                                     "cores": os.cpu_count(), "kind": "oracle",
+                                     "sample": f"FP64 C integrator, {ref_pts} sampled points, 16x16 spp"}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,295 @@
+/*
+ * fabric.h -- C ABI of the GB300 (sm_103a) footprint-filtered woven-fabric
+ * reflectance library: the per-shading-point path of Chen, Wang and Wang,
+ * "Real-time Neural Woven Fabric Rendering" (SIGGRAPH 2024).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ *  - Plain C types only.  `stream` is a cudaStream_t passed as void* (NULL =
+ *    the legacy default stream).  Pointers named *_dev are device pointers
+ *    owned by the caller; pointers without the suffix are host pointers.
+ *  - The context owns what it allocates: pattern and material tables,
+ *    network parameters (FP32 master copy), Adam moments, packed tensor-core
+ *    weights and per-call scratch.  It never frees caller memory.
+ *  - Every call that takes a stream is asynchronous on it and returns before
+ *    the GPU work finishes, except where a call says otherwise.  Arguments
+ *    are checked on the host before any launch; a rejected call launches
+ *    nothing and returns FABRIC_ERR_INVALID_ARG with a message available from
+ *    fabric_last_error().  No C++ exception and no process exit crosses the
+ *    ABI; device code never traps.
+ *  - Errors found on the device (a material index outside the material
+ *    table, an expired wait inside a kernel) are recorded in a device status
+ *    word; the faulty point's outputs are NaN.  fabric_sync_status() reports
+ *    and clears it.
+ *  - n = 0 is a no-op that returns FABRIC_OK.  NaN inputs propagate to the
+ *    affected point only.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef FABRIC_H
+#define FABRIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FABRIC_OK = 0,
+  FABRIC_ERR_INVALID_ARG = 1,
+  FABRIC_ERR_CUDA = 2,
+  FABRIC_ERR_OOM = 3,
+  FABRIC_ERR_TIMEOUT = 4,
+  FABRIC_ERR_IO = 5,
+  FABRIC_ERR_UNSUPPORTED = 6,
+  FABRIC_ERR_DEVICE = 7
+} fabric_status;
+
+typedef enum {
+  FABRIC_PREC_FP32 = 0,   /* SIMT FP32 decoder (accuracy anchor)                */
+  FABRIC_PREC_BF16 = 1,   /* tcgen05 tensor cores, BF16 operands, FP32 accum.   */
+  FABRIC_PREC_FP8 = 2,    /* tcgen05 tensor cores, E4M3 operands, FP32 accum.   */
+  FABRIC_PREC_FP16 = 3    /* tcgen05 tensor cores, FP16 operands, FP32 accum.   */
+} fabric_precision;
+
+/*
+ * Material record (host memory, 84 bytes, no padding): the shading-model
+ * parameters of Table 1 plus the procedural weave of Sec. 5.1.
+ *   pattern_id  built-in weave 0..7: plain, 2/1 twill, 3/1 twill, 4/1 satin
+ *               (warp-faced), 5-harness satin (weft-faced), 2x2 basket,
+ *               herringbone, warp rib
+ *   twist_deg   ply twist psi, degrees (Table 2)
+ *   incl_deg    yarn inclination u, degrees (Table 2)
+ *   alpha, beta roughness and height-field scale, [0] warp, [1] weft (Table 1)
+ *   kd, ks      diffuse / specular RGB albedos, [yarn][rgb]; they enter only
+ *               through Eq. 8, never the network (Sec. 4.1)
+ *   gap         gap ratio of a yarn's width (0.2 in Sec. 5.1)
+ *   w_blend     blended-Lambertian weight w of Eq. 1
+ * Accepted ranges: 0 < alpha <= 1, 0 <= beta <= 4, 0 <= gap < 1,
+ * 0 <= w_blend <= 1, |twist|, |incl| <= 89.
+ */
+typedef struct {
+  int32_t pattern_id;
+  float twist_deg;
+  float incl_deg;
+  float alpha[2];
+  float beta[2];
+  float kd[2][3];
+  float ks[2][3];
+  float gap;
+  float w_blend;
+} fabric_material;
+
+/*
+ * G-buffer of n shading points, structure of arrays, device memory, all
+ * arrays 4-byte aligned (16-byte alignment enables the vectorised paths).
+ * The query of Eq. 6: footprint centre (u, v) in pattern repeats (1 uv unit =
+ * one weave repeat), footprint half side `radius` in the same units (box
+ * kernel k_P over [u-r, u+r] x [v-r, v+r], Eq. 3), wi and wo as [n][3] unit
+ * vectors in the local shading frame (z = macro normal n_s, x along u, y
+ * along v), and a material index into the context's material table.
+ */
+typedef struct {
+  const float *u;
+  const float *v;
+  const float *radius;
+  const float *wi;
+  const float *wo;
+  const uint16_t *material;
+  int64_t n;
+} fabric_gbuffer;
+
+typedef struct fabric_ctx fabric_ctx;
+
+/* ------------------------------------------------------------------ */
+/* Lifecycle and status                                               */
+/* ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (becomes current for the calling
+ * thread).  Synchronous.  *out is NULL on failure. */
+fabric_status fabric_create(fabric_ctx **out, int device);
+
+/* Release everything the context owns (waits for its streams' work). */
+void fabric_destroy(fabric_ctx *ctx);
+
+/* Message describing the last failed call on this context ("" if none). */
+const char *fabric_last_error(const fabric_ctx *ctx);
+
+/* Name of a status code. */
+const char *fabric_status_string(fabric_status s);
+
+/* Synchronise `stream`, then read and clear the device status word:
+ * FABRIC_OK, FABRIC_ERR_DEVICE (bad material index) or FABRIC_ERR_TIMEOUT. */
+fabric_status fabric_sync_status(fabric_ctx *ctx, void *stream);
+
+/* Number of streaming multiprocessors of the context's device. */
+int fabric_sm_count(const fabric_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Materials                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Copy n_mat (1..65535) host material records into the context's material
+ * table (used by the shading calls: G-buffer material indices refer to it).
+ * Builds the weave and float-run tables.  Synchronous. */
+fabric_status fabric_set_materials(fabric_ctx *ctx, const fabric_material *m, int n_mat);
+
+/* ------------------------------------------------------------------ */
+/* Network parameters                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Flat FP32 parameter counts.  Decoder layout (weights [out][in]):
+ *   W1[64][71] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[4][64] b4[4]
+ * with input [latent(32) | enc(u)(16) | enc(v)(16) | l | wi(3) | wo(3)],
+ * output the four components of Eq. 7 (C_warp, C_weft, S'_warp, S'_weft).
+ * Encoder layout: E1[128][14] e1[128] E2[128][128] e2[128] E3[32][128] e3[32]
+ * (parameters -> latent, residual block of Sec. 4.2). */
+int64_t fabric_decoder_param_count(void);
+int64_t fabric_encoder_param_count(void);
+
+/* Copy host FP32 parameters into the context (either pointer may be NULL to
+ * leave that network unchanged).  Resets the Adam state.  Synchronous. */
+fabric_status fabric_set_params(fabric_ctx *ctx, const float *decoder, const float *encoder);
+
+/* Copy the context's parameters to host memory (NULL skips).  Synchronous. */
+fabric_status fabric_get_params(fabric_ctx *ctx, float *decoder, float *encoder);
+
+/* Device pointers to the context's FP32 master parameters (valid until the
+ * context is destroyed); for callers that drive training themselves. */
+fabric_status fabric_param_pointers(fabric_ctx *ctx, float **decoder_dev, float **encoder_dev);
+
+/* Checkpoint: parameters, Adam moments and step counter in a versioned
+ * binary file with a CRC-32.  Synchronous.  Load fails with FABRIC_ERR_IO on
+ * a missing, truncated or corrupted file and leaves the context unchanged. */
+fabric_status fabric_checkpoint_save(fabric_ctx *ctx, const char *path);
+fabric_status fabric_checkpoint_load(fabric_ctx *ctx, const char *path);
+
+/* ------------------------------------------------------------------ */
+/* The four calls of the shading path                                 */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Encoder (Sec. 4.2, "Encoder"; run only when materials change, Sec. 4.4):
+ * material parameters -> latent z in R^32 for n_mat host records, written
+ * to latents_dev [n_mat][32] FP32.  Input features: one-hot weave (8),
+ * psi/30, u/45, alpha_warp, beta_warp, alpha_weft, beta_weft.
+ */
+fabric_status fabric_encode_params(fabric_ctx *ctx, const fabric_material *m, int n_mat,
+                                   float *latents_dev, void *stream);
+
+/*
+ * Supersampled reference (the plain method, Eq. 3-5 with the components of
+ * Eq. 7 and Eq. 8): for every point, spp_x * spp_y stratified samples over
+ * the footprint square, jittered by SplitMix64(seed, point index, sample),
+ * shaded with the model of Eq. 1-2, summed with warp-level reductions.
+ * Outputs rgb_dev [n][3] (Eq. 8 with the material's albedos) and, if not
+ * NULL, comps_dev [n][4] = (C_warp, C_weft, S_warp, S_weft).
+ * 1 <= spp_x, spp_y <= 4096.
+ */
+fabric_status fabric_shade_reference(fabric_ctx *ctx, const fabric_gbuffer *g, int spp_x, int spp_y,
+                                     uint64_t seed, float *rgb_dev, float *comps_dev, void *stream);
+
+/*
+ * Neural shading (Sec. 4.4, "Rendering"): decoder over the G-buffer with the
+ * per-material latents latents_dev [n_mat][32] (n_mat = size of the material
+ * table), then C = max(0, y), S = max(0, expm1(y')/100) (inverse of Eq. 9)
+ * and Eq. 8.  Outputs as for fabric_shade_reference.  FP32 runs the SIMT
+ * decoder; FP16 / BF16 / FP8 run the tensor-core decoder (material table of at most
+ * 89 entries).
+ */
+fabric_status fabric_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                  fabric_precision prec, float *rgb_dev, float *comps_dev, void *stream);
+
+/*
+ * fabric_shade_neural split in its two stages, for renderers that edit
+ * materials rarely and draw frames often (Sec. 4.4: only the decoder runs per
+ * frame, the encoder and the latent fold run on edits):
+ *  - fabric_prepare_neural folds latents_dev [n_mat][32] into the first layer
+ *    and packs the operands of `prec` into the context (one small kernel);
+ *    latents_dev must stay valid for FP32 frames.
+ *  - fabric_shade_neural_prepared draws one G-buffer with the last prepared
+ *    state of the same precision (FABRIC_ERR_INVALID_ARG if none, or if the
+ *    material table or parameters changed since).
+ */
+fabric_status fabric_prepare_neural(fabric_ctx *ctx, const float *latents_dev, fabric_precision prec,
+                                    void *stream);
+fabric_status fabric_shade_neural_prepared(fabric_ctx *ctx, const fabric_gbuffer *g, fabric_precision prec,
+                                           float *rgb_dev, float *comps_dev, void *stream);
+
+/*
+ * Training batch: queries (material indices refer to the training material
+ * table set by fabric_set_train_materials) and ground-truth components
+ * target_dev [n][4] (C_warp, C_weft, S_warp, S_weft), e.g. from
+ * fabric_shade_reference.
+ */
+typedef struct {
+  fabric_gbuffer queries;
+  const float *target;
+} fabric_train_batch;
+
+/* Copy the training material table (1..65535 records).  Synchronous. */
+fabric_status fabric_set_train_materials(fabric_ctx *ctx, const fabric_material *m, int n_mat);
+
+/*
+ * One training step (Sec. 4.3, Sec. 5.2): encoder over the training
+ * materials, decoder over the batch, the loss of Eq. 11 (specular mapped by
+ * g(x) = ln(100 x + 1), Eq. 9; lambda_S = 0.4, lambda_C = 0.1), backward
+ * through both networks with deterministic reductions, one Adam update
+ * (beta1 0.9, beta2 0.999, eps 1e-8) of the context's parameters.
+ * *loss_dev (device double) receives the batch loss before the update.
+ * Batch size 1..1048576.
+ */
+fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr,
+                                double *loss_dev, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Building blocks for a torch.autograd.Function                      */
+/* ------------------------------------------------------------------ */
+
+/* Raw decoder head y_dev [n][4] (no output activation) for the G-buffer,
+ * with latents_dev [n_lat][32] indexed by g->material and explicit FP32
+ * decoder parameters dec_dev (layout above).  FP32 SIMT. */
+fabric_status fabric_decoder_forward(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                     int n_lat, const float *dec_dev, float *y_dev, void *stream);
+
+/* Gradients of sum(dy * y): ddec_dev [decoder params] and dlatents_dev
+ * [n_lat][32] are overwritten (not accumulated).  Deterministic. */
+fabric_status fabric_decoder_backward(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                      int n_lat, const float *dec_dev, const float *dy_dev,
+                                      float *ddec_dev, float *dlatents_dev, void *stream);
+
+/* Encoder on explicit features feats_dev [n][14] -> z_dev [n][32]. */
+fabric_status fabric_encoder_forward(fabric_ctx *ctx, const float *feats_dev, int n, const float *enc_dev,
+                                     float *z_dev, void *stream);
+
+/* Gradients of sum(dz * z): denc_dev [encoder params] overwritten. */
+fabric_status fabric_encoder_backward(fabric_ctx *ctx, const float *feats_dev, int n, const float *enc_dev,
+                                      const float *dz_dev, float *denc_dev, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Image-wide error (FP64 on the device)                              */
+/* ------------------------------------------------------------------ */
+
+/* out_dev[0] = sum (a-b)^2, out_dev[1] = sum b^2, out_dev[2] = max |a-b|
+ * over n floats (device double[3]); RMSE = sqrt(out0/n), rel-L2 =
+ * sqrt(out0/out1).  Deterministic. */
+fabric_status fabric_error_stats(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int64_t n,
+                                 double *out_dev, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics                                                        */
+/* ------------------------------------------------------------------ */
+
+/* One 128 x N x K BF16 tensor-core product through the same shared-memory
+ * layouts, descriptors and tensor-memory path as the decoder:
+ * d_dev[128][n] = a_dev[128][k] * b_dev[n][k]^T with a, b given as FP32 and
+ * rounded to BF16.  k in {16, 32, 48, 64}, n in {16, 32, 64}.  Used by the
+ * tests to check the tensor-core data layout in isolation. */
+fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
+                                  float *d_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FABRIC_H */

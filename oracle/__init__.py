@@ -76,7 +76,8 @@ def lib():
                                               u64, P(u32), P(u32)]
             L.ora_shade_reference.restype = None
             L.ora_shade_reference.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6 + [
-                i64, ctypes.c_int, ctypes.c_int, u64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+                i64, ctypes.c_int, ctypes.c_int, u64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                ctypes.c_void_p]
             L.ora_period_quadrature.restype = None
             L.ora_period_quadrature.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
@@ -177,10 +178,12 @@ def sample_position(u, v, r, pixel, k, nx, ny, seed):
     return pu.value, pv.value
 
 
-def shade_reference(materials, gbuf: dict, spp_x: int, spp_y: int, seed: int, nthreads: int = 0):
+def shade_reference(materials, gbuf: dict, spp_x: int, spp_y: int, seed: int, nthreads: int = 0,
+                    pixel_index=None):
     """Stratified footprint estimator over a G-buffer (dict of numpy arrays
     u, v, radius float32 [n]; wi, wo float32 [n,3]; material uint16 [n]).
-    Returns (comps [n,4], rgb [n,3]) in FP64."""
+    `pixel_index` (int64 [n]) gives each point's index in the full buffer when
+    the arrays are a subset of it.  Returns (comps [n,4], rgb [n,3]) in FP64."""
     rows = material_rows(materials)
     u = np.ascontiguousarray(gbuf["u"], np.float32)
     v = np.ascontiguousarray(gbuf["v"], np.float32)
@@ -191,9 +194,10 @@ def shade_reference(materials, gbuf: dict, spp_x: int, spp_y: int, seed: int, nt
     n = len(u)
     comps = np.zeros((n, 4))
     rgb = np.zeros((n, 3))
+    idx = None if pixel_index is None else np.ascontiguousarray(pixel_index, np.int64)
     lib().ora_shade_reference(_ptr(rows), len(rows), _ptr(u), _ptr(v), _ptr(r), _ptr(wi), _ptr(wo),
                               _ptr(mat), n, spp_x, spp_y, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
-                              _ptr(comps), _ptr(rgb), int(nthreads))
+                              _ptr(comps), _ptr(rgb), int(nthreads), None if idx is None else _ptr(idx))
     return comps, rgb
 
 

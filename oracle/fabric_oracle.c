@@ -323,18 +323,20 @@ static void shade_one(const double *mats, int n_mat, float u, float v, float r,
               m[M_KS_W + ch] * comps[2] + m[M_KS_F + ch] * comps[3];
 }
 
-/* Supersampled footprint integral for n points (structure of arrays). */
+/* Supersampled footprint integral for n points (structure of arrays).  The
+ * sample jitter of point p is keyed by its index in the full G-buffer:
+ * pixel_index[p] when given (a subset of a larger buffer), else p.          */
 void ora_shade_reference(const double *mats, int n_mat, const float *u, const float *v,
                          const float *r, const float *wi, const float *wo,
                          const uint16_t *mat, int64_t n, int nx, int ny, uint64_t seed,
-                         double *comps, double *rgb, int nthreads) {
+                         double *comps, double *rgb, int nthreads, const int64_t *pixel_index) {
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
 #endif
   for (int64_t p = 0; p < n; ++p)
-    shade_one(mats, n_mat, u[p], v[p], r[p], wi + 3 * p, wo + 3 * p, (int)mat[p], p,
-              nx, ny, seed, comps + 4 * p, rgb + 3 * p);
+    shade_one(mats, n_mat, u[p], v[p], r[p], wi + 3 * p, wo + 3 * p, (int)mat[p],
+              pixel_index ? pixel_index[p] : p, nx, ny, seed, comps + 4 * p, rgb + 3 * p);
   (void)nthreads;
 }
 

@@ -1,0 +1,292 @@
+"""Python binding of the fabric library: argument marshalling only.
+
+PyTorch supplies device memory and streams; every step of the shading path
+runs in the library's CUDA kernels behind the C ABI of include/fabric.h.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import FabricGBuffer, FabricMaterial, FabricTrainBatch, check
+
+LATENT = 32
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def material_array(materials) -> ctypes.Array:
+    """Host array of fabric_material from a structured numpy array with the
+    fields of ``workloads.MATERIAL_DTYPE`` (same 84-byte layout)."""
+    m = np.ascontiguousarray(np.atleast_1d(materials))
+    if m.dtype.itemsize != ctypes.sizeof(FabricMaterial):
+        raise ValueError("material records must be 84-byte structured records")
+    arr = (FabricMaterial * len(m))()
+    ctypes.memmove(arr, m.ctypes.data, m.nbytes)
+    return arr
+
+
+@dataclass
+class GBuffer:
+    """Device G-buffer (structure of arrays): u, v, radius float32 [n];
+    wi, wo float32 [n, 3]; material uint16 bits stored in an int16 [n]."""
+    u: torch.Tensor
+    v: torch.Tensor
+    radius: torch.Tensor
+    wi: torch.Tensor
+    wo: torch.Tensor
+    material: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.u.shape[0])
+
+    @classmethod
+    def from_numpy(cls, g: dict, device="cuda", pin: bool = False) -> "GBuffer":
+        def conv(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a).view(dt) if dt == np.int16 else np.ascontiguousarray(a, dt))
+            if device == "cpu":
+                return t.pin_memory() if pin else t
+            return t.to(device)
+        return cls(u=conv(g["u"], np.float32), v=conv(g["v"], np.float32), radius=conv(g["radius"], np.float32),
+                   wi=conv(g["wi"], np.float32), wo=conv(g["wo"], np.float32),
+                   material=conv(np.asarray(g["material"], np.uint16), np.int16))
+
+    def to(self, device, non_blocking=False) -> "GBuffer":
+        return GBuffer(*(getattr(self, k).to(device, non_blocking=non_blocking)
+                         for k in ("u", "v", "radius", "wi", "wo", "material")))
+
+    def copy_(self, src: "GBuffer", non_blocking=True) -> "GBuffer":
+        for k in ("u", "v", "radius", "wi", "wo", "material"):
+            getattr(self, k).copy_(getattr(src, k), non_blocking=non_blocking)
+        return self
+
+    def nbytes(self) -> int:
+        return sum(getattr(self, k).numel() * getattr(self, k).element_size()
+                   for k in ("u", "v", "radius", "wi", "wo", "material"))
+
+    def struct(self) -> FabricGBuffer:
+        for k in ("u", "v", "radius", "wi", "wo", "material"):
+            t = getattr(self, k)
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"G-buffer field {k} must be a contiguous CUDA tensor")
+        return FabricGBuffer(self.u.data_ptr(), self.v.data_ptr(), self.radius.data_ptr(), self.wi.data_ptr(),
+                             self.wo.data_ptr(), self.material.data_ptr(), self.n)
+
+
+class Fabric:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _abi.load()
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        h = ctypes.c_void_p()
+        check(self.lib.fabric_create(ctypes.byref(h), device))
+        self.h = h
+        self.n_dec = int(self.lib.fabric_decoder_param_count())
+        self.n_enc = int(self.lib.fabric_encoder_param_count())
+        self.n_mat = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fabric_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status):
+        check(status, self.h)
+
+    @property
+    def sm_count(self) -> int:
+        return int(self.lib.fabric_sm_count(self.h))
+
+    def sync_status(self, stream=None):
+        self._check(self.lib.fabric_sync_status(self.h, _stream_handle(stream)))
+
+    # ---------------------------------------------------------------- setup
+    def set_materials(self, materials):
+        arr = material_array(materials)
+        self._check(self.lib.fabric_set_materials(self.h, arr, len(arr)))
+        self.n_mat = len(arr)
+
+    def set_train_materials(self, materials):
+        arr = material_array(materials)
+        self._check(self.lib.fabric_set_train_materials(self.h, arr, len(arr)))
+
+    def set_params(self, decoder=None, encoder=None):
+        d = None if decoder is None else np.ascontiguousarray(decoder, np.float32)
+        e = None if encoder is None else np.ascontiguousarray(encoder, np.float32)
+        if d is not None and d.size != self.n_dec:
+            raise ValueError(f"decoder needs {self.n_dec} parameters")
+        if e is not None and e.size != self.n_enc:
+            raise ValueError(f"encoder needs {self.n_enc} parameters")
+        self._check(self.lib.fabric_set_params(self.h, None if d is None else d.ctypes.data_as(ctypes.c_void_p),
+                                               None if e is None else e.ctypes.data_as(ctypes.c_void_p)))
+
+    def get_params(self):
+        d = np.empty(self.n_dec, np.float32)
+        e = np.empty(self.n_enc, np.float32)
+        self._check(self.lib.fabric_get_params(self.h, d.ctypes.data_as(ctypes.c_void_p),
+                                               e.ctypes.data_as(ctypes.c_void_p)))
+        return d, e
+
+    def param_tensors(self):
+        """Views of the context's FP32 master parameters as CUDA tensors."""
+        pd, pe = ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(self.lib.fabric_param_pointers(self.h, ctypes.byref(pd), ctypes.byref(pe)))
+        return pd.value, pe.value
+
+    def checkpoint_save(self, path: str):
+        self._check(self.lib.fabric_checkpoint_save(self.h, path.encode()))
+
+    def checkpoint_load(self, path: str):
+        self._check(self.lib.fabric_checkpoint_load(self.h, path.encode()))
+
+    # ----------------------------------------------------------- the path
+    def encode_params(self, materials, stream=None) -> torch.Tensor:
+        arr = material_array(materials)
+        z = torch.empty((len(arr), LATENT), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_encode_params(self.h, arr, len(arr), _ptr(z), _stream_handle(stream)))
+        return z
+
+    def shade_reference(self, g: GBuffer, spp_x: int, spp_y: int, seed: int, comps: bool = False,
+                        out_rgb=None, out_comps=None, stream=None):
+        rgb = out_rgb if out_rgb is not None else torch.empty((g.n, 3), dtype=torch.float32, device=self.device)
+        cp = out_comps if out_comps is not None else (
+            torch.empty((g.n, 4), dtype=torch.float32, device=self.device) if comps else None)
+        gs = g.struct()
+        self._check(self.lib.fabric_shade_reference(self.h, ctypes.byref(gs), spp_x, spp_y,
+                                                    ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _ptr(rgb), _ptr(cp),
+                                                    _stream_handle(stream)))
+        return rgb, cp
+
+    def shade_neural(self, g: GBuffer, latents: torch.Tensor, precision: str = "fp16", comps: bool = False,
+                     out_rgb=None, out_comps=None, stream=None):
+        rgb = out_rgb if out_rgb is not None else torch.empty((g.n, 3), dtype=torch.float32, device=self.device)
+        cp = out_comps if out_comps is not None else (
+            torch.empty((g.n, 4), dtype=torch.float32, device=self.device) if comps else None)
+        lat = latents.contiguous()
+        gs = g.struct()
+        self._check(self.lib.fabric_shade_neural(self.h, ctypes.byref(gs), _ptr(lat), _abi.PREC[precision],
+                                                 _ptr(rgb), _ptr(cp), _stream_handle(stream)))
+        return rgb, cp
+
+    def prepare_neural(self, latents: torch.Tensor, precision: str = "fp16", stream=None):
+        """Fold the latents and pack the decoder operands (once per edit)."""
+        self._prepared_latents = latents.contiguous()
+        self._check(self.lib.fabric_prepare_neural(self.h, _ptr(self._prepared_latents), _abi.PREC[precision],
+                                                   _stream_handle(stream)))
+
+    def shade_neural_prepared(self, g: GBuffer, precision: str = "fp16", comps: bool = False, out_rgb=None,
+                              out_comps=None, stream=None):
+        """Draw one G-buffer with the last prepared state (one kernel)."""
+        rgb = out_rgb if out_rgb is not None else torch.empty((g.n, 3), dtype=torch.float32, device=self.device)
+        cp = out_comps if out_comps is not None else (
+            torch.empty((g.n, 4), dtype=torch.float32, device=self.device) if comps else None)
+        gs = g.struct()
+        self._check(self.lib.fabric_shade_neural_prepared(self.h, ctypes.byref(gs), _abi.PREC[precision],
+                                                          _ptr(rgb), _ptr(cp), _stream_handle(stream)))
+        return rgb, cp
+
+    def train_step(self, batch: GBuffer, target: torch.Tensor, lr: float, loss_out=None, stream=None):
+        loss = loss_out if loss_out is not None else torch.empty((), dtype=torch.float64, device=self.device)
+        tb = FabricTrainBatch(batch.struct(), target.contiguous().data_ptr())
+        self._check(self.lib.fabric_train_step(self.h, ctypes.byref(tb), ctypes.c_float(lr), _ptr(loss),
+                                               _stream_handle(stream)))
+        return loss
+
+    def error_stats(self, a: torch.Tensor, b: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        out = out if out is not None else torch.empty(3, dtype=torch.float64, device=self.device)
+        a = a.contiguous()
+        b = b.contiguous()
+        self._check(self.lib.fabric_error_stats(self.h, _ptr(a), _ptr(b), a.numel(), _ptr(out),
+                                                _stream_handle(stream)))
+        return out
+
+    def selftest_mma(self, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+        n, k = b.shape
+        d = torch.empty((128, n), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_selftest_mma(self.h, _ptr(a.contiguous()), _ptr(b.contiguous()), n, k, _ptr(d),
+                                                 _stream_handle(None)))
+        return d
+
+    # ---------------------------------------------- autograd building blocks
+    def decoder_forward(self, g: GBuffer, latents, dec, stream=None):
+        y = torch.empty((g.n, 4), dtype=torch.float32, device=self.device)
+        gs = g.struct()
+        self._check(self.lib.fabric_decoder_forward(self.h, ctypes.byref(gs), _ptr(latents.contiguous()),
+                                                    latents.shape[0], _ptr(dec.contiguous()), _ptr(y),
+                                                    _stream_handle(stream)))
+        return y
+
+    def decoder_backward(self, g: GBuffer, latents, dec, dy, stream=None):
+        ddec = torch.empty(self.n_dec, dtype=torch.float32, device=self.device)
+        dlat = torch.empty_like(latents)
+        gs = g.struct()
+        self._check(self.lib.fabric_decoder_backward(self.h, ctypes.byref(gs), _ptr(latents.contiguous()),
+                                                     latents.shape[0], _ptr(dec.contiguous()),
+                                                     _ptr(dy.contiguous()), _ptr(ddec), _ptr(dlat),
+                                                     _stream_handle(stream)))
+        return ddec, dlat
+
+    def encoder_forward(self, feats, enc, stream=None):
+        z = torch.empty((feats.shape[0], LATENT), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_encoder_forward(self.h, _ptr(feats.contiguous()), feats.shape[0],
+                                                    _ptr(enc.contiguous()), _ptr(z), _stream_handle(stream)))
+        return z
+
+    def encoder_backward(self, feats, enc, dz, stream=None):
+        denc = torch.empty(self.n_enc, dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_encoder_backward(self.h, _ptr(feats.contiguous()), feats.shape[0],
+                                                     _ptr(enc.contiguous()), _ptr(dz.contiguous()), _ptr(denc),
+                                                     _stream_handle(stream)))
+        return denc
+
+
+class DecoderFunction(torch.autograd.Function):
+    """y = decoder(latents[material], query; dec) with the library's FP32
+    forward and deterministic backward kernels."""
+
+    @staticmethod
+    def forward(ctx, dec: torch.Tensor, latents: torch.Tensor, fab: Fabric, g: GBuffer):
+        ctx.fab, ctx.g = fab, g
+        ctx.save_for_backward(dec, latents)
+        return fab.decoder_forward(g, latents, dec)
+
+    @staticmethod
+    def backward(ctx, dy):
+        dec, latents = ctx.saved_tensors
+        ddec, dlat = ctx.fab.decoder_backward(ctx.g, latents, dec, dy)
+        return ddec, dlat, None, None
+
+
+class EncoderFunction(torch.autograd.Function):
+    """z = encoder(features; enc) with the library's kernels."""
+
+    @staticmethod
+    def forward(ctx, enc: torch.Tensor, feats: torch.Tensor, fab: Fabric):
+        ctx.fab = fab
+        ctx.save_for_backward(enc, feats)
+        return fab.encoder_forward(feats, enc)
+
+    @staticmethod
+    def backward(ctx, dz):
+        enc, feats = ctx.saved_tensors
+        return ctx.fab.encoder_backward(feats, enc, dz), None, None

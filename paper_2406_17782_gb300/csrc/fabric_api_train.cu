@@ -1,0 +1,187 @@
+// fabric_api_train.cu -- C ABI entry points of the encoder, the training step
+// and the autograd building blocks (include/fabric.h).  Host code only.
+#include "fabric_internal.h"
+
+using namespace fab;
+
+namespace {
+
+#define FAB_CHECK_CTX(ctx)                                                \
+  do {                                                                    \
+    if (!(ctx)) return FABRIC_ERR_INVALID_ARG;                            \
+    (ctx)->last_error.clear();                                            \
+    if (cudaSetDevice((ctx)->device) != cudaSuccess)                      \
+      return cuda_fail((ctx), cudaGetLastError(), "cudaSetDevice");       \
+  } while (0)
+
+#define FAB_CUDA(ctx, expr, what)                                         \
+  do {                                                                    \
+    cudaError_t e_ = (expr);                                              \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, (what));           \
+  } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bump allocator over the context's scratch arena.
+struct Carve {
+  uint8_t *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    T *p = reinterpret_cast<T *>(base + off);
+    off = align_up(off + count * sizeof(T));
+    return p;
+  }
+};
+
+bool check_materials(fabric_ctx *ctx, const fabric_material *m, int n) {
+  for (int k = 0; k < n; ++k) {
+    DevMaterial tmp;
+    std::string why;
+    if (!build_material(m[k], &tmp, &why)) {
+      fail(ctx, FABRIC_ERR_INVALID_ARG, "material %d: %s", k, why.c_str());
+      return false;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+fabric_status fabric_encode_params(fabric_ctx *ctx, const fabric_material *m, int n_mat, float *latents_dev,
+                                   void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (n_mat == 0) return FABRIC_OK;
+  if (!m || !latents_dev || n_mat < 0 || n_mat > 65535)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "need materials, a latent buffer and 0..65535 records");
+  if (!check_materials(ctx, m, n_mat)) return FABRIC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ctx->enc_raw_cap < n_mat) {
+    FAB_CUDA(ctx, cudaStreamSynchronize(s), "encode staging");
+    cudaFree(ctx->d_enc_raw);
+    ctx->d_enc_raw = nullptr;
+    ctx->enc_raw_cap = 0;
+    FAB_CUDA(ctx, cudaMalloc(&ctx->d_enc_raw, n_mat * sizeof(fabric_material)), "encode staging");
+    ctx->enc_raw_cap = n_mat;
+  }
+  FAB_CUDA(ctx, cudaMemcpyAsync(ctx->d_enc_raw, m, n_mat * sizeof(fabric_material), cudaMemcpyHostToDevice, s),
+           "encode upload");
+  float *feats = static_cast<float *>(scratch(ctx, align_up((size_t)n_mat * kEncIn * 4)));
+  if (!feats) return fail(ctx, FABRIC_ERR_OOM, "scratch");
+  FAB_CUDA(ctx, launch_material_features(ctx->d_enc_raw, n_mat, feats, s), "features");
+  FAB_CUDA(ctx, launch_encoder_feats(feats, n_mat, ctx->d_enc, latents_dev, nullptr, s), "encoder");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr, double *loss_dev,
+                                void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!batch) return fail(ctx, FABRIC_ERR_INVALID_ARG, "batch is NULL");
+  const fabric_gbuffer &q = batch->queries;
+  if (!check_gbuffer(ctx, &q)) return FABRIC_ERR_INVALID_ARG;
+  if (q.n < 1 || q.n > (1 << 20)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "batch size must be 1..1048576");
+  if (!batch->target) return fail(ctx, FABRIC_ERR_INVALID_ARG, "targets are NULL");
+  if (!(lr >= 0.0f)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "learning rate must be >= 0");
+  if (ctx->n_train_mat < 1) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no training materials set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int M = ctx->n_train_mat;
+  const size_t need = align_up((size_t)M * kEncIn * 4) + align_up((size_t)M * kLatent * 4) +
+                      align_up((size_t)M * 2 * kEncHidden * 4) +
+                      align_up(((size_t)kDecParams + kEncParams) * 4) + align_up((size_t)M * kLatent * 4) +
+                      align_up(encoder_backward_work_floats(M) * 4) +
+                      align_up(decoder_backward_work_bytes(q.n, ctx->sm_count)) + align_up(8);
+  void *base = scratch(ctx, need);
+  if (!base) return fail(ctx, FABRIC_ERR_OOM, "training scratch (%zu bytes)", need);
+  Carve c{static_cast<uint8_t *>(base)};
+  float *feats = c.take<float>((size_t)M * kEncIn);
+  float *z = c.take<float>((size_t)M * kLatent);
+  float *acts = c.take<float>((size_t)M * 2 * kEncHidden);
+  float *grad = c.take<float>((size_t)kDecParams + kEncParams);
+  float *dz = c.take<float>((size_t)M * kLatent);
+  float *ework = c.take<float>(encoder_backward_work_floats(M));
+  void *dwork = c.take<uint8_t>(decoder_backward_work_bytes(q.n, ctx->sm_count));
+  double *loss_tmp = c.take<double>(1);
+  double *loss = loss_dev ? loss_dev : loss_tmp;
+  FAB_CUDA(ctx, launch_material_features(ctx->d_train_raw, M, feats, s), "features");
+  FAB_CUDA(ctx, launch_encoder_feats(feats, M, ctx->d_enc, z, acts, s), "encoder forward");
+  FAB_CUDA(ctx,
+           launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, grad, dz, loss, dwork, ctx->sm_count,
+                                   ctx->d_status, s),
+           "decoder forward/backward");
+  FAB_CUDA(ctx, launch_encoder_backward(feats, M, ctx->d_enc, acts, dz, grad + kDecParams, ework, s),
+           "encoder backward");
+  ctx->adam_step += 1;
+  ctx->version += 1;
+  const size_t np = (size_t)kDecParams + kEncParams;
+  float *m = ctx->d_adam, *v = ctx->d_adam + np;
+  FAB_CUDA(ctx, launch_adam(ctx->d_dec, grad, m, v, kDecParams, lr, ctx->adam_step, s), "adam");
+  FAB_CUDA(ctx,
+           launch_adam(ctx->d_enc, grad + kDecParams, m + kDecParams, v + kDecParams, kEncParams, lr,
+                       ctx->adam_step, s),
+           "adam");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_decoder_forward(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev, int n_lat,
+                                     const float *dec_dev, float *y_dev, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!check_gbuffer(ctx, g)) return FABRIC_ERR_INVALID_ARG;
+  if (g->n == 0) return FABRIC_OK;
+  if (!latents_dev || !dec_dev || !y_dev || n_lat < 1)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "NULL pointer or n_lat < 1");
+  if (!is_aligned16(y_dev)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "y must be 16-byte aligned");
+  FAB_CUDA(ctx, launch_decoder_raw(*g, latents_dev, n_lat, dec_dev, y_dev, ctx->d_status,
+                                   static_cast<cudaStream_t>(stream)),
+           "decoder forward");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_decoder_backward(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                      int n_lat, const float *dec_dev, const float *dy_dev, float *ddec_dev,
+                                      float *dlatents_dev, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!check_gbuffer(ctx, g)) return FABRIC_ERR_INVALID_ARG;
+  if (!latents_dev || !dec_dev || !dy_dev || !ddec_dev || n_lat < 1)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "NULL pointer or n_lat < 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    FAB_CUDA(ctx, cudaMemsetAsync(ddec_dev, 0, kDecParams * sizeof(float), s), "zero");
+    if (dlatents_dev) FAB_CUDA(ctx, cudaMemsetAsync(dlatents_dev, 0, (size_t)n_lat * kLatent * 4, s), "zero");
+    return FABRIC_OK;
+  }
+  void *work = scratch(ctx, decoder_backward_work_bytes(g->n, ctx->sm_count));
+  if (!work) return fail(ctx, FABRIC_ERR_OOM, "scratch");
+  FAB_CUDA(ctx,
+           launch_decoder_backward(*g, latents_dev, n_lat, dec_dev, dy_dev, nullptr, ddec_dev, dlatents_dev, nullptr,
+                                   work, ctx->sm_count, ctx->d_status, s),
+           "decoder backward");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_encoder_forward(fabric_ctx *ctx, const float *feats_dev, int n, const float *enc_dev,
+                                     float *z_dev, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (n == 0) return FABRIC_OK;
+  if (!feats_dev || !enc_dev || !z_dev || n < 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "bad arguments");
+  FAB_CUDA(ctx, launch_encoder_feats(feats_dev, n, enc_dev, z_dev, nullptr, static_cast<cudaStream_t>(stream)),
+           "encoder forward");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_encoder_backward(fabric_ctx *ctx, const float *feats_dev, int n, const float *enc_dev,
+                                      const float *dz_dev, float *denc_dev, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!feats_dev || !enc_dev || !dz_dev || !denc_dev || n < 1)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "bad arguments");
+  float *work = static_cast<float *>(scratch(ctx, encoder_backward_work_floats(n) * 4));
+  if (!work) return fail(ctx, FABRIC_ERR_OOM, "scratch");
+  FAB_CUDA(ctx,
+           launch_encoder_backward(feats_dev, n, enc_dev, nullptr, dz_dev, denc_dev, work,
+                                   static_cast<cudaStream_t>(stream)),
+           "encoder backward");
+  return FABRIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// fabric_internal.h -- private declarations shared by the library's
+// translation units (context, device material record, launch helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fabric.h"
+
+namespace fab {
+
+constexpr int kLatent = 32;
+constexpr int kHidden = 64;
+constexpr int kQueryFeat = 39;          // enc(u) 16 | enc(v) 16 | l | wi 3 | wo 3
+constexpr int kDecIn = kLatent + kQueryFeat;
+constexpr int kOut = 4;
+constexpr int kEncIn = 14;
+constexpr int kEncHidden = 128;
+constexpr int kMaxPatternDim = 16;
+
+// flat decoder parameter offsets (weights [out][in])
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kHidden * kDecIn;
+constexpr int kOffW2 = kOffB1 + kHidden;
+constexpr int kOffB2 = kOffW2 + kHidden * kHidden;
+constexpr int kOffW3 = kOffB2 + kHidden;
+constexpr int kOffB3 = kOffW3 + kHidden * kHidden;
+constexpr int kOffW4 = kOffB3 + kHidden;
+constexpr int kOffB4 = kOffW4 + kOut * kHidden;
+constexpr int kDecParams = kOffB4 + kOut;
+
+constexpr int kOffE1 = 0;
+constexpr int kOffEb1 = kOffE1 + kEncHidden * kEncIn;
+constexpr int kOffE2 = kOffEb1 + kEncHidden;
+constexpr int kOffEb2 = kOffE2 + kEncHidden * kEncHidden;
+constexpr int kOffE3 = kOffEb2 + kEncHidden;
+constexpr int kOffEb3 = kOffE3 + kLatent * kEncHidden;
+constexpr int kEncParams = kOffEb3 + kLatent;
+
+// log-footprint feature l = (ln max(r, 2^-20) - c0) / c1 maps [1e-4, 1e-1] to [-1, 1]
+constexpr float kLogRC0 = -5.756462732485114f;   // (ln 1e-4 + ln 1e-1) / 2
+constexpr float kLogRInvC1 = 0.28952965460216784f; // 2 / (ln 1e-1 - ln 1e-4)
+constexpr float kRFloor = 9.5367431640625e-07f;    // 2^-20
+constexpr float kSpecK = 100.0f;                    // g(x) = ln(100 x + 1)
+
+// Device status word values (OR-ed).
+constexpr int kStatusBadMaterial = 1;
+constexpr int kStatusTimeout = 2;
+
+// Per-material record on the device: weave bits, per-cell inclination
+// (theta = theta0 - theta1 * t along the float) and shading constants.
+struct alignas(16) DevMaterial {
+  uint32_t rows, cols, gap_fixed, pad0;
+  uint32_t top[kMaxPatternDim];        // bit j of top[i]: warp over weft at (i, j)
+  float inv_one_minus_gap;             // 1 / (1 - g)
+  float cos_psi, sin_psi, w_blend;
+  float alpha[2];
+  float inv_alpha2_minus1[2];          // 1/alpha^2 - 1
+  float one_minus_alpha2[2];           // 1 - alpha^2
+  float inv_pi_alpha[2];               // 1 / (pi alpha)
+  float slope_scale[2];                // -beta pi / 2
+  float kd[2][3];
+  float ks[2][3];
+  float2 theta[kMaxPatternDim * kMaxPatternDim];
+};
+
+// Caller-visible status and messages.
+struct Ctx;
+
+}  // namespace fab
+
+struct fabric_ctx {
+  int device = 0;
+  int sm_count = 0;
+  std::string last_error;
+  // materials for shading
+  int n_mat = 0;
+  fab::DevMaterial *d_mat = nullptr;
+  std::vector<fabric_material> h_mat;
+  // materials for training
+  int n_train_mat = 0;
+  fabric_material *d_train_raw = nullptr;
+  // parameters (FP32 master) and Adam state
+  float *d_dec = nullptr;
+  float *d_enc = nullptr;
+  float *d_adam = nullptr;          // [m | v] over [dec | enc]
+  int64_t adam_step = 0;
+  // device status word
+  int *d_status = nullptr;
+  // growable scratch arena
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // staging for host material records (encoder)
+  fabric_material *d_enc_raw = nullptr;
+  int enc_raw_cap = 0;
+  // packed tensor-core weights (fixed size, largest material table) and
+  // partial sums of the error reduction
+  void *d_blob = nullptr;
+  double *d_err_work = nullptr;
+  // state of the last fabric_prepare_neural: precision (-1 = none), latents
+  // and the material / parameter versions it was built from
+  int prepared_prec = -1;
+  const float *prepared_latents = nullptr;
+  uint64_t prepared_version = 0;
+  uint64_t version = 1;            // bumped when materials or parameters change
+};
+
+namespace fab {
+
+fabric_status fail(fabric_ctx *ctx, fabric_status s, const char *fmt, ...);
+fabric_status cuda_fail(fabric_ctx *ctx, cudaError_t e, const char *what);
+// Make sure the scratch arena holds `bytes`; returns nullptr on failure.
+void *scratch(fabric_ctx *ctx, size_t bytes);
+bool build_material(const fabric_material &m, DevMaterial *out, std::string *why);
+bool check_gbuffer(fabric_ctx *ctx, const fabric_gbuffer *g);
+bool is_aligned16(const void *p);
+
+// Launchers implemented in the kernel translation units.
+cudaError_t launch_reference(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, int spp_x, int spp_y,
+                             uint64_t seed, float *rgb, float *comps, int *status, int lanes_per_point,
+                             int sm_count, cudaStream_t s);
+cudaError_t launch_decoder_fp32(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, const float *latents,
+                                const float *dec, float *rgb, float *comps, float *y_raw, int *status,
+                                cudaStream_t s);
+size_t tc_blob_bytes(int n_mat);
+int tc_k1(int n_mat);
+cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMaterial *mats, int n_mat,
+                           int precision, void *blob, cudaStream_t s);
+cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,
+                              float *comps, int *status, int sm_count, int ctas_per_sm, cudaStream_t s);
+cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, float *d, int *status,
+                                cudaStream_t s);
+cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *z, cudaStream_t s);
+cudaError_t launch_encoder_feats(const float *feats, int n, const float *enc, float *z, float *acts,
+                                 cudaStream_t s);
+cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc, const float *acts,
+                                    const float *dz, float *denc, float *work, cudaStream_t s);
+size_t encoder_backward_work_floats(int n);
+cudaError_t launch_material_features(const fabric_material *raw, int n, float *feats, cudaStream_t s);
+cudaError_t launch_decoder_raw(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
+                               float *y_raw, int *status, cudaStream_t s);
+cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
+                                    const float *dy, const float *target, float *ddec, float *dlat,
+                                    double *loss, void *work, int sm_count, int *status, cudaStream_t s);
+size_t decoder_backward_work_bytes(int64_t n, int sm_count);
+cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, int64_t step,
+                        cudaStream_t s);
+cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, double *out, void *work,
+                               cudaStream_t s);
+size_t error_stats_work_bytes(int64_t n);
+
+}  // namespace fab

@@ -18,3 +18,14 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def fab():
+    """One library context on cuda:0 (GPU tests only)."""
+    from paper_2406_17782_gb300 import build as b
+    b.build()
+    from paper_2406_17782_gb300.api import Fabric
+    f = Fabric(0)
+    yield f
+    f.close()

@@ -1,0 +1,213 @@
+"""Parity of the neural decoder kernels with the FP64 network oracle.
+
+* FP32 SIMT: per point |dy| <= max(1e-5 |y*|, B) on the raw head, where B is
+  the first-order FP32 forward rounding bound (gamma_n = n 2^-24 per dot
+  product, propagated through the layers) that takes over where y* is too
+  close to zero for a relative error to mean anything.
+* FP16 tensor cores (the default tensor-core precision): relative L2
+  <= 5e-3 over the sampled frame against FP64, and <= 2e-3 against the FP16
+  operand-rounding emulation of the same network.
+* BF16 tensor cores: relative L2 <= 1.2e-2 against FP64 (BF16 operand
+  rounding alone costs 8.2e-3 on this network, see the emulation), and
+  <= 2e-3 against the BF16 emulation.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from oracle import mlp as M
+from paper_2406_17782_gb300 import FabricError
+from paper_2406_17782_gb300.api import GBuffer
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = {"fp16": 5e-3, "bf16": 1.2e-2}
+TOL_EMU = 2e-3
+
+
+def rel_l2(got, want):
+    got = np.asarray(got, np.float64)
+    return float(np.sqrt(((got - want) ** 2).sum() / (want ** 2).sum()))
+
+
+def round_fp16(x):
+    return np.asarray(x, np.float32).astype(np.float16).astype(np.float64)
+
+
+ROUND = {"fp16": round_fp16, "bf16": M.round_bf16}
+
+
+@pytest.fixture(scope="module")
+def setup(fab):
+    mats = W.frame_materials()
+    fab.set_materials(mats)
+    dec = W.decoder_init()
+    fab.set_params(dec, W.encoder_init())
+    z = W.random_latents(len(mats))
+    return mats, dec, z
+
+
+def emulate(prec, dec_flat, z, mats, g):
+    """The tensor-core path's operand rounding: rounded query features,
+    rounded weights, latent folded into a rounded per-material bias column,
+    FP32 bias adds, rounded activations, FP32 accumulation (FP64 here)."""
+    r = ROUND[prec]
+    P = M.unpack(dec_flat, M.DEC_SHAPES)
+    q = r(M.query_features(g["u"], g["v"], g["radius"], g["wi"], g["wo"]))
+    mat = np.asarray(g["material"], np.int64)
+    fold = P["b1"][None, :] + z.astype(np.float64) @ P["W1"][:, :32].T
+    h = np.maximum(q @ r(P["W1"][:, 32:]).T + r(fold)[mat], 0)
+    h = np.maximum(r(h) @ r(P["W2"]).T + P["b2"], 0)
+    h = np.maximum(r(h) @ r(P["W3"]).T + P["b3"], 0)
+    y = r(h) @ r(P["W4"]).T + P["b4"]
+    comps = M.head_to_components(y)
+    return comps, M.recombine(comps, mats, g["material"])
+
+
+def fp32_forward_bound(P, x):
+    """First-order bound on the FP32 evaluation error of the raw head:
+    |d a| <= |W| |d x| + gamma_n (|W| |x| + |b|), gamma_n = n u, u = 2^-24,
+    input features carrying one rounding each; ReLU is 1-Lipschitz."""
+    u = 2.0 ** -24
+    dx = u * np.abs(x) + 1e-300
+    h = x
+    for Wn, bn in (("W1", "b1"), ("W2", "b2"), ("W3", "b3"), ("W4", "b4")):
+        Wm, b = P[Wn], P[bn]
+        n = Wm.shape[1]
+        a = h @ Wm.T + b
+        da = dx @ np.abs(Wm).T + n * u * (np.abs(h) @ np.abs(Wm).T + np.abs(b))
+        h = np.maximum(a, 0) if Wn != "W4" else a
+        dx = da
+    return dx
+
+
+@pytest.mark.parametrize("n,k", [(64, 16), (64, 48), (16, 64), (32, 32), (64, 64)])
+def test_tensor_core_product_layout(fab, n, k):
+    rng = np.random.default_rng(n * 100 + k)
+    a = rng.standard_normal((128, k)).astype(np.float32)
+    b = rng.standard_normal((n, k)).astype(np.float32)
+    d = fab.selftest_mma(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    fab.sync_status()
+    want = M.round_bf16(a) @ M.round_bf16(b).T
+    np.testing.assert_allclose(d, want, rtol=1e-5, atol=1e-5)
+
+
+def test_fp32_decoder_per_point(fab, setup):
+    mats, dec, z = setup
+    g = W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 4096, stream="dec-fp32"))
+    gd = GBuffer.from_numpy(g)
+    zt = torch.from_numpy(z).cuda()
+    y_gpu = fab.decoder_forward(gd, zt, torch.from_numpy(dec).cuda()).cpu().numpy()
+    rgb, comps = fab.shade_neural(gd, zt, "fp32", comps=True)
+    fab.sync_status()
+    P = M.unpack(dec, M.DEC_SHAPES)
+    x = M.decoder_inputs(z, g["material"], g)
+    y = M.decoder_forward(P, x)
+    tol = np.maximum(1e-5 * np.abs(y), fp32_forward_bound(P, x))
+    worst = np.max(np.abs(y_gpu - y) / tol)
+    rel = np.abs(y_gpu - y) / np.maximum(np.abs(y), 1e-30)
+    print(f"fp32 decoder: worst |dy|/tol {worst:.3f}; median rel {np.median(rel):.1e}; "
+          f"fraction within 1e-5 rel {np.mean(rel <= 1e-5):.4f}")
+    assert worst <= 1.0
+    assert rel_l2(y_gpu, y) <= 1e-6
+    want_c = M.head_to_components(y)
+    slope = np.concatenate([np.ones_like(y[:, :2]), np.exp(y[:, 2:]) / M.K_SPEC], axis=1)
+    assert np.all(np.abs(comps.cpu().numpy() - want_c) <= tol * slope * 1.01 + 1e-12)
+    want_rgb = M.recombine(want_c, mats, g["material"])
+    np.testing.assert_allclose(rgb.cpu().numpy(), want_rgb, rtol=2e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tensor_core_decoder_rel_l2(fab, setup, prec):
+    mats, dec, z = setup
+    g = W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 8192, stream="dec-bf16"))
+    rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), prec, comps=True)
+    fab.sync_status()
+    P = M.unpack(dec, M.DEC_SHAPES)
+    want_c, want_rgb = M.shade_neural(P, z, mats, g)
+    e_c, e_rgb = rel_l2(comps.cpu().numpy(), want_c), rel_l2(rgb.cpu().numpy(), want_rgb)
+    emu_c, _ = emulate(prec, dec, z, mats, g)
+    e_emu = rel_l2(comps.cpu().numpy(), emu_c)
+    print(f"{prec} rel-L2 vs FP64: comps {e_c:.2e} rgb {e_rgb:.2e}; vs {prec} emulation {e_emu:.2e}")
+    assert e_c <= TOL_FP64[prec] and e_rgb <= TOL_FP64[prec]
+    assert e_emu <= TOL_EMU
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
+def test_fp16_ragged_tiles(fab, setup, n):
+    mats, dec, z = setup
+    g = W.subset(W.frame_gbuffer(), np.arange(7000, 7000 + n))
+    rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp16", comps=True)
+    fab.sync_status()
+    want_c, _ = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, g)
+    assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
+
+
+def test_fp16_full_frame_sampled(fab, setup):
+    """The full 1080p G-buffer in the launch configuration the benchmark
+    times (prepared state, one decoder launch); 8192 sampled points
+    recomputed by the oracle."""
+    mats, dec, z = setup
+    g = W.frame_gbuffer()
+    gd = GBuffer.from_numpy(g)
+    fab.prepare_neural(torch.from_numpy(z).cuda(), "fp16")
+    rgb, comps = fab.shade_neural_prepared(gd, "fp16", comps=True)
+    fab.sync_status()
+    idx = W.sample_indices(len(g["u"]), 8192, stream="dec-full")
+    sub = W.subset(g, idx)
+    want_c, want_rgb = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, sub)
+    assert rel_l2(comps.cpu().numpy()[idx], want_c) <= TOL_FP64["fp16"]
+    assert rel_l2(rgb.cpu().numpy()[idx], want_rgb) <= TOL_FP64["fp16"]
+    assert np.isfinite(rgb.cpu().numpy()).all()
+    # the prepared state is refused once the parameters change
+    fab.set_params(dec, W.encoder_init())
+    with pytest.raises(FabricError):
+        fab.shade_neural_prepared(gd, "fp16")
+
+
+def test_fp16_material_limit_and_bad_index(fab, setup):
+    mats, dec, z = setup
+    g = W.subset(W.frame_gbuffer(), np.arange(0, 300))
+    g["material"] = g["material"].copy()
+    g["material"][17] = 9
+    rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp16", comps=True)
+    with pytest.raises(FabricError) as e:
+        fab.sync_status()
+    assert e.value.status == 7
+    c = comps.cpu().numpy()
+    assert np.isnan(c[17]).all() and np.isfinite(np.delete(c, 17, 0)).all()
+    many = np.concatenate([mats] * 12)          # 96 materials > 89
+    fab.set_materials(many)
+    with pytest.raises(FabricError) as e:
+        fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(W.random_latents(96)).cuda(), "fp16")
+    assert e.value.status == 6
+    fab.set_materials(mats)
+
+
+def test_fp16_many_materials_wider_first_layer(fab, setup):
+    """40 materials: the one-hot bias columns widen layer 1 to K = 80."""
+    mats, dec, z = setup
+    many = np.concatenate([mats] * 5)
+    fab.set_materials(many)
+    zz = W.random_latents(len(many), seed=11)
+    g = W.subset(W.frame_gbuffer(), np.arange(0, 2000))
+    g["material"] = (np.arange(2000) % len(many)).astype(np.uint16)
+    _, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(zz).cuda(), "fp16", comps=True)
+    fab.sync_status()
+    want_c, _ = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), zz, many, g)
+    fab.set_materials(mats)
+    assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
+
+
+def test_neural_error_stats_fp64_reduction(fab, setup):
+    """The FP64 image-wide error reduction against numpy on the same data."""
+    rng = np.random.default_rng(9)
+    a = rng.standard_normal(1_000_003).astype(np.float32)
+    b = (a + 1e-3 * rng.standard_normal(a.size)).astype(np.float32)
+    out = fab.error_stats(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    d = a.astype(np.float64) - b.astype(np.float64)
+    np.testing.assert_allclose(out[0], (d * d).sum(), rtol=1e-12)
+    np.testing.assert_allclose(out[1], (b.astype(np.float64) ** 2).sum(), rtol=1e-12)
+    assert out[2] == np.abs(d).max()

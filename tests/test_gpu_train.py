@@ -1,0 +1,183 @@
+"""Training kernels against the FP64 oracle: decoder and encoder gradients,
+the autograd Functions (finite differences), the fused Eq. 11 train step with
+Adam, determinism and checkpoint/resume."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from oracle import mlp as M
+from paper_2406_17782_gb300 import FabricError
+from paper_2406_17782_gb300.api import DecoderFunction, EncoderFunction, GBuffer
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(got, want):
+    got = np.asarray(got, np.float64)
+    return float(np.sqrt(((got - want) ** 2).sum() / max((want ** 2).sum(), 1e-300)))
+
+
+def batch(n, n_mat, stream="train-test"):
+    return W.training_queries(n, n_mat, stream=stream)
+
+
+def test_encode_params_matches_oracle(fab):
+    mats = W.training_materials(4)
+    enc = W.encoder_init()
+    fab.set_params(W.decoder_init(), enc)
+    z = fab.encode_params(mats).cpu().numpy()
+    want = M.encoder_forward(M.unpack(enc, M.ENC_SHAPES), M.encoder_features(mats))
+    np.testing.assert_allclose(z, want, rtol=1e-5, atol=1e-6)
+
+
+def test_decoder_gradients_match_oracle(fab):
+    rng = np.random.default_rng(0)
+    n_lat = 16
+    g = batch(3000, n_lat)
+    dec = W.decoder_init()
+    z = W.random_latents(n_lat, seed=21)
+    dy = rng.standard_normal((3000, 4)).astype(np.float32)
+    gd = GBuffer.from_numpy(g)
+    y = fab.decoder_forward(gd, torch.from_numpy(z).cuda(), torch.from_numpy(dec).cuda())
+    ddec, dlat = fab.decoder_backward(gd, torch.from_numpy(z).cuda(), torch.from_numpy(dec).cuda(),
+                                      torch.from_numpy(dy).cuda())
+    fab.sync_status()
+    P = M.unpack(dec, M.DEC_SHAPES)
+    x = M.decoder_inputs(z, g["material"], g)
+    yo, cache = M.decoder_forward(P, x, keep=True)
+    gr, dx = M.decoder_backward(P, cache, dy.astype(np.float64))
+    assert rel_l2(y.cpu().numpy(), yo) < 1e-5
+    got = M.unpack(ddec.cpu().numpy(), M.DEC_SHAPES)
+    for k, _ in M.DEC_SHAPES:
+        assert rel_l2(got[k], gr[k]) < 1e-4, k
+    dz = np.zeros((n_lat, 32))
+    np.add.at(dz, g["material"].astype(np.int64), dx[:, :32])
+    assert rel_l2(dlat.cpu().numpy(), dz) < 1e-4
+
+
+def test_encoder_gradients_match_oracle(fab):
+    rng = np.random.default_rng(1)
+    mats = W.training_materials(4)
+    f = M.encoder_features(mats)
+    enc = W.encoder_init()
+    dz = rng.standard_normal((len(mats), 32))
+    denc = fab.encoder_backward(torch.from_numpy(f.astype(np.float32)).cuda(), torch.from_numpy(enc).cuda(),
+                                torch.from_numpy(dz.astype(np.float32)).cuda()).cpu().numpy()
+    P = M.unpack(enc, M.ENC_SHAPES)
+    _, cache = M.encoder_forward(P, f, keep=True)
+    want = M.encoder_backward(P, cache, dz)
+    got = M.unpack(denc, M.ENC_SHAPES)
+    for k, _ in M.ENC_SHAPES:
+        assert rel_l2(got[k], want[k]) < 1e-4, k
+
+
+def test_autograd_functions_against_finite_differences(fab):
+    """Directional derivatives of L = sum(w * decoder(encoder(f))) by central
+    differences of the library's own forward passes (FP64 sums on the host)
+    against the gradients autograd obtains from the backward kernels."""
+    rng = np.random.default_rng(2)
+    mats = W.training_materials(2)
+    g = batch(2000, len(mats), stream="fd")
+    gd = GBuffer.from_numpy(g)
+    f = torch.from_numpy(M.encoder_features(mats).astype(np.float32)).cuda()
+    dec = torch.from_numpy(W.decoder_init()).cuda().requires_grad_(True)
+    enc = torch.from_numpy(W.encoder_init()).cuda().requires_grad_(True)
+    w = torch.from_numpy(rng.standard_normal((2000, 4)).astype(np.float32)).cuda()
+
+    def loss(d, e):
+        z = EncoderFunction.apply(e, f, fab)
+        y = DecoderFunction.apply(d, z, fab, gd)
+        return (y.double() * w.double()).sum()
+
+    L = loss(dec, enc)
+    gdec, genc = torch.autograd.grad(L, [dec, enc])
+    n_head = 4 * 64 + 4            # W4, b4: L is linear in them, no ReLU kink on the path
+    for which, rtol in (("dec", 2e-2), ("enc", 2e-2), ("head", 2e-3)):
+        base = enc if which == "enc" else dec
+        grad = genc if which == "enc" else gdec
+        v = rng.standard_normal(base.numel())
+        if which == "head":
+            v[:-n_head] = 0.0
+        v = torch.from_numpy((v / np.linalg.norm(v)).astype(np.float32)).cuda()   # unit direction
+        h = 3e-3
+        with torch.no_grad():
+            if which == "enc":
+                lp, lm = loss(dec, enc + h * v), loss(dec, enc - h * v)
+            else:
+                lp, lm = loss(dec + h * v, enc), loss(dec - h * v, enc)
+        fd = float((lp - lm) / (2 * h))
+        an = float((grad.double() * v.double()).sum())
+        assert abs(fd - an) <= rtol * max(abs(an), 1.0), (which, fd, an)
+
+
+def test_train_steps_match_fp64_oracle(fab):
+    mats = W.training_materials(2)
+    g = batch(1024, len(mats), stream="parity-steps")
+    rng = np.random.default_rng(3)
+    target = np.abs(rng.standard_normal((1024, 4)) * 0.2).astype(np.float32)
+    dec, enc = W.decoder_init(), W.encoder_init()
+    fab.set_params(dec, enc)
+    fab.set_train_materials(mats)
+    gd = GBuffer.from_numpy(g)
+    tt = torch.from_numpy(target).cuda()
+    lr = 1e-3
+    state = {}
+    od, oe = dec.astype(np.float64), enc.astype(np.float64)
+    for step in range(3):
+        loss = fab.train_step(gd, tt, lr)
+        fab.sync_status()
+        lo, od, oe = M.train_step(od, oe, state, mats, g["material"], g, target.astype(np.float64), lr)
+        assert abs(float(loss.item()) - lo) <= 1e-5 * abs(lo), (step, float(loss.item()), lo)
+    d, e = fab.get_params()
+    assert np.max(np.abs(d - od)) < 1e-4
+    assert np.max(np.abs(e - oe)) < 1e-4
+
+
+def test_train_step_deterministic_and_loss_decreases(fab):
+    mats = W.training_materials(2)
+    g = batch(4096, len(mats), stream="det")
+    target = np.abs(np.random.default_rng(4).standard_normal((4096, 4)) * 0.2).astype(np.float32)
+    gd, tt = GBuffer.from_numpy(g), torch.from_numpy(target).cuda()
+    fab.set_train_materials(mats)
+    runs = []
+    for _ in range(2):
+        fab.set_params(W.decoder_init(), W.encoder_init())
+        losses = [float(fab.train_step(gd, tt, 3e-3).item()) for _ in range(150)]
+        runs.append((losses, fab.get_params()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1][0], runs[1][1][0]) and np.array_equal(runs[0][1][1], runs[1][1][1])
+    assert runs[0][0][-1] < 0.5 * runs[0][0][0]
+
+
+def test_checkpoint_resume_is_bitwise(fab, tmp_path):
+    mats = W.training_materials(2)
+    g = batch(2048, len(mats), stream="ckpt")
+    target = np.abs(np.random.default_rng(5).standard_normal((2048, 4)) * 0.2).astype(np.float32)
+    gd, tt = GBuffer.from_numpy(g), torch.from_numpy(target).cuda()
+    fab.set_train_materials(mats)
+    fab.set_params(W.decoder_init(), W.encoder_init())
+    for _ in range(5):
+        fab.train_step(gd, tt, 1e-3)
+    path = str(tmp_path / "ck.bin")
+    fab.checkpoint_save(path)
+    for _ in range(5):
+        fab.train_step(gd, tt, 1e-3)
+    a = fab.get_params()
+    fab.set_params(np.zeros(13188, np.float32), np.zeros(22560, np.float32))
+    fab.checkpoint_load(path)
+    for _ in range(5):
+        fab.train_step(gd, tt, 1e-3)
+    b = fab.get_params()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0x40
+    open(path, "wb").write(bytes(raw))
+    with pytest.raises(FabricError) as e:
+        fab.checkpoint_load(path)
+    assert e.value.status == 5
+    with pytest.raises(FabricError):
+        fab.checkpoint_load(str(tmp_path / "missing.bin"))
