@@ -277,6 +277,38 @@ fabric_status fabric_error_stats(fabric_ctx *ctx, const float *a_dev, const floa
                                  double *out_dev, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Neural shading without any device allocation                       */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory while they draw: a renderer that captures its
+ * frame into a CUDA graph (cudaMalloc is not allowed during stream capture),
+ * or a host application that owns all device memory and forbids plug-ins to
+ * allocate at draw time.
+ *
+ * Same arguments, outputs and errors as fabric_shade_neural with
+ * prec = FABRIC_PREC_FP16 or FABRIC_PREC_BF16 (anything else is
+ * FABRIC_ERR_INVALID_ARG).  It uses the context's material table and
+ * parameters, set up beforehand, and keeps its per-call scratch (the packed
+ * decoder operands, at most 64 KiB) in one static device array that every
+ * GPU loading the library holds until the process exits.  It never calls
+ * cudaMalloc, cudaFree or any allocating routine.
+ *  - A material table whose packed operands do not fit the 64 KiB array is
+ *    rejected with FABRIC_ERR_INVALID_ARG; beyond 89 materials the call
+ *    returns FABRIC_ERR_UNSUPPORTED as fabric_shade_neural does.
+ *  - The first call on each device resolves the array's device address;
+ *    make that first call before any stream capture.
+ *  - All calls share the one array and overwrite all of it that they read,
+ *    so nothing needs clearing between calls, but calls that overlap on the
+ *    GPU (other streams, other host threads, other contexts on the same
+ *    device) race on it: order them on one stream.
+ */
+fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                          fabric_precision prec, float *rgb_dev, float *comps_dev,
+                                          void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Diagnostics                                                        */
 /* ------------------------------------------------------------------ */
 

@@ -93,6 +93,7 @@ def load(path: str | None = None):
         "fabric_encoder_backward": (st, [vp, vp, i32, vp, vp, vp, vp]),
         "fabric_error_stats": (st, [vp, vp, vp, i64, vp, vp]),
         "fabric_selftest_mma": (st, [vp, vp, vp, i32, i32, vp, vp]),
+        "fabric_shade_neural_noalloc": (st, [vp, P(FabricGBuffer), vp, st, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):
