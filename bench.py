@@ -220,6 +220,11 @@ def main():
     rgbs = [torch.empty((N_POINTS, 3), dtype=torch.float32, device="cuda") for _ in range(copies)]
     fab.prepare_neural(latents, args.precision)
     stream = torch.cuda.current_stream()
+    launch = None
+    if args.precision != "fp32":
+        from paper_2406_17782_gb300 import autotune
+        launch = autotune.tune_decoder(fab, gbufs[0], args.precision, reps=30)
+        launch = {"warpgroups": launch["warpgroups"], "ctas_per_sm": launch["ctas_per_sm"], "tuned_ms": launch["ms"]}
 
     sampler = ClockSampler(local, os.path.join(ROOT, f".bench_clocks_{rank}.csv"))
     for k in range(args.warmup):
@@ -274,7 +279,8 @@ def main():
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "points_per_frame": N_POINTS,
                    "l2": "4 rotating G-buffer copies, 4 x 79 MB > 129 MB L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "decoder_launch": launch},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_t, "unit": "TFLOP/s",
                      "frac": tflops / peak_t, "traffic": None,
                      "note": f"fused decoder kernel, {FLOP_PER_POINT} FLOP/pt x {N_POINTS} pts per launch, "

@@ -125,6 +125,22 @@ fabric_status fabric_sync_status(fabric_ctx *ctx, void *stream);
 /* Number of streaming multiprocessors of the context's device. */
 int fabric_sm_count(const fabric_ctx *ctx);
 
+/*
+ * Launch configuration (no counterpart in the paper; set by the autotuner):
+ *   decoder_ctas_per_sm  resident CTAs per SM of the persistent tensor-core
+ *                        decoder (0 = as many as fit; capped at what fits)
+ *   decoder_warpgroups   independent 128-point tile pipelines per decoder
+ *                        CTA sharing one copy of the weights, 1, 2 or 4
+ *                        (0 or 3 = 1); each uses 128 of the SM's 512
+ *                        tensor-memory columns
+ *   reference_lanes      lanes per shading point of the reference kernel,
+ *                        1, 2, 4, 8, 16 or 32 (0 = by sample count)
+ * Takes effect for the following calls.  FABRIC_ERR_INVALID_ARG on values
+ * outside those sets.
+ */
+fabric_status fabric_set_launch_config(fabric_ctx *ctx, int decoder_ctas_per_sm, int decoder_warpgroups,
+                                       int reference_lanes);
+
 /* ------------------------------------------------------------------ */
 /* Materials                                                          */
 /* ------------------------------------------------------------------ */
@@ -270,11 +286,47 @@ fabric_status fabric_encoder_backward(fabric_ctx *ctx, const float *feats_dev, i
 /* Image-wide error (FP64 on the device)                              */
 /* ------------------------------------------------------------------ */
 
-/* out_dev[0] = sum (a-b)^2, out_dev[1] = sum b^2, out_dev[2] = max |a-b|
- * over n floats (device double[3]); RMSE = sqrt(out0/n), rel-L2 =
- * sqrt(out0/out1).  Deterministic. */
+/* out_dev[0] = sum (w(a-b))^2, out_dev[1] = sum (w b)^2, out_dev[2] =
+ * max |w(a-b)| over n floats (device double[3]); RMSE = sqrt(out0/n),
+ * rel-L2 = sqrt(out0/out1).  w = 1 when weights_dev is NULL, else
+ * weights_dev[i / group] (one weight per group of `group` consecutive
+ * floats, e.g. per RGB pixel), read with stride weight_stride floats, so
+ * that for instance the z of a [n][3] direction array can weight RGB
+ * (renderers multiply f_P by <wi . n_s> under direct light).  Deterministic. */
 fabric_status fabric_error_stats(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int64_t n,
-                                 double *out_dev, void *stream);
+                                 const float *weights_dev, int group, int weight_stride, double *out_dev,
+                                 void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Batched draws                                                      */
+/* ------------------------------------------------------------------ */
+
+/* One segment of a batched draw: a G-buffer and its own outputs (device
+ * memory, caller-owned; comps_dev may be NULL, else 16-byte aligned). */
+typedef struct {
+  fabric_gbuffer g;
+  float *rgb_dev;     /* [g.n][3] */
+  float *comps_dev;   /* [g.n][4] or NULL */
+} fabric_segment;
+
+typedef struct fabric_plan fabric_plan;
+
+/*
+ * Batching (the paper renders one view per frame; a renderer with several
+ * views, cameras or ragged tiles per frame wants them in one launch):
+ * fabric_plan_create checks and uploads a table of 1..1048576 segments once
+ * (synchronous; the plan keeps the device pointers, not the data).
+ * fabric_plan_shade then shades every segment with the prepared neural
+ * state (fabric_prepare_neural, FP16 or BF16) in one persistent
+ * tensor-core launch over all segments' 128-point tiles: asynchronous, no
+ * host-side work besides the launch, so it can be captured in a CUDA graph
+ * and replayed.  Results equal per-segment fabric_shade_neural_prepared
+ * calls bit for bit.
+ */
+fabric_status fabric_plan_create(fabric_ctx *ctx, const fabric_segment *segs, int n_segs, fabric_plan **out);
+fabric_status fabric_plan_shade(fabric_ctx *ctx, const fabric_plan *plan, fabric_precision prec, void *stream);
+int64_t fabric_plan_points(const fabric_plan *plan);
+void fabric_plan_destroy(fabric_plan *plan);
 
 /* ------------------------------------------------------------------ */
 /* Neural shading without any device allocation                       */
@@ -315,10 +367,11 @@ fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabric_gbuffer 
 /* One 128 x N x K BF16 tensor-core product through the same shared-memory
  * layouts, descriptors and tensor-memory path as the decoder:
  * d_dev[128][n] = a_dev[128][k] * b_dev[n][k]^T with a, b given as FP32 and
- * rounded to BF16.  k in {16, 32, 48, 64}, n in {16, 32, 64}.  Used by the
- * tests to check the tensor-core data layout in isolation. */
+ * rounded to BF16.  k in {16, 32, 48, 64}, n in {16, 32, 64}.  a_in_tmem = 1
+ * places A in tensor memory (written with tcgen05.st), 0 in shared memory.
+ * Used by the tests to check the tensor-core data layouts in isolation. */
 fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
-                                  float *d_dev, void *stream);
+                                  int a_in_tmem, float *d_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,10 @@ class FabricTrainBatch(ctypes.Structure):
     _fields_ = [("queries", FabricGBuffer), ("target", ctypes.c_void_p)]
 
 
+class FabricSegment(ctypes.Structure):
+    _fields_ = [("g", FabricGBuffer), ("rgb_dev", ctypes.c_void_p), ("comps_dev", ctypes.c_void_p)]
+
+
 class FabricError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -72,6 +76,7 @@ def load(path: str | None = None):
         "fabric_status_string": (ctypes.c_char_p, [st]),
         "fabric_sync_status": (st, [vp, vp]),
         "fabric_sm_count": (i32, [vp]),
+        "fabric_set_launch_config": (st, [vp, i32, i32, i32]),
         "fabric_set_materials": (st, [vp, vp, i32]),
         "fabric_set_train_materials": (st, [vp, vp, i32]),
         "fabric_decoder_param_count": (i64, []),
@@ -91,9 +96,13 @@ def load(path: str | None = None):
         "fabric_decoder_backward": (st, [vp, P(FabricGBuffer), vp, i32, vp, vp, vp, vp, vp]),
         "fabric_encoder_forward": (st, [vp, vp, i32, vp, vp, vp]),
         "fabric_encoder_backward": (st, [vp, vp, i32, vp, vp, vp, vp]),
-        "fabric_error_stats": (st, [vp, vp, vp, i64, vp, vp]),
-        "fabric_selftest_mma": (st, [vp, vp, vp, i32, i32, vp, vp]),
+        "fabric_error_stats": (st, [vp, vp, vp, i64, vp, i32, i32, vp, vp]),
+        "fabric_selftest_mma": (st, [vp, vp, vp, i32, i32, i32, vp, vp]),
         "fabric_shade_neural_noalloc": (st, [vp, P(FabricGBuffer), vp, st, vp, vp, vp]),
+        "fabric_plan_create": (st, [vp, vp, i32, P(vp)]),
+        "fabric_plan_shade": (st, [vp, vp, st, vp]),
+        "fabric_plan_points": (i64, [vp]),
+        "fabric_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):

@@ -120,6 +120,11 @@ class Fabric:
     def sync_status(self, stream=None):
         self._check(self.lib.fabric_sync_status(self.h, _stream_handle(stream)))
 
+    def set_launch_config(self, decoder_ctas_per_sm: int = 0, decoder_warpgroups: int = 0, reference_lanes: int = 0):
+        self._check(self.lib.fabric_set_launch_config(self.h, int(decoder_ctas_per_sm), int(decoder_warpgroups),
+                                                      int(reference_lanes)))
+        self.launch_config = (int(decoder_ctas_per_sm), int(decoder_warpgroups), int(reference_lanes))
+
     # ---------------------------------------------------------------- setup
     def set_materials(self, materials):
         arr = material_array(materials)
@@ -205,6 +210,10 @@ class Fabric:
                                                           _ptr(rgb), _ptr(cp), _stream_handle(stream)))
         return rgb, cp
 
+    def plan(self, segments) -> "Plan":
+        """Batched draw over (GBuffer, rgb_out, comps_out or None) triples."""
+        return Plan(self, segments)
+
     def train_step(self, batch: GBuffer, target: torch.Tensor, lr: float, loss_out=None, stream=None):
         loss = loss_out if loss_out is not None else torch.empty((), dtype=torch.float64, device=self.device)
         tb = FabricTrainBatch(batch.struct(), target.contiguous().data_ptr())
@@ -212,19 +221,23 @@ class Fabric:
                                                _stream_handle(stream)))
         return loss
 
-    def error_stats(self, a: torch.Tensor, b: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    def error_stats(self, a: torch.Tensor, b: torch.Tensor, weights: torch.Tensor = None, group: int = 1,
+                    weight_stride: int = 1, out=None, stream=None) -> torch.Tensor:
+        """[sum (w(a-b))^2, sum (w b)^2, max |w(a-b)|] in FP64 on the device;
+        w = weights[i // group * weight_stride] (e.g. wi.z per RGB pixel)."""
         out = out if out is not None else torch.empty(3, dtype=torch.float64, device=self.device)
         a = a.contiguous()
         b = b.contiguous()
-        self._check(self.lib.fabric_error_stats(self.h, _ptr(a), _ptr(b), a.numel(), _ptr(out),
-                                                _stream_handle(stream)))
+        self._check(self.lib.fabric_error_stats(self.h, _ptr(a), _ptr(b), a.numel(),
+                                                _ptr(weights) if weights is not None else None, int(group),
+                                                int(weight_stride), _ptr(out), _stream_handle(stream)))
         return out
 
-    def selftest_mma(self, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    def selftest_mma(self, a: torch.Tensor, b: torch.Tensor, a_in_tmem: bool = False) -> torch.Tensor:
         n, k = b.shape
         d = torch.empty((128, n), dtype=torch.float32, device=self.device)
-        self._check(self.lib.fabric_selftest_mma(self.h, _ptr(a.contiguous()), _ptr(b.contiguous()), n, k, _ptr(d),
-                                                 _stream_handle(None)))
+        self._check(self.lib.fabric_selftest_mma(self.h, _ptr(a.contiguous()), _ptr(b.contiguous()), n, k,
+                                                 int(a_in_tmem), _ptr(d), _stream_handle(None)))
         return d
 
     # ---------------------------------------------- autograd building blocks
@@ -258,6 +271,37 @@ class Fabric:
                                                      _ptr(enc.contiguous()), _ptr(dz.contiguous()), _ptr(denc),
                                                      _stream_handle(stream)))
         return denc
+
+
+class Plan:
+    """Segments (views, ragged tiles) shaded by one persistent launch; the
+    tensors stay referenced for the plan's lifetime."""
+
+    def __init__(self, fab: Fabric, segments):
+        self.fab = fab
+        self.segments = list(segments)
+        arr = (_abi.FabricSegment * len(self.segments))()
+        for k, (g, rgb, comps) in enumerate(self.segments):
+            arr[k] = _abi.FabricSegment(g.struct(), rgb.data_ptr(), comps.data_ptr() if comps is not None else None)
+        h = ctypes.c_void_p()
+        fab._check(fab.lib.fabric_plan_create(fab.h, arr, len(arr), ctypes.byref(h)))
+        self.h = h
+        self.points = int(fab.lib.fabric_plan_points(h))
+
+    def shade(self, precision: str = "fp16", stream=None):
+        self.fab._check(self.fab.lib.fabric_plan_shade(self.fab.h, self.h, _abi.PREC[precision],
+                                                       _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.fab.lib.fabric_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class DecoderFunction(torch.autograd.Function):

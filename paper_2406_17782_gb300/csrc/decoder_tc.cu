@@ -2,20 +2,28 @@
 // (tcgen05, tensor memory), the per-shading-point hot path of the neural
 // method (Sec. 4.4: only the decoder runs per pixel).
 //
-// Per CTA (128 threads, one shading point per thread and per tile row):
-//   1. one bulk (TMA) copy stages the packed BF16 weights, biases and the
-//      per-material albedos in shared memory, once per CTA;
-//   2. persistent loop over 128-point tiles: each thread streams its point
-//      from the G-buffer, encodes it (sin/cos of 8 octaves of u and v, log
-//      footprint, wi, wo) and writes one BF16 row of the A tile;
-//   3. layer 1 (the latent part of W1 is folded into one per-material bias
+// A CTA holds one copy of the packed 16-bit weights in shared memory and WG
+// independent tile pipelines (warpgroups of 128 threads, one shading point
+// per thread and tile row).  Activations never touch shared memory: each
+// warpgroup owns 128 tensor-memory columns, [0, 64) for the FP32
+// accumulator D and [64, 128) for the 16-bit A operand of the next layer
+// (two values per 32-bit column, row i in lane i).
+//   1. one bulk (TMA) copy stages the weights and the per-material albedos
+//      in shared memory, once per CTA;
+//   2. each warpgroup loops over its 128-point tiles: every thread encodes
+//      its point (sin/cos of 8 octaves of u and v, log footprint, wi, wo)
+//      from registers loaded during the previous tile and stores its row of
+//      the layer-1 A operand into tensor memory (tcgen05.st);
+//   3. layer 1 (the latent part of W1 folded into one per-material bias
 //      column selected by a one-hot of the material: W1 z_m + b1 is exact
-//      algebra, computed once per call) and layers 2-4 run as tcgen05.mma
-//      chains into tensor memory; the epilogue of each layer reads its row
-//      back with tcgen05.ld, adds the bias, applies ReLU, rounds to BF16 and
-//      writes the next A tile;
+//      algebra, computed once per call) and layers 2-4 (their biases in a
+//      constant-one input column) run as tcgen05.mma with A in tensor memory
+//      and B in shared memory; each epilogue reads D back (tcgen05.ld),
+//      converts it with ReLU (cvt.rn.relu) and stores the next A operand;
 //   4. the head's four outputs become C = max(0, y), S = max(0, expm1(y)/100)
 //      and RGB by Eq. 8; only RGB (and optionally the components) is stored.
+// While one warpgroup waits for its products the others encode and convert,
+// which keeps the tensor pipe and the ALUs busy together.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -26,13 +34,15 @@ namespace fab {
 namespace {
 
 constexpr int kTile = 128;
-constexpr int kTmemCols = 64;
+constexpr int kKH = 80;                            // K of layers 2-4: 64 inputs + bias column + pad
+constexpr uint32_t kColsPerTile = 128;             // D [0, 64) | A [64, 128)
+constexpr uint32_t kColA = 64;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
-// ---- packed-weight blob layout (bytes), identical in global and shared memory
+// ---- packed-operand blob layout (bytes), identical in global and shared memory
 struct BlobLayout {
   int k1;
-  uint32_t w1, w2, w3, w4, b2, b3, b4, alb, total;
+  uint32_t w1, w2, w3, w4, alb, total;
 };
 
 __host__ __device__ inline BlobLayout blob_layout(int n_mat, int k1) {
@@ -40,15 +50,14 @@ __host__ __device__ inline BlobLayout blob_layout(int n_mat, int k1) {
   L.k1 = k1;
   L.w1 = 0;
   L.w2 = L.w1 + 64u * k1 * 2u;
-  L.w3 = L.w2 + 64u * 64u * 2u;
-  L.w4 = L.w3 + 64u * 64u * 2u;
-  L.b2 = L.w4 + 16u * 64u * 2u;
-  L.b3 = L.b2 + 64u * 4u;
-  L.b4 = L.b3 + 64u * 4u;
-  L.alb = L.b4 + 16u * 4u;
+  L.w3 = L.w2 + 64u * kKH * 2u;
+  L.w4 = L.w3 + 64u * kKH * 2u;
+  L.alb = L.w4 + 16u * kKH * 2u;
   L.total = L.alb + ((uint32_t)(n_mat * 12 * 4) + 15u) / 16u * 16u;
   return L;
 }
+
+__host__ __device__ inline uint32_t align1k(uint32_t x) { return (x + 1023u) & ~1023u; }
 
 __device__ __forceinline__ void put_bf16(uint8_t *base, uint32_t off, float v) {
   *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(v);
@@ -61,8 +70,9 @@ __device__ __forceinline__ void put_op(uint8_t *base, uint32_t off, float v) {
     put_bf16(base, off, v);
 }
 
-// Fold the latents into the first layer and pack every operand into the
-// canonical shared-memory layout (FP16 or BF16 operands).  One CTA.
+// Fold the latents into the first layer, append the biases of layers 2-4 as
+// an extra input column, and pack every operand into the canonical
+// shared-memory layout (FP16 or BF16).  One CTA.
 template <bool F16>
 __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ dec, const float *__restrict__ lat,
                                                    const DevMaterial *__restrict__ mats, int n_mat, int k1,
@@ -86,23 +96,19 @@ __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ dec
       v = fold[(c - kQueryFeat) * kHidden + o];
     put_op<F16>(blob, L.w1 + tc::core_offset(o, c, k1), v);
   }
-  for (int e = threadIdx.x; e < kHidden * kHidden; e += blockDim.x) {
-    const int o = e / kHidden, c = e % kHidden;
-    put_op<F16>(blob, L.w2 + tc::core_offset(o, c, 64), dec[kOffW2 + e]);
-    put_op<F16>(blob, L.w3 + tc::core_offset(o, c, 64), dec[kOffW3 + e]);
+  for (int e = threadIdx.x; e < kHidden * kKH; e += blockDim.x) {
+    const int o = e / kKH, c = e % kKH;
+    const float v2 = c < kHidden ? dec[kOffW2 + o * kHidden + c] : (c == kHidden ? dec[kOffB2 + o] : 0.0f);
+    const float v3 = c < kHidden ? dec[kOffW3 + o * kHidden + c] : (c == kHidden ? dec[kOffB3 + o] : 0.0f);
+    put_op<F16>(blob, L.w2 + tc::core_offset(o, c, kKH), v2);
+    put_op<F16>(blob, L.w3 + tc::core_offset(o, c, kKH), v3);
   }
-  for (int e = threadIdx.x; e < 16 * kHidden; e += blockDim.x) {
-    const int o = e / kHidden, c = e % kHidden;
-    put_op<F16>(blob, L.w4 + tc::core_offset(o, c, 64), o < kOut ? dec[kOffW4 + o * kHidden + c] : 0.0f);
+  for (int e = threadIdx.x; e < 16 * kKH; e += blockDim.x) {
+    const int o = e / kKH, c = e % kKH;
+    float v = 0.0f;
+    if (o < kOut) v = c < kHidden ? dec[kOffW4 + o * kHidden + c] : (c == kHidden ? dec[kOffB4 + o] : 0.0f);
+    put_op<F16>(blob, L.w4 + tc::core_offset(o, c, kKH), v);
   }
-  float *b2 = reinterpret_cast<float *>(blob + L.b2);
-  float *b3 = reinterpret_cast<float *>(blob + L.b3);
-  float *b4 = reinterpret_cast<float *>(blob + L.b4);
-  for (int e = threadIdx.x; e < kHidden; e += blockDim.x) {
-    b2[e] = dec[kOffB2 + e];
-    b3[e] = dec[kOffB3 + e];
-  }
-  if (threadIdx.x < 16) b4[threadIdx.x] = threadIdx.x < kOut ? dec[kOffB4 + threadIdx.x] : 0.0f;
   float *alb = reinterpret_cast<float *>(blob + L.alb);
   for (int e = threadIdx.x; e < n_mat * 12; e += blockDim.x) {
     const int m = e / 12, q = e % 12;
@@ -111,6 +117,9 @@ __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ dec
   }
 }
 
+// Single G-buffer: the pointers below.  Batched: `segs` / `seg_tile0` list
+// the segments (tile t belongs to the segment s with seg_tile0[s] <= t <
+// seg_tile0[s + 1]) and the single-buffer fields are unused.
 struct TcArgs {
   const float *u, *v, *radius, *wi, *wo;
   const uint16_t *material;
@@ -120,17 +129,49 @@ struct TcArgs {
   int n_mat, k1;
   float *rgb, *comps;
   int *status;
+  const SegDesc *segs;
+  const int64_t *seg_tile0;
+  int n_segs;
 };
 
-template <bool F16>
-__device__ __forceinline__ void store_row_chunk(uint8_t *tile, int row, int chunk, int K, const float *f8) {
-  tc::st_shared_v4(tile + tc::core_offset(row, chunk * 8, K), tc::pack2<F16>(f8[0], f8[1]),
-                   tc::pack2<F16>(f8[2], f8[3]), tc::pack2<F16>(f8[4], f8[5]), tc::pack2<F16>(f8[6], f8[7]));
+// Segment holding global tile `tile` (binary search over the prefix sums).
+__device__ __forceinline__ int find_segment(const TcArgs &a, int64_t tile) {
+  int lo = 0, hi = a.n_segs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(a.seg_tile0 + mid) <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Where tile `tile`'s rows live: point index base and the buffers.
+struct TileView {
+  const float *u, *v, *radius, *wi, *wo;
+  const uint16_t *material;
+  float *rgb, *comps;
+  int64_t n, first;   // points in the segment, index of the tile's first point in it
+};
+
+template <bool MULTI>
+__device__ __forceinline__ TileView tile_view(const TcArgs &a, int64_t tile) {
+  TileView t;
+  if (!MULTI || tile >= a.n_tiles) {
+    t.u = a.u; t.v = a.v; t.radius = a.radius; t.wi = a.wi; t.wo = a.wo; t.material = a.material;
+    t.rgb = a.rgb; t.comps = a.comps; t.n = MULTI ? 0 : a.n; t.first = tile * 128;
+  } else {
+    const int s = find_segment(a, tile);
+    const SegDesc &d = a.segs[s];
+    t.u = d.u; t.v = d.v; t.radius = d.radius; t.wi = d.wi; t.wo = d.wo; t.material = d.material;
+    t.rgb = d.rgb; t.comps = d.comps; t.n = d.n; t.first = (tile - __ldg(a.seg_tile0 + s)) * 128;
+  }
+  return t;
 }
 
 // sin / cos of 2 pi 2^k frac(x) for k = 0..7 by angle doubling from one
-// hardware sincos of the reduced angle 2 pi (frac(x) - 1/2) in [-pi, pi).
-__device__ __forceinline__ void octave_sincos(float x, float *f16) {
+// hardware sincos of the reduced angle 2 pi (frac(x) - 1/2) in [-pi, pi);
+// w[k] packs (sin, cos) of octave k.
+template <bool F16>
+__device__ __forceinline__ void octave_words(float x, uint32_t *w) {
   const float fr = x - floorf(x);
   float s, c;
   __sincosf(6.283185307179586f * (fr - 0.5f), &s, &c);
@@ -138,156 +179,219 @@ __device__ __forceinline__ void octave_sincos(float x, float *f16) {
   c = -c;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    f16[2 * k] = s;
-    f16[2 * k + 1] = c;
+    w[k] = tc::pack2<F16>(s, c);
     const float s2 = 2.0f * s * c;
     c = (c - s) * (c + s);
     s = s2;
   }
 }
 
-template <bool F16>
-__global__ void __launch_bounds__(kTile, 1) decoder_tc_kernel(const TcArgs a) {
+// One shading point's G-buffer record, held in registers between tiles.
+struct Point {
+  float u, v, r, wi0, wi1, wi2, wo0, wo1, wo2;
+  int mat;   // -1: beyond the end
+};
+
+__device__ __forceinline__ Point load_point(const TileView &a, int64_t p) {
+  Point q;
+  if (p < a.n) {
+    q.u = __ldg(a.u + p);
+    q.v = __ldg(a.v + p);
+    q.r = __ldg(a.radius + p);
+    q.wi0 = __ldg(a.wi + 3 * p);
+    q.wi1 = __ldg(a.wi + 3 * p + 1);
+    q.wi2 = __ldg(a.wi + 3 * p + 2);
+    q.wo0 = __ldg(a.wo + 3 * p);
+    q.wo1 = __ldg(a.wo + 3 * p + 1);
+    q.wo2 = __ldg(a.wo + 3 * p + 2);
+    q.mat = __ldg(a.material + p);
+  } else {
+    q.u = q.v = q.r = q.wi0 = q.wi1 = q.wi2 = q.wo0 = q.wo1 = q.wo2 = 0.0f;
+    q.mat = -1;
+  }
+  return q;
+}
+
+// Named barrier ID over the 128 threads of one warpgroup, OR-reducing `pred`.
+template <int ID>
+__device__ __forceinline__ bool bar_or(bool pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, 128, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)pred), "n"(ID)
+      : "memory");
+  return r != 0;
+}
+// Warpgroup wg synchronises on barrier 1 + wg (barrier 0 is __syncthreads).
+__device__ __forceinline__ bool wg_sync_or(int wg, bool pred) {
+  switch (wg) {
+    case 0: return bar_or<1>(pred);
+    case 1: return bar_or<2>(pred);
+    case 2: return bar_or<3>(pred);
+    default: return bar_or<4>(pred);
+  }
+}
+
+template <bool F16, int WG, bool MULTI>
+__global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bar_w = reinterpret_cast<uint64_t *>(smem);
-  uint64_t *bar_mma = bar_w + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_w + 2);
+  uint64_t *bar_mma = bar_w + 1;                         // one per warpgroup
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_w + 1 + WG);
   const BlobLayout L = blob_layout(a.n_mat, a.k1);
   uint8_t *wts = smem + 1024;
-  uint8_t *atile = wts + ((L.total + 1023u) & ~1023u);
   const int tid = threadIdx.x;
+  const int wg = tid >> 7;              // warpgroup: its own tile pipeline
+  const int row = tid & (kTile - 1);    // tile row owned by this thread
   const int warp = tid >> 5;
+  uint64_t *my_bar = bar_mma + wg;
 
   if (tid == 0) {
     tc::mbar_init(bar_w, 1);
-    tc::mbar_init(bar_mma, 1);
+    for (int g = 0; g < WG; ++g) tc::mbar_init(bar_mma + g, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kColsPerTile * WG);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tmem = *tmem_slot + kColsPerTile * (uint32_t)wg;   // this warpgroup's D column 0, lane 0
+  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;          // this warp's lane quadrant
+  const uint32_t t_d = tmem + lane, t_a = tmem + lane + kColA;
 
   if (tid == 0) {
     tc::mbar_arrive_expect_tx(bar_w, L.total);
     tc::bulk_g2s(wts, a.blob, L.total, bar_w);
   }
-  bool ok = tc::mbar_wait(bar_w, 0, kWaitCycles);
-  const float *b2 = reinterpret_cast<const float *>(wts + L.b2);
-  const float *b3 = reinterpret_cast<const float *>(wts + L.b3);
-  const float *b4 = reinterpret_cast<const float *>(wts + L.b4);
+  // first tile's inputs travel while the weights land
+  const int64_t stride = (int64_t)gridDim.x * WG;
+  int64_t tile = (int64_t)blockIdx.x * WG + wg;
+  TileView view = tile_view<MULTI>(a, tile);
+  Point pt = load_point(view, view.first + row);
+  bool ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
   const float *alb = reinterpret_cast<const float *>(wts + L.alb);
 
-  const uint32_t a_addr = tc::smem_addr(atile);
   const uint32_t w1_addr = tc::smem_addr(wts + L.w1), w2_addr = tc::smem_addr(wts + L.w2);
   const uint32_t w3_addr = tc::smem_addr(wts + L.w3), w4_addr = tc::smem_addr(wts + L.w4);
   const uint32_t id64 = F16 ? tc::idesc_f16(128, 64) : tc::idesc_bf16(128, 64);
   const uint32_t id16 = F16 ? tc::idesc_f16(128, 16) : tc::idesc_bf16(128, 16);
+  const uint32_t one16 = F16 ? 0x3C00u : 0x3F80u;   // 1.0 in the operand type
   uint32_t phase = 0;
 
-  if (__syncthreads_or(!ok)) goto teardown;
-
-  for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-    const int64_t p = tile * kTile + tid;
-    const bool live = p < a.n;
-    int mat = -1;
-    // ---- encode this thread's point into row `tid` of the layer-1 A tile
+  for (; tile < a.n_tiles; tile += stride) {
+    // this tile's outputs (the view moves on to the next tile at layer 1)
+    float *const out_rgb = view.rgb;
+    float *const out_comps = view.comps;
+    const int64_t p = view.first + row;
+    const int64_t p_end = view.n;
+    int mat = pt.mat;
+    if (mat >= a.n_mat) {
+      atomicOr(a.status, kStatusBadMaterial);
+      mat = -2;
+    }
+    // ---- encode this thread's point into its row of the layer-1 A operand
     {
-      float q[40];
+      uint32_t w[16];
+      if (mat >= 0) {
+        octave_words<F16>(pt.u, w);
+        octave_words<F16>(pt.v, w + 8);
+      } else {
 #pragma unroll
-      for (int i = 0; i < 40; ++i) q[i] = 0.0f;
-      if (live) {
-        mat = a.material[p];
-        if (mat >= a.n_mat) {
-          atomicOr(a.status, kStatusBadMaterial);
-          mat = -2;
-        } else {
-          octave_sincos(a.u[p], q);
-          octave_sincos(a.v[p], q + 16);
-          q[32] = (__logf(fmaxf(a.radius[p], kRFloor)) - kLogRC0) * kLogRInvC1;
-          q[33] = a.wi[3 * p];
-          q[34] = a.wi[3 * p + 1];
-          q[35] = a.wi[3 * p + 2];
-          q[36] = a.wo[3 * p];
-          q[37] = a.wo[3 * p + 1];
-          q[38] = a.wo[3 * p + 2];
-          q[39] = mat == 0 ? 1.0f : 0.0f;
-        }
+        for (int k = 0; k < 16; ++k) w[k] = 0u;
       }
-#pragma unroll
-      for (int c = 0; c < 5; ++c) store_row_chunk<F16>(atile, tid, c, a.k1, q + 8 * c);
-      for (int c = 5; c < a.k1 / 8; ++c) {
-        float f[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] = (8 * c + e == kQueryFeat + mat) ? 1.0f : 0.0f;
-        store_row_chunk<F16>(atile, tid, c, a.k1, f);
+      tc::tmem_st8(t_a, w);                          // features 0..15 (u)
+      tc::tmem_st8(t_a + 8, w + 8);                  // features 16..31 (v)
+      if (mat >= 0) {
+        const float l = (__logf(fmaxf(pt.r, kRFloor)) - kLogRC0) * kLogRInvC1;
+        w[0] = tc::pack2<F16>(l, pt.wi0);
+        w[1] = tc::pack2<F16>(pt.wi1, pt.wi2);
+        w[2] = tc::pack2<F16>(pt.wo0, pt.wo1);
+        w[3] = tc::pack2<F16>(pt.wo2, mat == 0 ? 1.0f : 0.0f);
+      } else {
+        w[0] = w[1] = w[2] = w[3] = 0u;
       }
+      // features 40.. are the one-hot material columns (39 is in w[3])
+      const int hot = kQueryFeat + mat;
+#pragma unroll
+      for (int k = 4; k < 8; ++k) w[k] = (hot == 2 * (16 + k) ? one16 : 0u) | (hot == 2 * (16 + k) + 1 ? one16 << 16 : 0u);
+      tc::tmem_st8(t_a + 16, w);                     // features 32..47
+      for (int c = 3; c < a.k1 / 16; ++c) {          // features 48.. (wider one-hot)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          w[k] = (hot == 16 * c + 2 * k ? one16 : 0u) | (hot == 16 * c + 2 * k + 1 ? one16 << 16 : 0u);
+        tc::tmem_st8(t_a + 8 * c, w);
+      }
+      tc::tmem_st_wait();
     }
     // ---- four layers
 #pragma unroll 1
     for (int layer = 0; layer < 4; ++layer) {
-      tc::fence_proxy_async_smem();
       tc::tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
+      if (wg_sync_or(wg, !ok)) goto teardown;
+      if (row == 0) {
         tc::tc_fence_after();
-        const int K = layer == 0 ? a.k1 : 64;
+        const int K = layer == 0 ? a.k1 : kKH;
         const uint32_t w_addr = layer == 0 ? w1_addr : layer == 1 ? w2_addr : layer == 2 ? w3_addr : w4_addr;
         const uint32_t sbo = (uint32_t)K * 16u;
         for (int kk = 0; kk < K / 16; ++kk) {
-          const uint64_t ad = tc::smem_desc(a_addr + kk * 256u, 128u, sbo);
           const uint64_t bd = tc::smem_desc(w_addr + kk * 256u, 128u, sbo);
-          tc::mma_bf16(tmem, ad, bd, layer == 3 ? id16 : id64, kk > 0 ? 1u : 0u);
+          tc::mma_f16_ts(tmem, tmem + kColA + 8u * kk, bd, layer == 3 ? id16 : id64, kk > 0 ? 1u : 0u);
         }
-        tc::mma_commit(bar_mma);
+        tc::mma_commit(my_bar);
       }
-      ok = tc::mbar_wait(bar_mma, phase, kWaitCycles);
+      if (layer == 0) {   // next tile's inputs, in flight during this tile's layers
+        view = tile_view<MULTI>(a, tile + stride);
+        pt = load_point(view, view.first + row);
+      }
+      // one warp sleeps on the barrier; the other three wait at the named
+      // barrier, which costs them no issue slots
+      if (row < 32) ok = tc::mbar_wait_sleep(my_bar, phase, kWaitCycles);
       phase ^= 1u;
-      if (__syncthreads_or(!ok)) goto teardown;
+      tc::tc_fence_before();
+      ok = !wg_sync_or(wg, !ok);
       tc::tc_fence_after();
       if (layer < 3) {
-        float acc[64];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tc::tmem_ld16(tmem_row + 16 * c, acc + 16 * c);
-        tc::tmem_ld_wait();
-        const float *bias = layer == 1 ? b2 : b3;
+        for (int half = 0; half < 2; ++half) {
+          float acc[32];
+          tc::tmem_ld16(t_d + 32 * half, acc);
+          tc::tmem_ld16(t_d + 32 * half + 16, acc + 16);
+          tc::tmem_ld_wait();
+          uint32_t w[16];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint32_t w[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int col = 8 * c + 2 * e;
-            float lo = acc[col], hi = acc[col + 1];
-            if (layer > 0) {
-              lo += bias[col];
-              hi += bias[col + 1];
-            }
-            w[e] = tc::pack2_relu<F16>(lo, hi);
-          }
-          tc::st_shared_v4(atile + tc::core_offset(tid, 8 * c, 64), w[0], w[1], w[2], w[3]);
+          for (int k = 0; k < 16; ++k) w[k] = tc::pack2_relu<F16>(acc[2 * k], acc[2 * k + 1]);
+          tc::tmem_st8(t_a + 16 * half, w);
+          tc::tmem_st8(t_a + 16 * half + 8, w + 8);
         }
+        // constant-one column (bias of layers 2-4) and zero padding, K = 64..79
+        uint32_t w[8] = {one16, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        tc::tmem_st8(t_a + 32, w);
+        tc::tmem_st_wait();
       } else {
         float y[16];
-        tc::tmem_ld16(tmem_row, y);
+        tc::tmem_ld16(t_d, y);
         tc::tmem_ld_wait();
-        if (live) {
+        if (p < p_end) {
           float c4[4];
           if (mat < 0) {
             c4[0] = c4[1] = c4[2] = c4[3] = __int_as_float(0x7FC00000);
           } else {
-            c4[0] = fmaxf(0.0f, y[0] + b4[0]);
-            c4[1] = fmaxf(0.0f, y[1] + b4[1]);
-            c4[2] = fmaxf(0.0f, expm1f(y[2] + b4[2]) * (1.0f / kSpecK));
-            c4[3] = fmaxf(0.0f, expm1f(y[3] + b4[3]) * (1.0f / kSpecK));
+            c4[0] = fmaxf(0.0f, y[0]);
+            c4[1] = fmaxf(0.0f, y[1]);
+            c4[2] = fmaxf(0.0f, expm1f(y[2]) * (1.0f / kSpecK));
+            c4[3] = fmaxf(0.0f, expm1f(y[3]) * (1.0f / kSpecK));
           }
-          if (a.comps) reinterpret_cast<float4 *>(a.comps)[p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
-          const float *al = alb + (mat < 0 ? 0 : mat) * 12;
-#pragma unroll
-          for (int ch = 0; ch < 3; ++ch)
-            a.rgb[3 * p + ch] = al[ch] * c4[0] + al[3 + ch] * c4[1] + al[6 + ch] * c4[2] + al[9 + ch] * c4[3];
+          if (out_comps) reinterpret_cast<float4 *>(out_comps)[p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+          const float4 *al = reinterpret_cast<const float4 *>(alb + (mat < 0 ? 0 : mat) * 12);
+          const float4 k0 = al[0], k1 = al[1], k2 = al[2];   // kd_warp, kd_weft, ks_warp, ks_weft (RGB each)
+          out_rgb[3 * p + 0] = k0.x * c4[0] + k0.w * c4[1] + k1.z * c4[2] + k2.y * c4[3];
+          out_rgb[3 * p + 1] = k0.y * c4[0] + k1.x * c4[1] + k1.w * c4[2] + k2.z * c4[3];
+          out_rgb[3 * p + 2] = k0.z * c4[0] + k1.y * c4[1] + k2.x * c4[2] + k2.w * c4[3];
         }
       }
     }
@@ -298,19 +402,19 @@ teardown:
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     // let any copy or product still in flight land before the memory goes away
     tc::mbar_wait(bar_w, 0, kWaitCycles);
+    tc::mbar_wait(my_bar, phase ^ 1u, kWaitCycles);   // the phase whose wait expired (passes if none issued)
   }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, kTmemCols);
+    tc::tmem_dealloc(*tmem_slot, kColsPerTile * WG);
   }
 }
 
 size_t tc_smem_bytes(int n_mat, int k1) {
   const BlobLayout L = blob_layout(n_mat, k1);
-  const int kmax = k1 > 64 ? k1 : 64;
-  return 1024 /* alignment slack */ + 1024 /* barriers */ + ((L.total + 1023u) & ~1023u) + (size_t)kTile * kmax * 2;
+  return 1024 /* alignment slack */ + 1024 /* barriers */ + align1k(L.total);
 }
 
 // ---- self-test: one 128 x n x k product through the same layout and path
@@ -367,6 +471,109 @@ __global__ void __launch_bounds__(128, 1) selftest_kernel(const float *__restric
   }
 }
 
+// ---- self-test with the A operand in tensor memory: row i of A in lane i,
+// two bf16 per 32-bit column (K along the columns), B in shared memory.
+__global__ void __launch_bounds__(128, 1) selftest_ts_kernel(const float *__restrict__ A, const float *__restrict__ B,
+                                                             int n, int k, float *__restrict__ D, int *status) {
+  __shared__ __align__(1024) uint8_t sb[64 * 64 * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < n * k; e += 128) {
+    const int r = e / k, c = e % k;
+    put_bf16(sb, tc::core_offset(r, c, k), B[e]);
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&slot, 256);
+  tc::fence_proxy_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  uint32_t w[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w[j] = (2 * j < k) ? tc::pack_bf16(A[tid * k + 2 * j], A[tid * k + 2 * j + 1]) : 0u;
+  for (int c = 0; c < k / 16; ++c) tc::tmem_st8(tmem + lane_base + 64 + 8 * c, w + 8 * c);
+  tc::tmem_st_wait();
+  tc::tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc::tc_fence_after();
+    for (int kk = 0; kk < k / 16; ++kk) {
+      const uint64_t bd = tc::smem_desc(tc::smem_addr(sb) + kk * 256u, 128u, (uint32_t)k * 16u);
+      tc::mma_f16_ts(tmem, tmem + 64 + 8 * kk, bd, tc::idesc_bf16(128, n), kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&bar);
+  }
+  const bool ok = tc::mbar_wait(&bar, 0, kWaitCycles);
+  if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
+  tc::tc_fence_after();
+  if (__syncthreads_and(ok)) {
+    for (int c = 0; c < n; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_base + c, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int e = 0; e < 16; ++e) D[tid * n + c + e] = v[e];
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 256);
+  }
+}
+
+template <bool F16, int WG, bool MULTI>
+const void *kernel_ptr() {
+  return reinterpret_cast<const void *>(decoder_tc_kernel<F16, WG, MULTI>);
+}
+
+// Supported tile pipelines per CTA: 1, 2 or 4 (128 tensor-memory columns each).
+int norm_wg(int wg) { return wg == 2 || wg == 4 ? wg : 1; }
+
+template <bool MULTI>
+const void *pick_kernel_m(bool f16, int wg) {
+  if (f16)
+    return wg == 1 ? kernel_ptr<true, 1, MULTI>() : wg == 2 ? kernel_ptr<true, 2, MULTI>()
+                                                            : kernel_ptr<true, 4, MULTI>();
+  return wg == 1 ? kernel_ptr<false, 1, MULTI>() : wg == 2 ? kernel_ptr<false, 2, MULTI>()
+                                                           : kernel_ptr<false, 4, MULTI>();
+}
+const void *pick_kernel(bool f16, int wg, bool multi = false) {
+  return multi ? pick_kernel_m<true>(f16, wg) : pick_kernel_m<false>(f16, wg);
+}
+
+// CTAs of the decoder that fit on one SM, counted from the kernel's
+// registers (allocated per warp in units of 8), its shared memory (plus the
+// 1 KB the driver reserves per CTA) and the 512 tensor-memory columns.
+int tc_resident_ctas(const void *fn, size_t smem, int wg) {
+  int dev = 0, smem_sm = 0, regs_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaFuncAttributes fa;
+  int regs = 128;
+  size_t static_smem = 0;
+  if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) {
+    regs = fa.numRegs;
+    static_smem = fa.sharedSizeBytes;
+  }
+  cudaGetLastError();
+  const int by_smem = (int)(smem_sm / (smem + static_smem + 1024));
+  const int by_regs = regs_sm / (((regs + 7) & ~7) * kTile * wg);
+  const int by_tmem = 512 / (int)(kColsPerTile * wg);
+  int occ = by_smem < by_regs ? by_smem : by_regs;
+  if (occ > by_tmem) occ = by_tmem;
+  return occ < 1 ? 1 : occ;
+}
+
 }  // namespace
 
 int tc_k1(int n_mat) {
@@ -378,7 +585,6 @@ size_t tc_blob_bytes(int n_mat) { return blob_layout(n_mat, tc_k1(n_mat) > 0 ? t
 
 cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMaterial *mats, int n_mat, int precision,
                            void *blob, cudaStream_t s) {
-  (void)precision;
   const int k1 = tc_k1(n_mat);
   if (k1 < 0) return cudaErrorInvalidValue;
   const size_t smem = (size_t)n_mat * kHidden * sizeof(float);
@@ -389,22 +595,44 @@ cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMate
   return cudaGetLastError();
 }
 
-cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,
-                              float *comps, int *status, int sm_count, int ctas_per_sm, cudaStream_t s) {
+int tc_default_ctas_per_sm(int n_mat, int precision) {
+  const int k1 = tc_k1(n_mat);
+  if (k1 < 0) return 1;
+  const int wg = 1;
+  const void *fn = pick_kernel(precision == FABRIC_PREC_FP16, wg, false);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return tc_resident_ctas(fn, tc_smem_bytes(n_mat, k1), wg);
+}
+
+static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count, int ctas_per_sm, int warpgroups,
+                             cudaStream_t s) {
   const bool f16 = precision == FABRIC_PREC_FP16;
+  const int wg = norm_wg(warpgroups);
+  const size_t smem = tc_smem_bytes(a.n_mat, a.k1);
+  const void *fn = pick_kernel(f16, wg, multi);
+  static bool attr_set[2][5][2] = {};
+  if (!attr_set[f16][wg][multi]) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set[f16][wg][multi] = true;
+  }
+  const int resident = tc_resident_ctas(fn, smem, wg);
+  int per_sm = ctas_per_sm > 0 ? ctas_per_sm : resident;
+  if (per_sm > resident) per_sm = resident;
+  int64_t grid = (int64_t)sm_count * per_sm;
+  const int64_t need = (a.n_tiles + wg - 1) / wg;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  void *args[] = {&a};
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kTile * wg), args, smem, s);
+}
+
+cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,
+                              float *comps, int *status, int sm_count, int ctas_per_sm, int warpgroups,
+                              cudaStream_t s) {
   const int k1 = tc_k1(n_mat);
   if (k1 < 0) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(n_mat, k1);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(decoder_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(decoder_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  TcArgs a;
+  TcArgs a = {};
   a.u = g.u;
   a.v = g.v;
   a.radius = g.radius;
@@ -419,27 +647,34 @@ cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_m
   a.rgb = rgb;
   a.comps = comps;
   a.status = status;
-  int per_sm = ctas_per_sm;
-  if (per_sm <= 0) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f16 ? decoder_tc_kernel<true> : decoder_tc_kernel<false>,
-                                                  kTile, smem);
-    per_sm = occ < 1 ? 1 : occ;
-  }
-  if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;
-  int64_t grid = (int64_t)sm_count * per_sm;
-  if (grid > a.n_tiles) grid = a.n_tiles;
-  if (grid < 1) grid = 1;
-  if (f16)
-    decoder_tc_kernel<true><<<(unsigned)grid, kTile, smem, s>>>(a);
-  else
-    decoder_tc_kernel<false><<<(unsigned)grid, kTile, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_tc(a, false, precision, sm_count, ctas_per_sm, warpgroups, s);
 }
 
-cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, float *d, int *status,
+int64_t tc_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+
+cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_tile0, int n_segs, int64_t n_tiles,
+                                       const void *blob, int n_mat, int precision, int *status, int sm_count,
+                                       int ctas_per_sm, int warpgroups, cudaStream_t s) {
+  const int k1 = tc_k1(n_mat);
+  if (k1 < 0) return cudaErrorInvalidValue;
+  TcArgs a = {};
+  a.n_tiles = n_tiles;
+  a.blob = static_cast<const uint8_t *>(blob);
+  a.n_mat = n_mat;
+  a.k1 = k1;
+  a.status = status;
+  a.segs = segs;
+  a.seg_tile0 = seg_tile0;
+  a.n_segs = n_segs;
+  return launch_tc(a, true, precision, sm_count, ctas_per_sm, warpgroups, s);
+}
+
+cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, int a_in_tmem, float *d, int *status,
                                 cudaStream_t s) {
-  selftest_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);
+  if (a_in_tmem)
+    selftest_ts_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);
+  else
+    selftest_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);
   return cudaGetLastError();
 }
 

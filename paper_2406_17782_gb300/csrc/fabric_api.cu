@@ -286,6 +286,23 @@ const char *fabric_last_error(const fabric_ctx *ctx) { return ctx ? ctx->last_er
 
 int fabric_sm_count(const fabric_ctx *ctx) { return ctx ? ctx->sm_count : 0; }
 
+fabric_status fabric_set_launch_config(fabric_ctx *ctx, int decoder_ctas_per_sm, int decoder_warpgroups,
+                                       int reference_lanes) {
+  if (!ctx) return FABRIC_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  const bool lanes_ok = reference_lanes == 0 || reference_lanes == 1 || reference_lanes == 2 ||
+                        reference_lanes == 4 || reference_lanes == 8 || reference_lanes == 16 ||
+                        reference_lanes == 32;
+  if (decoder_ctas_per_sm < 0 || decoder_ctas_per_sm > 8 || decoder_warpgroups < 0 || decoder_warpgroups > 4 ||
+      !lanes_ok)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG,
+                "decoder CTAs per SM in 0..8, warpgroups in 0..4, reference lanes in {0,1,2,4,8,16,32}");
+  ctx->tc_ctas_per_sm = decoder_ctas_per_sm;
+  ctx->tc_warpgroups = decoder_warpgroups;
+  ctx->ref_lanes = reference_lanes;
+  return FABRIC_OK;
+}
+
 fabric_status fabric_sync_status(fabric_ctx *ctx, void *stream) {
   FAB_CHECK_CTX(ctx);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -468,7 +485,8 @@ fabric_status fabric_shade_reference(fabric_ctx *ctx, const fabric_gbuffer *g, i
   if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
   const int spp = spp_x * spp_y;
   // lanes per point: a whole warp for large sample counts, fewer otherwise
-  const int lanes = spp >= 256 ? 32 : spp >= 64 ? 16 : spp >= 16 ? 8 : spp >= 4 ? 4 : 1;
+  const int lanes = ctx->ref_lanes > 0 ? ctx->ref_lanes
+                    : spp >= 256 ? 32 : spp >= 64 ? 16 : spp >= 16 ? 8 : spp >= 4 ? 4 : 1;
   FAB_CUDA(ctx,
            launch_reference(*g, ctx->d_mat, ctx->n_mat, spp_x, spp_y, seed, rgb_dev, comps_dev, ctx->d_status,
                             lanes, ctx->sm_count, static_cast<cudaStream_t>(stream)),
@@ -521,7 +539,7 @@ fabric_status fabric_shade_neural_prepared(fabric_ctx *ctx, const fabric_gbuffer
   }
   FAB_CUDA(ctx,
            launch_decoder_tc(*g, ctx->d_blob, ctx->n_mat, (int)prec, rgb_dev, comps_dev, ctx->d_status, ctx->sm_count,
-                             0, s),
+                             ctx->tc_ctas_per_sm, ctx->tc_warpgroups, s),
            "tensor-core decoder launch");
   return FABRIC_OK;
 }
@@ -543,21 +561,29 @@ fabric_status fabric_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g, cons
 }
 
 fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
-                                  float *d_dev, void *stream) {
+                                  int a_in_tmem, float *d_dev, void *stream) {
   FAB_CHECK_CTX(ctx);
   if (!a_dev || !b_dev || !d_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "NULL pointer");
   if (!(k == 16 || k == 32 || k == 48 || k == 64) || !(n == 16 || n == 32 || n == 64))
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "k must be 16/32/48/64 and n 16/32/64");
-  FAB_CUDA(ctx, launch_selftest_mma(a_dev, b_dev, n, k, d_dev, ctx->d_status, static_cast<cudaStream_t>(stream)),
+  FAB_CUDA(ctx,
+           launch_selftest_mma(a_dev, b_dev, n, k, a_in_tmem ? 1 : 0, d_dev, ctx->d_status,
+                               static_cast<cudaStream_t>(stream)),
            "selftest launch");
   return FABRIC_OK;
 }
 
 fabric_status fabric_error_stats(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int64_t n,
-                                 double *out_dev, void *stream) {
+                                 const float *weights_dev, int group, int weight_stride, double *out_dev,
+                                 void *stream) {
   FAB_CHECK_CTX(ctx);
   if (!a_dev || !b_dev || !out_dev || n < 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "bad arguments");
-  FAB_CUDA(ctx, launch_error_stats(a_dev, b_dev, n, out_dev, ctx->d_err_work, static_cast<cudaStream_t>(stream)),
+  if (weights_dev && (group < 1 || weight_stride < 1))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "group and weight_stride must be >= 1 with weights");
+  FAB_CUDA(ctx,
+           launch_error_stats(a_dev, b_dev, n, weights_dev, group < 1 ? 1 : group,
+                              weight_stride < 1 ? 1 : weight_stride, out_dev, ctx->d_err_work,
+                              static_cast<cudaStream_t>(stream)),
            "error stats launch");
   return FABRIC_OK;
 }

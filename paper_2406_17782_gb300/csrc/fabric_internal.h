@@ -67,10 +67,24 @@ struct alignas(16) DevMaterial {
   float2 theta[kMaxPatternDim * kMaxPatternDim];
 };
 
-// Caller-visible status and messages.
-struct Ctx;
+// One segment of a batched draw, as the kernel reads it.
+struct SegDesc {
+  const float *u, *v, *radius, *wi, *wo;
+  const uint16_t *material;
+  float *rgb, *comps;
+  int64_t n;
+};
 
 }  // namespace fab
+
+struct fabric_plan {
+  int device = 0;
+  int n_segs = 0;
+  int64_t n_tiles = 0;
+  int64_t n_points = 0;
+  fab::SegDesc *d_segs = nullptr;
+  int64_t *d_tile0 = nullptr;   // [n_segs + 1] first tile of each segment
+};
 
 struct fabric_ctx {
   int device = 0;
@@ -106,6 +120,10 @@ struct fabric_ctx {
   const float *prepared_latents = nullptr;
   uint64_t prepared_version = 0;
   uint64_t version = 1;            // bumped when materials or parameters change
+  // launch configuration (0 = automatic)
+  int tc_ctas_per_sm = 0;
+  int tc_warpgroups = 0;
+  int ref_lanes = 0;
 };
 
 namespace fab {
@@ -129,9 +147,15 @@ size_t tc_blob_bytes(int n_mat);
 int tc_k1(int n_mat);
 cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMaterial *mats, int n_mat,
                            int precision, void *blob, cudaStream_t s);
+int tc_default_ctas_per_sm(int n_mat, int precision);
 cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,
-                              float *comps, int *status, int sm_count, int ctas_per_sm, cudaStream_t s);
-cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, float *d, int *status,
+                              float *comps, int *status, int sm_count, int ctas_per_sm, int warpgroups,
+                              cudaStream_t s);
+int64_t tc_tiles(int64_t n);
+cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_tile0, int n_segs, int64_t n_tiles,
+                                       const void *blob, int n_mat, int precision, int *status, int sm_count,
+                                       int ctas_per_sm, int warpgroups, cudaStream_t s);
+cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, int a_in_tmem, float *d, int *status,
                                 cudaStream_t s);
 cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *z, cudaStream_t s);
 cudaError_t launch_encoder_feats(const float *feats, int n, const float *enc, float *z, float *acts,
@@ -148,8 +172,8 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
 size_t decoder_backward_work_bytes(int64_t n, int sm_count);
 cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, int64_t step,
                         cudaStream_t s);
-cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, double *out, void *work,
-                               cudaStream_t s);
+cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
+                               double *out, void *work, cudaStream_t s);
 size_t error_stats_work_bytes(int64_t n);
 
 }  // namespace fab

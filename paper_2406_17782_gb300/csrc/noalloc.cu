@@ -54,7 +54,8 @@ extern "C" fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabr
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_tc_pack(ctx->d_dec, latents_dev, ctx->d_mat, ctx->n_mat, (int)prec, blob, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
-  e = launch_decoder_tc(*g, blob, ctx->n_mat, (int)prec, rgb_dev, comps_dev, ctx->d_status, ctx->sm_count, 0, s);
+  e = launch_decoder_tc(*g, blob, ctx->n_mat, (int)prec, rgb_dev, comps_dev, ctx->d_status, ctx->sm_count,
+                        ctx->tc_ctas_per_sm, ctx->tc_warpgroups, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core decoder launch");
   return FABRIC_OK;
 }

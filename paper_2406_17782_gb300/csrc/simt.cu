@@ -477,13 +477,16 @@ constexpr int kErrThreads = 256;
 
 __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *__restrict__ a,
                                                                   const float *__restrict__ b, int64_t n,
-                                                                  double *__restrict__ part) {
+                                                                  const float *__restrict__ w, int group,
+                                                                  int w_stride, double *__restrict__ part) {
   __shared__ double s0[kErrThreads], s1[kErrThreads], s2[kErrThreads];
   double e2 = 0.0, b2 = 0.0, mx = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kErrThreads + threadIdx.x; i < n; i += (int64_t)kErrBlocks * kErrThreads) {
-    const double d = (double)a[i] - (double)b[i];
+    const double wi = w ? (double)w[(i / group) * w_stride] : 1.0;
+    const double d = ((double)a[i] - (double)b[i]) * wi;
+    const double bb = (double)b[i] * wi;
     e2 += d * d;
-    b2 += (double)b[i] * (double)b[i];
+    b2 += bb * bb;
     mx = fmax(mx, fabs(d));
   }
   s0[threadIdx.x] = e2;
@@ -670,10 +673,10 @@ cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, in
 
 size_t error_stats_work_bytes(int64_t) { return (size_t)kErrBlocks * 3 * sizeof(double); }
 
-cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, double *out, void *work,
-                               cudaStream_t s) {
+cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
+                               double *out, void *work, cudaStream_t s) {
   double *part = static_cast<double *>(work);
-  err_partial_kernel<<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, part);
+  err_partial_kernel<<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
   err_final_kernel<<<1, 32, 0, s>>>(part, out);
   return cudaGetLastError();
 }

@@ -52,16 +52,17 @@ def setup(fab):
 def emulate(prec, dec_flat, z, mats, g):
     """The tensor-core path's operand rounding: rounded query features,
     rounded weights, latent folded into a rounded per-material bias column,
-    FP32 bias adds, rounded activations, FP32 accumulation (FP64 here)."""
+    biases of layers 2-4 rounded (they ride in a constant-one input column),
+    rounded activations, FP32 accumulation (FP64 here)."""
     r = ROUND[prec]
     P = M.unpack(dec_flat, M.DEC_SHAPES)
     q = r(M.query_features(g["u"], g["v"], g["radius"], g["wi"], g["wo"]))
     mat = np.asarray(g["material"], np.int64)
     fold = P["b1"][None, :] + z.astype(np.float64) @ P["W1"][:, :32].T
     h = np.maximum(q @ r(P["W1"][:, 32:]).T + r(fold)[mat], 0)
-    h = np.maximum(r(h) @ r(P["W2"]).T + P["b2"], 0)
-    h = np.maximum(r(h) @ r(P["W3"]).T + P["b3"], 0)
-    y = r(h) @ r(P["W4"]).T + P["b4"]
+    h = np.maximum(r(h) @ r(P["W2"]).T + r(P["b2"]), 0)
+    h = np.maximum(r(h) @ r(P["W3"]).T + r(P["b3"]), 0)
+    y = r(h) @ r(P["W4"]).T + r(P["b4"])
     comps = M.head_to_components(y)
     return comps, M.recombine(comps, mats, g["material"])
 
@@ -83,12 +84,13 @@ def fp32_forward_bound(P, x):
     return dx
 
 
+@pytest.mark.parametrize("a_in_tmem", [False, True])
 @pytest.mark.parametrize("n,k", [(64, 16), (64, 48), (16, 64), (32, 32), (64, 64)])
-def test_tensor_core_product_layout(fab, n, k):
+def test_tensor_core_product_layout(fab, n, k, a_in_tmem):
     rng = np.random.default_rng(n * 100 + k)
     a = rng.standard_normal((128, k)).astype(np.float32)
     b = rng.standard_normal((n, k)).astype(np.float32)
-    d = fab.selftest_mma(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    d = fab.selftest_mma(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), a_in_tmem).cpu().numpy()
     fab.sync_status()
     want = M.round_bf16(a) @ M.round_bf16(b).T
     np.testing.assert_allclose(d, want, rtol=1e-5, atol=1e-5)
@@ -211,3 +213,12 @@ def test_neural_error_stats_fp64_reduction(fab, setup):
     np.testing.assert_allclose(out[0], (d * d).sum(), rtol=1e-12)
     np.testing.assert_allclose(out[1], (b.astype(np.float64) ** 2).sum(), rtol=1e-12)
     assert out[2] == np.abs(d).max()
+    # one weight per RGB triple, read with a stride (the z of [n][3] directions)
+    n = 3 * 100_001
+    dirs = rng.uniform(0, 1, (n // 3, 3)).astype(np.float32)
+    td = torch.from_numpy(dirs).cuda()
+    out = fab.error_stats(torch.from_numpy(a[:n]).cuda(), torch.from_numpy(b[:n]).cuda(), weights=td[:, 2],
+                          group=3, weight_stride=3).cpu().numpy()
+    w = np.repeat(dirs[:, 2].astype(np.float64), 3)
+    np.testing.assert_allclose(out[0], ((d[:n] * w) ** 2).sum(), rtol=1e-12)
+    np.testing.assert_allclose(out[1], ((b[:n].astype(np.float64) * w) ** 2).sum(), rtol=1e-12)
