@@ -309,3 +309,47 @@ def round_e4m3(x) -> np.ndarray:
     r = np.round(a / q) * q             # np.round is ties-to-even
     r = np.minimum(r, E4M3_MAX)
     return np.sign(x) * r
+
+
+def round_fp16(x) -> np.ndarray:
+    """Round to IEEE binary16 (ties to even) via FP32, returned as FP64."""
+    return np.asarray(x, np.float32).astype(np.float16).astype(np.float64)
+
+
+def e4m3_scale_exponent(w) -> int:
+    """Per-layer power-of-two weight scale of the E4M3 operand path: with
+    amax = max |w| written as m 2^E (m in [0.5, 1), frexp of the FP32 value),
+    the weights are stored as E4M3(w 2^(8 - E)), so the largest lands in
+    [128, 256) below the E4M3 maximum of 448 and no weight is rescaled
+    inexactly.  Returns 8 - E (the scale is 2^(8 - E))."""
+    amax = np.float32(np.max(np.abs(np.asarray(w, np.float32))))
+    _, e = np.frexp(amax)
+    return 8 - int(e)
+
+
+def shade_neural_e4m3(dec: dict, z: np.ndarray, materials, gbuf: dict,
+                      r16=round_fp16, r8=round_e4m3):
+    """Operand-rounding emulation of the E4M3 tensor-core decoder.
+
+    Layer 1 keeps 16-bit operands (r16): its weight block carries the latent
+    folded into a per-material bias column (W1 z_m + b1), which E4M3 would
+    cut to 3 mantissa bits.  Layers 2-4 take E4M3 operands (r8): the
+    activations unscaled (saturating at 448), the weights scaled by the
+    per-layer power of two of e4m3_scale_exponent; their biases and the
+    undoing of the scale are applied in FP32 to the FP32 product.  Every
+    value is rounded to FP32 before it is rounded to an operand type, as in
+    the kernel.  With r16 = r8 = identity this is the FP64 network up to
+    those FP32 roundings.  Returns (components [n, 4], rgb [n, 3])."""
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    q = r16(f32(query_features(gbuf["u"], gbuf["v"], gbuf["radius"], gbuf["wi"], gbuf["wo"])))
+    mat = np.asarray(gbuf["material"], np.int64)
+    zf = np.asarray(z, np.float64)
+    fold = dec["b1"][None, :] + zf @ dec["W1"][:, :LATENT].T            # [n_mat, 64]
+    a = q @ r16(f32(dec["W1"][:, LATENT:])).T + r16(f32(fold))[mat]
+    h = r8(np.maximum(f32(a), 0.0))
+    for wn, bn, last in (("W2", "b2", False), ("W3", "b3", False), ("W4", "b4", True)):
+        s = 2.0 ** e4m3_scale_exponent(dec[wn])
+        a = f32(f32(h @ r8(f32(dec[wn]) * s).T) / s + f32(dec[bn]))
+        h = a if last else r8(np.maximum(a, 0.0))
+    comps = head_to_components(h)
+    return comps, recombine(comps, materials, gbuf["material"])

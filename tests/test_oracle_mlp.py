@@ -216,3 +216,36 @@ def test_e4m3_rounding_matches_torch(M):
     x = x.astype(np.float32).astype(np.float64)
     want = torch.tensor(x, dtype=torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
     np.testing.assert_array_equal(M.round_e4m3(x), want)
+
+
+def test_e4m3_scale_exponent_places_amax_below_the_e4m3_maximum(M):
+    rng = np.random.default_rng(11)
+    for mag in (1e-6, 3e-3, 0.3, 1.0, 7.5, 300.0):
+        w = rng.standard_normal((64, 64)) * mag
+        e = M.e4m3_scale_exponent(w)
+        top = float(np.float32(np.abs(w).max())) * 2.0 ** e
+        assert 128.0 <= top < 256.0
+    # exact powers of two land on 128 exactly
+    assert M.e4m3_scale_exponent(np.array([[0.5, -0.25]])) == 8
+    assert float(0.5 * 2.0 ** 8) == 128.0
+
+
+def test_e4m3_emulation_reduces_to_the_network_without_rounding(M):
+    """With identity rounding the E4M3 emulation (folded latent, scaled
+    weights, FP32 bias epilogue) is the FP64 network up to FP32 rounding of
+    the intermediate values: a dropped bias, an unreverted scale or a
+    transposed operand fails this."""
+    import workloads as W
+    mats = W.frame_materials()
+    P = M.unpack(W.decoder_init(), M.DEC_SHAPES)
+    z = W.random_latents(len(mats))
+    g = W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 2048, stream="e4m3-pin"))
+    want, want_rgb = M.shade_neural(P, z, mats, g)
+    ident = lambda x: np.asarray(x, np.float64)
+    got, got_rgb = M.shade_neural_e4m3(P, z, mats, g, r16=ident, r8=ident)
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6 * np.abs(want).max())
+    np.testing.assert_allclose(got_rgb, want_rgb, rtol=1e-5, atol=1e-6 * np.abs(want_rgb).max())
+    # with E4M3 rounding the error is that of a 3-bit mantissa, not a bug's
+    q, _ = M.shade_neural_e4m3(P, z, mats, g)
+    rel = np.sqrt(((q - want) ** 2).sum() / (want ** 2).sum())
+    assert 1e-2 < rel < 0.3
