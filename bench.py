@@ -43,6 +43,9 @@ WIDTH, HEIGHT = 1920, 1080
 N_POINTS = WIDTH * HEIGHT
 FLOP_PER_POINT = 2 * (39 * 64 + 64 * 64 + 64 * 64 + 64 * 4)      # 21,888 (layer 1 with the latent folded)
 BYTES_PER_POINT = 38 + 12                                          # G-buffer record in, RGB out
+# DRAM bytes (read + write) of one FP16 decoder launch on this frame, from the
+# ncu capture summarised in profiles/decoder_tc_1080p_fp16.md (same kernel)
+TRAFFIC_FP16 = 78_853_376 + 5_593_600
 WORKLOAD = "1920x1080 G-buffer, 8 weave materials (one per 240-px band), random-init decoder"
 
 
@@ -187,6 +190,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed neural frames")
+    ap.add_argument("--no-quality", action="store_true", help="skip training and the frame-RMSE comparison")
+    ap.add_argument("--quality-queries", type=int, default=1 << 23)
+    ap.add_argument("--quality-steps", type=int, default=30000)
+    ap.add_argument("--quality-lr", type=float, default=3e-3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -282,7 +289,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "decoder_launch": launch},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_t, "unit": "TFLOP/s",
-                     "frac": tflops / peak_t, "traffic": None,
+                     "frac": tflops / peak_t, "traffic": TRAFFIC_FP16 if args.precision == "fp16" else None,
                      "note": f"fused decoder kernel, {FLOP_PER_POINT} FLOP/pt x {N_POINTS} pts per launch, "
                              f"one launch per step, peak = bf16 burst {which}"},
         "hbm_view": {"achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"],
@@ -307,6 +314,61 @@ def timed(torch, stream, fn, reps):
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1) / reps
+
+
+def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
+    """Train the decoder and encoder with the library's kernels on data from
+    the reference kernel, then measure the 1080p frame's RMSE (rendered under
+    a unit directional light) of the neural path and of the reference at
+    1-64 spp against the reference at 1024 spp, and time each of them: the
+    speed ratio at equal quality, and where the reference reaches 0.01."""
+    from paper_2406_17782_gb300 import train as T
+    tm = W.training_materials(32)
+    fab.set_params(W.decoder_init(), W.encoder_init())
+    t0 = time.time()
+    g_tr, target = T.generate_dataset(fab, tm, args.quality_queries, (64, 32), frame_share=0.5)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    t0 = time.time()
+    T.train(fab, tm, g_tr, target, args.quality_steps, 65536, args.quality_lr, log_every=1000, verbose=False)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del g_tr, target
+    spps = (1, 2, 4, 8)
+    rm = T.frame_rmse(fab, "fp16", gt_spp=(32, 32), ref_spps=spps)
+    rm8 = T.frame_rmse(fab, "fp8", gt_spp=(32, 32), ref_spps=())
+    # timings on the same frame (materials and trained latents now prepared)
+    copies = len(gbufs)
+    lat = fab.encode_params(W.frame_materials())
+    times = {}
+    for prec in ("fp16", "fp8"):
+        fab.prepare_neural(lat, prec)
+        times[prec] = timed(torch, stream, lambda k: fab.shade_neural_prepared(gbufs[k % copies], prec,
+                                                                               out_rgb=rgbs[k % copies]), 200)
+    for sp in spps:
+        fab.shade_reference(gbufs[0], sp, sp, 5, out_rgb=rgbs[0])
+        times[f"ref{sp * sp}"] = timed(torch, stream, lambda k: fab.shade_reference(gbufs[k % copies], sp, sp, 5,
+                                                                                   out_rgb=rgbs[k % copies]), 20)
+    fab.sync_status()
+    ladder = [{"spp": sp * sp, "rmse": rm[f"reference_{sp * sp}spp"]["rmse"], "ms": times[f"ref{sp * sp}"]}
+              for sp in spps]
+    neural = {"rmse": rm["neural"]["rmse"], "rel_l2": rm["neural"]["rel_l2"], "ms": times["fp16"]}
+    eq = next((r for r in ladder if r["rmse"] <= neural["rmse"]), None)
+    at01 = next((r for r in ladder if r["rmse"] <= 0.01), None)
+    return {
+        "metric": "RMSE of the 1080p frame, f_P <wi.n> per RGB channel (unit directional light), "
+                  "against the reference at 1024 spp",
+        "gt_rms": rm["gt_rms"],
+        "neural_fp16": neural,
+        "neural_fp8": {"rmse": rm8["neural"]["rmse"], "rel_l2": rm8["neural"]["rel_l2"], "ms": times["fp8"]},
+        "reference": ladder,
+        "neural_meets_0.01": neural["rmse"] <= 0.01,
+        "reference_at_0.01": at01,
+        "reference_at_neural_rmse": eq,
+        "speedup_at_equal_rmse": (eq["ms"] / neural["ms"]) if eq else None,
+        "training": {"queries": args.quality_queries, "data_spp": 2048, "steps": args.quality_steps,
+                     "batch": 65536, "lr": args.quality_lr, "data_seconds": t_data, "train_seconds": t_train},
+    }
 
 
 def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, args, stream):
@@ -340,6 +402,55 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     ms_e2e = timed(torch, stream, e2e, reps)
     out["e2e"] = {"value": N_POINTS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                   "h2d_bytes_per_step": host.nbytes(), "d2h_bytes_per_step": rgb_host.numel() * 4}
+    # batched 4K: one persistent launch over a 3840x2160 frame with materials
+    # interleaved per 16x16 tile plus 4 views x 64 ragged tiles, from a CUDA
+    # graph, per operand precision; the reference at 256 spp on the 4K view
+    segs_host, n_b = W.batched_4k()
+    segs = []
+    for sh in segs_host:
+        gseg = GBuffer.from_numpy(sh)
+        segs.append((gseg, torch.empty((gseg.n, 3), dtype=torch.float32, device="cuda"), None))
+    plan = fab.plan(segs)
+    side = torch.cuda.Stream()
+    b4k = {"points": n_b, "segments": len(segs), "launches_per_replay": 1,
+           "note": "3840x2160 tile-interleaved + 256 ragged tiles (256..65536 pts), CUDA graph replay"}
+    for prec in ("fp16", "bf16", "fp8"):
+        fab.prepare_neural(latents, prec)
+        plan.shade(prec)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.shade(prec)
+        graph.replay()
+        ms_b = timed(torch, stream, lambda k: graph.replay(), 50)
+        fab.sync_status()
+        b4k[prec] = {"ms_per_replay": ms_b, "pts_per_s": n_b / (ms_b * 1e-3)}
+        del graph
+    g4k = segs[0][0]
+    out4k = segs[0][1]
+    fab.shade_reference(g4k, 16, 16, 11, out_rgb=out4k)
+    ms_r4k = timed(torch, stream, lambda k: fab.shade_reference(g4k, 16, 16, 11, out_rgb=out4k), 3)
+    fab.sync_status()
+    b4k["reference_256spp_4k_view"] = {"points": g4k.n, "ms": ms_r4k, "pts_per_s": g4k.n / (ms_r4k * 1e-3)}
+    out["batched_4k"] = b4k
+    plan.close()
+    del segs
+    # FP8 (E4M3 layers 2-4) on the 1080p frame, and its distance to the FP16 frame
+    fab.prepare_neural(latents, "fp8")
+    ms_f8 = timed(torch, stream, lambda k: fab.shade_neural_prepared(gbufs[k % copies], "fp8",
+                                                                     out_rgb=rgbs[k % copies]), 200)
+    f8 = torch.empty((N_POINTS, 3), dtype=torch.float32, device="cuda")
+    f16 = torch.empty((N_POINTS, 3), dtype=torch.float32, device="cuda")
+    fab.shade_neural_prepared(gbufs[0], "fp8", out_rgb=f8)
+    fab.prepare_neural(latents, "fp16")
+    fab.shade_neural_prepared(gbufs[0], "fp16", out_rgb=f16)
+    st = fab.error_stats(f8, f16).cpu().numpy()
+    fab.sync_status()
+    out["fp8"] = {"ms_per_frame": ms_f8, "pts_per_s": N_POINTS / (ms_f8 * 1e-3),
+                  "rel_l2_vs_fp16_frame": math.sqrt(float(st[0]) / float(st[1])),
+                  "note": "E4M3 operands in layers 2-4 (layer 1 FP16), per-layer power-of-two weight scale"}
     # one training step, batch 65536, over 256 training materials
     tm = W.training_materials(32)
     fab.set_train_materials(tm)
@@ -356,6 +467,8 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     fab.sync_status()
     out["train"] = {"ms_per_step": ms_train, "batch": 65536, "samples_per_s": 65536 / (ms_train * 1e-3),
                     "materials": len(tm)}
+    if not args.no_quality:
+        out["quality"] = measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream)
     # the FP64 oracle on the host cores, bounded sample
     rate, cores, what = oracle_decoder_rate(16384)
     pts = int(min(2_000_000, max(4096, rate * args.cpu_seconds / 4)))

@@ -211,7 +211,10 @@ fabric_status fabric_shade_reference(fabric_ctx *ctx, const fabric_gbuffer *g, i
  * table), then C = max(0, y), S = max(0, expm1(y')/100) (inverse of Eq. 9)
  * and Eq. 8.  Outputs as for fabric_shade_reference.  FP32 runs the SIMT
  * decoder; FP16 / BF16 / FP8 run the tensor-core decoder (material table of at most
- * 89 entries).
+ * 89 entries).  FP8: layer 1 keeps FP16 operands (its weights carry the folded
+ * latent); layers 2-4 take E4M3 activations (unscaled, saturating at 448)
+ * and E4M3 weights scaled per layer by 2^(8 - E), where max |W| = m 2^E with
+ * m in [0.5, 1); the scale is undone and the bias added in FP32.
  */
 fabric_status fabric_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
                                   fabric_precision prec, float *rgb_dev, float *comps_dev, void *stream);
@@ -317,7 +320,7 @@ typedef struct fabric_plan fabric_plan;
  * fabric_plan_create checks and uploads a table of 1..1048576 segments once
  * (synchronous; the plan keeps the device pointers, not the data).
  * fabric_plan_shade then shades every segment with the prepared neural
- * state (fabric_prepare_neural, FP16 or BF16) in one persistent
+ * state (fabric_prepare_neural, FP16, BF16 or FP8) in one persistent
  * tensor-core launch over all segments' 128-point tiles: asynchronous, no
  * host-side work besides the launch, so it can be captured in a CUDA graph
  * and replayed.  Results equal per-segment fabric_shade_neural_prepared
@@ -340,8 +343,8 @@ void fabric_plan_destroy(fabric_plan *plan);
  * allocate at draw time.
  *
  * Same arguments, outputs and errors as fabric_shade_neural with
- * prec = FABRIC_PREC_FP16 or FABRIC_PREC_BF16 (anything else is
- * FABRIC_ERR_INVALID_ARG).  It uses the context's material table and
+ * prec = FABRIC_PREC_FP16, FABRIC_PREC_BF16 or FABRIC_PREC_FP8 (anything else
+ * is FABRIC_ERR_INVALID_ARG).  It uses the context's material table and
  * parameters, set up beforehand, and keeps its per-call scratch (the packed
  * decoder operands, at most 64 KiB) in one static device array that every
  * GPU loading the library holds until the process exits.  It never calls
@@ -372,6 +375,13 @@ fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabric_gbuffer 
  * Used by the tests to check the tensor-core data layouts in isolation. */
 fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
                                   int a_in_tmem, float *d_dev, void *stream);
+
+/* The same product with E4M3 operands (kind::f8f6f4), A in tensor memory
+ * (four E4M3 values per 32-bit column), B in shared memory: a, b given as
+ * FP32 and rounded to E4M3 (nearest even, saturating).  k in {32, 64},
+ * n in {16, 32, 64}. */
+fabric_status fabric_selftest_mma_e4m3(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
+                                       float *d_dev, void *stream);
 
 #ifdef __cplusplus
 }

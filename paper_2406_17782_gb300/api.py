@@ -240,6 +240,14 @@ class Fabric:
                                                  int(a_in_tmem), _ptr(d), _stream_handle(None)))
         return d
 
+    def selftest_mma_e4m3(self, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+        """128 x n x k product with E4M3 operands (A in tensor memory)."""
+        n, k = b.shape
+        d = torch.empty((128, n), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_selftest_mma_e4m3(self.h, _ptr(a.contiguous()), _ptr(b.contiguous()), n, k,
+                                                      _ptr(d), _stream_handle(None)))
+        return d
+
     # ---------------------------------------------- autograd building blocks
     def decoder_forward(self, g: GBuffer, latents, dec, stream=None):
         y = torch.empty((g.n, 4), dtype=torch.float32, device=self.device)

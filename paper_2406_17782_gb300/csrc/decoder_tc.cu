@@ -22,10 +22,16 @@
 //      converts it with ReLU (cvt.rn.relu) and stores the next A operand;
 //   4. the head's four outputs become C = max(0, y), S = max(0, expm1(y)/100)
 //      and RGB by Eq. 8; only RGB (and optionally the components) is stored.
+// Operand precisions: FP16 or BF16 throughout, or E4M3 for layers 2-4
+// (kind::f8f6f4, K = 64 in two instructions, four values per tensor-memory
+// column) with layer 1 in FP16; there the weights of layers 2-4 carry a
+// per-layer power-of-two scale, and the unscaling and their biases are one
+// FP32 FMA per value in the epilogue instead of a constant-one column.
 // While one warpgroup waits for its products the others encode and convert,
 // which keeps the tensor pipe and the ALUs busy together.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "fabric_internal.h"
 #include "tc_ptx.h"
@@ -39,20 +45,44 @@ constexpr uint32_t kColsPerTile = 128;             // D [0, 64) | A [64, 128)
 constexpr uint32_t kColA = 64;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
+// Operand precision of a kernel instance.
+constexpr int kPrBF16 = 0;   // BF16 everywhere
+constexpr int kPrF16 = 1;    // FP16 everywhere
+constexpr int kPrE4M3 = 2;   // FP16 layer 1, E4M3 layers 2-4
+
+__host__ __device__ constexpr int prec_code(int fabric_prec) {
+  return fabric_prec == FABRIC_PREC_FP16 ? kPrF16 : fabric_prec == FABRIC_PREC_FP8 ? kPrE4M3 : kPrBF16;
+}
+
+// E4M3 epilogue block (FP32): per layer l = 0..3 a 64-entry bias row (row 0
+// zero: layer 1's bias rides in its folded column; row 3 holds b4 and zeros)
+// followed by the four unscaling factors (1 for layer 1).
+constexpr int kF8Bias = 0;
+constexpr int kF8Inv = 4 * 64;
+constexpr uint32_t kF8EpiBytes = (4 * 64 + 4) * 4;
+
 // ---- packed-operand blob layout (bytes), identical in global and shared memory
 struct BlobLayout {
   int k1;
-  uint32_t w1, w2, w3, w4, alb, total;
+  uint32_t w1, w2, w3, w4, epi, alb, total;
 };
 
-__host__ __device__ inline BlobLayout blob_layout(int n_mat, int k1) {
+__host__ __device__ inline BlobLayout blob_layout(int n_mat, int k1, bool f8) {
   BlobLayout L;
   L.k1 = k1;
   L.w1 = 0;
   L.w2 = L.w1 + 64u * k1 * 2u;
-  L.w3 = L.w2 + 64u * kKH * 2u;
-  L.w4 = L.w3 + 64u * kKH * 2u;
-  L.alb = L.w4 + 16u * kKH * 2u;
+  if (f8) {
+    L.w3 = L.w2 + 64u * 64u;
+    L.w4 = L.w3 + 64u * 64u;
+    L.epi = L.w4 + 16u * 64u;
+    L.alb = L.epi + kF8EpiBytes;
+  } else {
+    L.w3 = L.w2 + 64u * kKH * 2u;
+    L.w4 = L.w3 + 64u * kKH * 2u;
+    L.epi = L.w4 + 16u * kKH * 2u;
+    L.alb = L.epi;
+  }
   L.total = L.alb + ((uint32_t)(n_mat * 12 * 4) + 15u) / 16u * 16u;
   return L;
 }
@@ -70,16 +100,25 @@ __device__ __forceinline__ void put_op(uint8_t *base, uint32_t off, float v) {
     put_bf16(base, off, v);
 }
 
-// Fold the latents into the first layer, append the biases of layers 2-4 as
-// an extra input column, and pack every operand into the canonical
-// shared-memory layout (FP16 or BF16).  One CTA.
-template <bool F16>
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Fold the latents into the first layer and pack every operand into the
+// canonical shared-memory layout.  16-bit layers 2-4 get their biases as an
+// extra input column; E4M3 layers 2-4 get the per-layer power-of-two scale
+// 2^(8 - E), amax = m 2^E with m in [0.5, 1), and an FP32 epilogue block.
+// One CTA.
+template <int PR>
 __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ dec, const float *__restrict__ lat,
                                                    const DevMaterial *__restrict__ mats, int n_mat, int k1,
                                                    uint8_t *__restrict__ blob) {
+  constexpr bool H16 = PR != kPrBF16, F8 = PR == kPrE4M3;
   extern __shared__ float fold[];   // [n_mat][64]
-  const BlobLayout L = blob_layout(n_mat, k1);
+  __shared__ unsigned amax_bits[3];
+  const BlobLayout L = blob_layout(n_mat, k1, F8);
   const float *W1 = dec + kOffW1;
+  if (threadIdx.x < 3) amax_bits[threadIdx.x] = 0u;
   for (int e = threadIdx.x; e < n_mat * kHidden; e += blockDim.x) {
     const int m = e / kHidden, o = e % kHidden;
     float acc = dec[kOffB1 + o];
@@ -94,20 +133,57 @@ __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ dec
       v = W1[o * kDecIn + kLatent + c];
     else if (c < kQueryFeat + n_mat)
       v = fold[(c - kQueryFeat) * kHidden + o];
-    put_op<F16>(blob, L.w1 + tc::core_offset(o, c, k1), v);
+    put_op<H16>(blob, L.w1 + tc::core_offset(o, c, k1), v);
   }
-  for (int e = threadIdx.x; e < kHidden * kKH; e += blockDim.x) {
-    const int o = e / kKH, c = e % kKH;
-    const float v2 = c < kHidden ? dec[kOffW2 + o * kHidden + c] : (c == kHidden ? dec[kOffB2 + o] : 0.0f);
-    const float v3 = c < kHidden ? dec[kOffW3 + o * kHidden + c] : (c == kHidden ? dec[kOffB3 + o] : 0.0f);
-    put_op<F16>(blob, L.w2 + tc::core_offset(o, c, kKH), v2);
-    put_op<F16>(blob, L.w3 + tc::core_offset(o, c, kKH), v3);
-  }
-  for (int e = threadIdx.x; e < 16 * kKH; e += blockDim.x) {
-    const int o = e / kKH, c = e % kKH;
-    float v = 0.0f;
-    if (o < kOut) v = c < kHidden ? dec[kOffW4 + o * kHidden + c] : (c == kHidden ? dec[kOffB4 + o] : 0.0f);
-    put_op<F16>(blob, L.w4 + tc::core_offset(o, c, kKH), v);
+  if (!F8) {
+    for (int e = threadIdx.x; e < kHidden * kKH; e += blockDim.x) {
+      const int o = e / kKH, c = e % kKH;
+      const float v2 = c < kHidden ? dec[kOffW2 + o * kHidden + c] : (c == kHidden ? dec[kOffB2 + o] : 0.0f);
+      const float v3 = c < kHidden ? dec[kOffW3 + o * kHidden + c] : (c == kHidden ? dec[kOffB3 + o] : 0.0f);
+      put_op<H16>(blob, L.w2 + tc::core_offset(o, c, kKH), v2);
+      put_op<H16>(blob, L.w3 + tc::core_offset(o, c, kKH), v3);
+    }
+    for (int e = threadIdx.x; e < 16 * kKH; e += blockDim.x) {
+      const int o = e / kKH, c = e % kKH;
+      float v = 0.0f;
+      if (o < kOut) v = c < kHidden ? dec[kOffW4 + o * kHidden + c] : (c == kHidden ? dec[kOffB4 + o] : 0.0f);
+      put_op<H16>(blob, L.w4 + tc::core_offset(o, c, kKH), v);
+    }
+  } else {
+    // per-layer amax (non-negative floats order like their bit patterns)
+    float m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+    for (int e = threadIdx.x; e < kHidden * kHidden; e += blockDim.x) {
+      m2 = fmaxf(m2, fabsf(dec[kOffW2 + e]));
+      m3 = fmaxf(m3, fabsf(dec[kOffW3 + e]));
+      if (e < kOut * kHidden) m4 = fmaxf(m4, fabsf(dec[kOffW4 + e]));
+    }
+    atomicMax(&amax_bits[0], __float_as_uint(m2));
+    atomicMax(&amax_bits[1], __float_as_uint(m3));
+    atomicMax(&amax_bits[2], __float_as_uint(m4));
+    __syncthreads();
+    float scale[3];
+    float *epi = reinterpret_cast<float *>(blob + L.epi);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      int ex = 0;
+      frexpf(__uint_as_float(amax_bits[l]), &ex);
+      scale[l] = ldexpf(1.0f, 8 - ex);
+      if (threadIdx.x == 0) epi[kF8Inv + 1 + l] = ldexpf(1.0f, ex - 8);
+    }
+    if (threadIdx.x == 0) epi[kF8Inv] = 1.0f;
+    for (int e = threadIdx.x; e < 4 * 64; e += blockDim.x) {
+      const int l = e / 64, o = e % 64;
+      epi[kF8Bias + e] = l == 1 ? dec[kOffB2 + o] : l == 2 ? dec[kOffB3 + o] : (l == 3 && o < kOut) ? dec[kOffB4 + o] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < kHidden * kHidden; e += blockDim.x) {
+      const int o = e / kHidden, c = e % kHidden;
+      blob[L.w2 + tc::core_offset8(o, c, 64)] = to_e4m3(dec[kOffW2 + e] * scale[0]);
+      blob[L.w3 + tc::core_offset8(o, c, 64)] = to_e4m3(dec[kOffW3 + e] * scale[1]);
+    }
+    for (int e = threadIdx.x; e < 16 * kHidden; e += blockDim.x) {
+      const int o = e / kHidden, c = e % kHidden;
+      blob[L.w4 + tc::core_offset8(o, c, 64)] = o < kOut ? to_e4m3(dec[kOffW4 + e] * scale[2]) : (uint8_t)0;
+    }
   }
   float *alb = reinterpret_cast<float *>(blob + L.alb);
   for (int e = threadIdx.x; e < n_mat * 12; e += blockDim.x) {
@@ -167,22 +243,21 @@ __device__ __forceinline__ TileView tile_view(const TcArgs &a, int64_t tile) {
   return t;
 }
 
-// sin / cos of 2 pi 2^k frac(x) for k = 0..7 by angle doubling from one
-// hardware sincos of the reduced angle 2 pi (frac(x) - 1/2) in [-pi, pi);
-// w[k] packs (sin, cos) of octave k.
+// sin / cos of 2 pi 2^k frac(x) for k = 0..7: f_k = frac(2^k frac(x)) is
+// exact in FP32 (doubling and dropping the integer part), and each octave
+// takes one hardware sincos of the reduced angle 2 pi (f_k - 1/2) in
+// [-pi, pi), whose absolute error (~4e-7) does not grow with k as an
+// angle-doubling recurrence would; w[k] packs (sin, cos) of octave k.
 template <bool F16>
 __device__ __forceinline__ void octave_words(float x, uint32_t *w) {
-  const float fr = x - floorf(x);
-  float s, c;
-  __sincosf(6.283185307179586f * (fr - 0.5f), &s, &c);
-  s = -s;
-  c = -c;
+  float f = x - floorf(x);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    w[k] = tc::pack2<F16>(s, c);
-    const float s2 = 2.0f * s * c;
-    c = (c - s) * (c + s);
-    s = s2;
+    float s, c;
+    __sincosf(6.283185307179586f * (f - 0.5f), &s, &c);
+    w[k] = tc::pack2<F16>(-s, -c);
+    f = 2.0f * f;
+    f -= floorf(f);
   }
 }
 
@@ -236,14 +311,16 @@ __device__ __forceinline__ bool wg_sync_or(int wg, bool pred) {
   }
 }
 
-template <bool F16, int WG, bool MULTI>
+template <int PR, int WG, bool MULTI>
 __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const TcArgs a) {
+  constexpr bool F16 = PR != kPrBF16;   // layer-1 (and, unless E4M3, every) operand type
+  constexpr bool F8 = PR == kPrE4M3;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bar_w = reinterpret_cast<uint64_t *>(smem);
   uint64_t *bar_mma = bar_w + 1;                         // one per warpgroup
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_w + 1 + WG);
-  const BlobLayout L = blob_layout(a.n_mat, a.k1);
+  const BlobLayout L = blob_layout(a.n_mat, a.k1, F8);
   uint8_t *wts = smem + 1024;
   const int tid = threadIdx.x;
   const int wg = tid >> 7;              // warpgroup: its own tile pipeline
@@ -275,11 +352,13 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
   Point pt = load_point(view, view.first + row);
   bool ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
   const float *alb = reinterpret_cast<const float *>(wts + L.alb);
+  const float *epi = reinterpret_cast<const float *>(wts + L.epi);   // E4M3 only
 
   const uint32_t w1_addr = tc::smem_addr(wts + L.w1), w2_addr = tc::smem_addr(wts + L.w2);
   const uint32_t w3_addr = tc::smem_addr(wts + L.w3), w4_addr = tc::smem_addr(wts + L.w4);
   const uint32_t id64 = F16 ? tc::idesc_f16(128, 64) : tc::idesc_bf16(128, 64);
   const uint32_t id16 = F16 ? tc::idesc_f16(128, 16) : tc::idesc_bf16(128, 16);
+  const uint32_t id8_64 = tc::idesc_e4m3(128, 64), id8_16 = tc::idesc_e4m3(128, 16);
   const uint32_t one16 = F16 ? 0x3C00u : 0x3F80u;   // 1.0 in the operand type
   uint32_t phase = 0;
 
@@ -335,12 +414,21 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
       if (wg_sync_or(wg, !ok)) goto teardown;
       if (row == 0) {
         tc::tc_fence_after();
-        const int K = layer == 0 ? a.k1 : kKH;
         const uint32_t w_addr = layer == 0 ? w1_addr : layer == 1 ? w2_addr : layer == 2 ? w3_addr : w4_addr;
-        const uint32_t sbo = (uint32_t)K * 16u;
-        for (int kk = 0; kk < K / 16; ++kk) {
-          const uint64_t bd = tc::smem_desc(w_addr + kk * 256u, 128u, sbo);
-          tc::mma_f16_ts(tmem, tmem + kColA + 8u * kk, bd, layer == 3 ? id16 : id64, kk > 0 ? 1u : 0u);
+        if (F8 && layer > 0) {
+          // E4M3: K = 64 in two K = 32 steps (8 columns of A, 2 core matrices of B each)
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t bd = tc::smem_desc(w_addr + kk * 256u, 128u, 64u * 8u);
+            tc::mma_f8_ts(tmem, tmem + kColA + 8u * kk, bd, layer == 3 ? id8_16 : id8_64, kk > 0 ? 1u : 0u);
+          }
+        } else {
+          const int K = layer == 0 ? a.k1 : kKH;
+          const uint32_t sbo = (uint32_t)K * 16u;
+          for (int kk = 0; kk < K / 16; ++kk) {
+            const uint64_t bd = tc::smem_desc(w_addr + kk * 256u, 128u, sbo);
+            tc::mma_f16_ts(tmem, tmem + kColA + 8u * kk, bd, layer == 3 ? id16 : id64, kk > 0 ? 1u : 0u);
+          }
         }
         tc::mma_commit(my_bar);
       }
@@ -355,7 +443,27 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
       tc::tc_fence_before();
       ok = !wg_sync_or(wg, !ok);
       tc::tc_fence_after();
-      if (layer < 3) {
+      if (F8 && layer < 3) {
+        // y = acc * 2^-s_l + b_l (exactly acc for layer 1), ReLU, E4M3
+        const float inv = epi[kF8Inv + layer];
+        const float4 *bl = reinterpret_cast<const float4 *>(epi + kF8Bias + 64 * layer);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float acc[32];
+          tc::tmem_ld16(t_d + 32 * half, acc);
+          tc::tmem_ld16(t_d + 32 * half + 16, acc + 16);
+          tc::tmem_ld_wait();
+          uint32_t w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float4 b = bl[8 * half + k];
+            w[k] = tc::pack4_e4m3_relu(fmaf(acc[4 * k], inv, b.x), fmaf(acc[4 * k + 1], inv, b.y),
+                                       fmaf(acc[4 * k + 2], inv, b.z), fmaf(acc[4 * k + 3], inv, b.w));
+          }
+          tc::tmem_st8(t_a + 8 * half, w);
+        }
+        tc::tmem_st_wait();
+      } else if (layer < 3) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           float acc[32];
@@ -376,6 +484,11 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
         float y[16];
         tc::tmem_ld16(t_d, y);
         tc::tmem_ld_wait();
+        if (F8) {
+          const float inv = epi[kF8Inv + 3];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) y[c] = fmaf(y[c], inv, epi[kF8Bias + 64 * 3 + c]);
+        }
         if (p < p_end) {
           float c4[4];
           if (mat < 0) {
@@ -412,8 +525,8 @@ teardown:
   }
 }
 
-size_t tc_smem_bytes(int n_mat, int k1) {
-  const BlobLayout L = blob_layout(n_mat, k1);
+size_t tc_smem_bytes(int n_mat, int k1, bool f8) {
+  const BlobLayout L = blob_layout(n_mat, k1, f8);
   return 1024 /* alignment slack */ + 1024 /* barriers */ + align1k(L.total);
 }
 
@@ -530,24 +643,86 @@ __global__ void __launch_bounds__(128, 1) selftest_ts_kernel(const float *__rest
   }
 }
 
-template <bool F16, int WG, bool MULTI>
+// ---- self-test of the E4M3 path: A in tensor memory (four bytes per
+// column), B in shared memory (core_offset8), kind::f8f6f4, K = 32 per step.
+__global__ void __launch_bounds__(128, 1) selftest_f8_kernel(const float *__restrict__ A, const float *__restrict__ B,
+                                                             int n, int k, float *__restrict__ D, int *status) {
+  __shared__ __align__(1024) uint8_t sb[64 * 64];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < n * k; e += 128) {
+    const int r = e / k, c = e % k;
+    sb[tc::core_offset8(r, c, k)] = to_e4m3(B[e]);
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&slot, 128);
+  tc::fence_proxy_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  uint32_t w[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    w[j] = (4 * j < k) ? tc::pack4_e4m3(A[tid * k + 4 * j], A[tid * k + 4 * j + 1], A[tid * k + 4 * j + 2],
+                                        A[tid * k + 4 * j + 3])
+                       : 0u;
+  for (int c = 0; c < k / 32; ++c) tc::tmem_st8(tmem + lane_base + 64 + 8 * c, w + 8 * c);
+  tc::tmem_st_wait();
+  tc::tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc::tc_fence_after();
+    for (int kk = 0; kk < k / 32; ++kk) {
+      const uint64_t bd = tc::smem_desc(tc::smem_addr(sb) + kk * 256u, 128u, (uint32_t)k * 8u);
+      tc::mma_f8_ts(tmem, tmem + 64 + 8 * kk, bd, tc::idesc_e4m3(128, n), kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&bar);
+  }
+  const bool ok = tc::mbar_wait(&bar, 0, kWaitCycles);
+  if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
+  tc::tc_fence_after();
+  if (__syncthreads_and(ok)) {
+    for (int c = 0; c < n; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_base + c, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int e = 0; e < 16; ++e) D[tid * n + c + e] = v[e];
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+template <int PR, int WG, bool MULTI>
 const void *kernel_ptr() {
-  return reinterpret_cast<const void *>(decoder_tc_kernel<F16, WG, MULTI>);
+  return reinterpret_cast<const void *>(decoder_tc_kernel<PR, WG, MULTI>);
 }
 
 // Supported tile pipelines per CTA: 1, 2 or 4 (128 tensor-memory columns each).
 int norm_wg(int wg) { return wg == 2 || wg == 4 ? wg : 1; }
 
-template <bool MULTI>
-const void *pick_kernel_m(bool f16, int wg) {
-  if (f16)
-    return wg == 1 ? kernel_ptr<true, 1, MULTI>() : wg == 2 ? kernel_ptr<true, 2, MULTI>()
-                                                            : kernel_ptr<true, 4, MULTI>();
-  return wg == 1 ? kernel_ptr<false, 1, MULTI>() : wg == 2 ? kernel_ptr<false, 2, MULTI>()
-                                                           : kernel_ptr<false, 4, MULTI>();
+template <int PR, bool MULTI>
+const void *pick_kernel_pm(int wg) {
+  return wg == 1 ? kernel_ptr<PR, 1, MULTI>() : wg == 2 ? kernel_ptr<PR, 2, MULTI>() : kernel_ptr<PR, 4, MULTI>();
 }
-const void *pick_kernel(bool f16, int wg, bool multi = false) {
-  return multi ? pick_kernel_m<true>(f16, wg) : pick_kernel_m<false>(f16, wg);
+template <bool MULTI>
+const void *pick_kernel_m(int pr, int wg) {
+  return pr == kPrF16 ? pick_kernel_pm<kPrF16, MULTI>(wg)
+                      : pr == kPrE4M3 ? pick_kernel_pm<kPrE4M3, MULTI>(wg) : pick_kernel_pm<kPrBF16, MULTI>(wg);
+}
+const void *pick_kernel(int pr, int wg, bool multi = false) {
+  return multi ? pick_kernel_m<true>(pr, wg) : pick_kernel_m<false>(pr, wg);
 }
 
 // CTAs of the decoder that fit on one SM, counted from the kernel's
@@ -581,17 +756,24 @@ int tc_k1(int n_mat) {
   return (n_mat >= 1 && k1 <= 128) ? k1 : -1;
 }
 
-size_t tc_blob_bytes(int n_mat) { return blob_layout(n_mat, tc_k1(n_mat) > 0 ? tc_k1(n_mat) : 128).total; }
+// Largest packed blob over the precisions (the 16-bit layout is the larger).
+size_t tc_blob_bytes(int n_mat) {
+  const int k1 = tc_k1(n_mat) > 0 ? tc_k1(n_mat) : 128;
+  const uint32_t a = blob_layout(n_mat, k1, false).total, b = blob_layout(n_mat, k1, true).total;
+  return a > b ? a : b;
+}
 
 cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMaterial *mats, int n_mat, int precision,
                            void *blob, cudaStream_t s) {
   const int k1 = tc_k1(n_mat);
   if (k1 < 0) return cudaErrorInvalidValue;
   const size_t smem = (size_t)n_mat * kHidden * sizeof(float);
-  if (precision == FABRIC_PREC_FP16)
-    pack_kernel<true><<<1, 256, smem, s>>>(dec, latents, mats, n_mat, k1, static_cast<uint8_t *>(blob));
-  else
-    pack_kernel<false><<<1, 256, smem, s>>>(dec, latents, mats, n_mat, k1, static_cast<uint8_t *>(blob));
+  uint8_t *out = static_cast<uint8_t *>(blob);
+  switch (prec_code(precision)) {
+    case kPrF16: pack_kernel<kPrF16><<<1, 256, smem, s>>>(dec, latents, mats, n_mat, k1, out); break;
+    case kPrE4M3: pack_kernel<kPrE4M3><<<1, 256, smem, s>>>(dec, latents, mats, n_mat, k1, out); break;
+    default: pack_kernel<kPrBF16><<<1, 256, smem, s>>>(dec, latents, mats, n_mat, k1, out); break;
+  }
   return cudaGetLastError();
 }
 
@@ -599,22 +781,23 @@ int tc_default_ctas_per_sm(int n_mat, int precision) {
   const int k1 = tc_k1(n_mat);
   if (k1 < 0) return 1;
   const int wg = 1;
-  const void *fn = pick_kernel(precision == FABRIC_PREC_FP16, wg, false);
+  const int pr = prec_code(precision);
+  const void *fn = pick_kernel(pr, wg, false);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  return tc_resident_ctas(fn, tc_smem_bytes(n_mat, k1), wg);
+  return tc_resident_ctas(fn, tc_smem_bytes(n_mat, k1, pr == kPrE4M3), wg);
 }
 
 static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count, int ctas_per_sm, int warpgroups,
                              cudaStream_t s) {
-  const bool f16 = precision == FABRIC_PREC_FP16;
+  const int pr = prec_code(precision);
   const int wg = norm_wg(warpgroups);
-  const size_t smem = tc_smem_bytes(a.n_mat, a.k1);
-  const void *fn = pick_kernel(f16, wg, multi);
-  static bool attr_set[2][5][2] = {};
-  if (!attr_set[f16][wg][multi]) {
+  const size_t smem = tc_smem_bytes(a.n_mat, a.k1, pr == kPrE4M3);
+  const void *fn = pick_kernel(pr, wg, multi);
+  static bool attr_set[3][5][2] = {};
+  if (!attr_set[pr][wg][multi]) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set[f16][wg][multi] = true;
+    attr_set[pr][wg][multi] = true;
   }
   const int resident = tc_resident_ctas(fn, smem, wg);
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : resident;
@@ -671,7 +854,9 @@ cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_t
 
 cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, int a_in_tmem, float *d, int *status,
                                 cudaStream_t s) {
-  if (a_in_tmem)
+  if (a_in_tmem == 2)
+    selftest_f8_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);
+  else if (a_in_tmem)
     selftest_ts_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);
   else
     selftest_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);

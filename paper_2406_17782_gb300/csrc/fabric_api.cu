@@ -503,7 +503,6 @@ fabric_status fabric_prepare_neural(fabric_ctx *ctx, const float *latents_dev, f
   if (!latents_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "latents are NULL");
   if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
   ctx->prepared_prec = -1;
-  if (prec == FABRIC_PREC_FP8) return fail(ctx, FABRIC_ERR_UNSUPPORTED, "FP8 decoder not built yet");
   if (prec != FABRIC_PREC_FP32) {
     if (tc_k1(ctx->n_mat) < 0)
       return fail(ctx, FABRIC_ERR_UNSUPPORTED, "tensor-core decoder supports at most 89 materials (have %d)",
@@ -569,6 +568,17 @@ fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const flo
   FAB_CUDA(ctx,
            launch_selftest_mma(a_dev, b_dev, n, k, a_in_tmem ? 1 : 0, d_dev, ctx->d_status,
                                static_cast<cudaStream_t>(stream)),
+           "selftest launch");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_selftest_mma_e4m3(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
+                                       float *d_dev, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!a_dev || !b_dev || !d_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "NULL pointer");
+  if (!(k == 32 || k == 64) || !(n == 16 || n == 32 || n == 64))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "k must be 32/64 and n 16/32/64");
+  FAB_CUDA(ctx, launch_selftest_mma(a_dev, b_dev, n, k, 2, d_dev, ctx->d_status, static_cast<cudaStream_t>(stream)),
            "selftest launch");
   return FABRIC_OK;
 }

@@ -64,8 +64,8 @@ fabric_status fabric_plan_shade(fabric_ctx *ctx, const fabric_plan *plan, fabric
   if (!ctx) return FABRIC_ERR_INVALID_ARG;
   ctx->last_error.clear();
   if (!plan || plan->device != ctx->device) return fail(ctx, FABRIC_ERR_INVALID_ARG, "plan is NULL or on another device");
-  if (prec != FABRIC_PREC_FP16 && prec != FABRIC_PREC_BF16)
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "batched draws run the FP16 or BF16 tensor-core decoder");
+  if (prec != FABRIC_PREC_FP16 && prec != FABRIC_PREC_BF16 && prec != FABRIC_PREC_FP8)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "batched draws run the FP16, BF16 or FP8 tensor-core decoder");
   if (ctx->prepared_prec != (int)prec || ctx->prepared_version != ctx->version)
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "no prepared state for this precision, materials and parameters");
   if (plan->n_tiles == 0) return FABRIC_OK;

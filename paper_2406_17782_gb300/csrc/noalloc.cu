@@ -27,8 +27,8 @@ extern "C" fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabr
   ctx->last_error.clear();
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   if (!check_gbuffer(ctx, g)) return FABRIC_ERR_INVALID_ARG;
-  if (prec != FABRIC_PREC_FP16 && prec != FABRIC_PREC_BF16)
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "the no-allocation call runs the FP16 or BF16 tensor-core decoder only");
+  if (prec != FABRIC_PREC_FP16 && prec != FABRIC_PREC_BF16 && prec != FABRIC_PREC_FP8)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "the no-allocation call runs the FP16, BF16 or FP8 tensor-core decoder only");
   if (g->n == 0) return FABRIC_OK;
   if (!rgb_dev || !latents_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "rgb output or latents is NULL");
   if (comps_dev && !is_aligned16(comps_dev))

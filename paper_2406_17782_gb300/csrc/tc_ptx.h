@@ -33,6 +33,20 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 A and B (format code 0 for
+// both), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 8-bit operands use the same core matrices (8 rows x 16 bytes, here 16
+// elements), so element (row, k) of a rows x K tile lives at
+//     ((row / 8) * (K / 16) + k / 16) * 128 + (row % 8) * 16 + k % 16
+// and the stride-dimension byte offset is K * 8.
+__host__ __device__ __forceinline__ uint32_t core_offset8(int row, int k, int K) {
+  return (uint32_t)(((row >> 3) * (K >> 4) + (k >> 4)) * 128 + (row & 7) * 16 + (k & 15));
+}
+
 // Shared-memory matrix descriptor (no swizzle, K-major canonical layout).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -148,6 +162,18 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
       "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// 8-bit operands (kind::f8f6f4) with A in tensor memory: four elements per
+// 32-bit column (element k in byte k % 4), row i in lane i.  One instruction
+// covers K = 32.
+__device__ __forceinline__ void mma_f8_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // 32 lanes x 32 bit, 8 consecutive columns from registers: thread t of the
 // warp writes row (lane base + t), columns [col, col + 8).
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
@@ -211,6 +237,21 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 template <bool F16>
 __device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
   return F16 ? pack_f16_relu(lo, hi) : pack_bf16_relu(lo, hi);
+}
+
+// Four floats to four E4M3 bytes (round to nearest even, saturating to
+// +-448), v0 in the lowest byte; the _relu form clamps negatives to +0.
+__device__ __forceinline__ uint32_t pack4_e4m3(float v0, float v1, float v2, float v3) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(v1), "f"(v0));
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(v3), "f"(v2));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ uint32_t pack4_e4m3_relu(float v0, float v1, float v2, float v3) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(v1), "f"(v0));
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(v3), "f"(v2));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
 __device__ __forceinline__ void st_shared_v4(void *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {

@@ -65,7 +65,7 @@ def shuffled(g: GBuffer, target: torch.Tensor, gen: torch.Generator):
 
 
 def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch: int = 65536,
-          lr0: float = 1e-3, lr1: float = 1e-5, log_every: int = 1000, seed: int = 1):
+          lr0: float = 1e-3, lr1: float = 1e-5, log_every: int = 1000, seed: int = 1, verbose: bool = True):
     fab.set_train_materials(mats)
     gen = torch.Generator(device=fab.device)
     gen.manual_seed(seed)
@@ -85,7 +85,8 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
         if (step + 1) % log_every == 0:
             mean = float(loss_buf.mean().item())
             losses.append((step + 1, mean))
-            print(f"step {step + 1:7d}  loss {mean:.5f}  lr {lr:.2e}  {time.time() - t0:6.1f}s", flush=True)
+            if verbose:
+                print(f"step {step + 1:7d}  loss {mean:.5f}  lr {lr:.2e}  {time.time() - t0:6.1f}s", flush=True)
     fab.sync_status()
     return losses
 
@@ -116,7 +117,7 @@ def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(
         r, _ = fab.shade_reference(g, s, s, 0x1234)
         out[f"reference_{s * s}spp"] = _errors(fab, r, gt, g)
     lit = fab.error_stats(gt, torch.zeros_like(gt), weights=g.wi[:, 2], group=3, weight_stride=3).cpu().numpy()
-    out["gt_rms"] = math.sqrt(float(lit[1]) / gt.numel())
+    out["gt_rms"] = math.sqrt(float(lit[0]) / gt.numel())      # sum (gt w)^2 over the frame
     fab.sync_status()
     return out
 

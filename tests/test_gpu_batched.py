@@ -40,7 +40,7 @@ def make_segments(sizes, seed=0):
 SIZES = [50_000, 1, 127, 128, 129, 0, 300, 4097, 65_536, 256, 999]
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
 def test_plan_equals_per_segment_draws(fab, prepared, prec):
     mats, dec, z, lat = prepared
     segs = make_segments(SIZES)
@@ -55,11 +55,12 @@ def test_plan_equals_per_segment_draws(fab, prepared, prec):
         want_rgb, want_c = fab.shade_neural_prepared(g, prec, comps=True)
         fab.sync_status()
         assert torch.equal(rgb, want_rgb) and torch.equal(comps, want_c)
-    # one segment against the FP64 decoder
+    # one segment against the FP64 decoder (FP8: against its E4M3 emulation)
     host, g, rgb, comps = segs[0]
-    want_c, _ = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, host)
+    P = M.unpack(dec, M.DEC_SHAPES)
+    want_c, _ = M.shade_neural_e4m3(P, z, mats, host) if prec == "fp8" else M.shade_neural(P, z, mats, host)
     d = comps.cpu().numpy() - want_c
-    assert np.sqrt((d ** 2).sum() / (want_c ** 2).sum()) < (5e-3 if prec == "fp16" else 1.2e-2)
+    assert np.sqrt((d ** 2).sum() / (want_c ** 2).sum()) < {"fp16": 5e-3, "bf16": 1.2e-2, "fp8": 5e-3}[prec]
     plan.close()
 
 

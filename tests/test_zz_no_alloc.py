@@ -32,7 +32,7 @@ def call_noalloc(fab, g: GBuffer, latents, prec, rgb, comps):
                                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
 def test_noalloc_matches_allocating_call_twice(fab, prec):
     mats = W.frame_materials()
     fab.set_materials(mats)
