@@ -229,10 +229,26 @@ def encoder_backward(p: dict, cache: dict, dz: np.ndarray):
 # --------------------------------------------------------------------------
 # loss (Eq. 9-11)
 # --------------------------------------------------------------------------
-def loss_and_grad(y: np.ndarray, target: np.ndarray):
+Y_CLAMP = 12.0          # head pre-activation limit of the rendered-space loss
+
+
+def loss_and_grad(y: np.ndarray, target: np.ndarray, mode: str = "eq11", wz=None):
     """y: raw head [B,4] = (C_warp, C_weft, S'_warp, S'_weft); target: ground
-    truth components [B,4].  Loss = sum over yarn types of
-    lambda_S mean (S' - ln(k S_gt + 1))^2 + lambda_C mean (C - C_gt)^2."""
+    truth components [B,4].
+
+    mode "eq11" (Eq. 9-11): sum over yarn types of
+    lambda_S mean (S' - ln(k S_gt + 1))^2 + lambda_C mean (C - C_gt)^2.
+
+    mode "rendered" (this build's option): the squared error of the
+    components as they light the frame, (1/B) sum_p sum_c ((c_hat - c_gt)
+    max(wz, 0))^2 with wz = <wi . n_s> per query, c_hat = y for C and
+    c_hat = (exp(min(S', 12)) - 1) / k for S (the inverse of Eq. 9 without
+    the inference clamp at 0; the gradient is 0 above the limit)."""
+    if mode == "rendered":
+        return _loss_rendered(np.asarray(y, np.float64), np.asarray(target, np.float64),
+                              np.asarray(wz, np.float64))
+    if mode != "eq11":
+        raise ValueError(mode)
     B = y.shape[0]
     t = np.empty_like(target, dtype=np.float64)
     t[:, 0:2] = target[:, 0:2]
@@ -241,6 +257,20 @@ def loss_and_grad(y: np.ndarray, target: np.ndarray):
     lam = np.array([LAMBDA_C, LAMBDA_C, LAMBDA_S, LAMBDA_S])
     loss = float(np.sum(lam * np.mean(d * d, axis=0)))
     dy = 2.0 * lam * d / B
+    return loss, dy
+
+
+def _loss_rendered(y, target, wz):
+    B = y.shape[0]
+    w = np.maximum(wz, 0.0)[:, None]
+    c = y.copy()
+    ys = np.minimum(y[:, 2:4], Y_CLAMP)
+    c[:, 2:4] = np.expm1(ys) / K_SPEC
+    dc = np.ones_like(y)
+    dc[:, 2:4] = np.where(y[:, 2:4] < Y_CLAMP, np.exp(ys) / K_SPEC, 0.0)
+    d = (c - target) * w
+    loss = float(np.sum(d * d) / B)
+    dy = 2.0 * d * w * dc / B
     return loss, dy
 
 
@@ -259,9 +289,11 @@ def adam_step(theta, grad, m, v, step: int, lr: float):
     return theta - lr * mh / (np.sqrt(vh) + ADAM_EPS), m, v
 
 
-def train_step(dec_flat, enc_flat, state: dict, materials, mat_idx, gbuf, target, lr: float):
+def train_step(dec_flat, enc_flat, state: dict, materials, mat_idx, gbuf, target, lr: float,
+               loss_mode: str = "eq11"):
     """One full training step in FP64: encoder over all materials, decoder over
-    the batch, Eq. 11 loss, backward through both, Adam on the concatenated
+    the batch, the loss (Eq. 11, or the rendered-space option of
+    loss_and_grad), backward through both, Adam on the concatenated
     [decoder | encoder] parameter vector.  Returns (loss, new dec, new enc)."""
     dec = unpack(dec_flat, DEC_SHAPES)
     enc = unpack(enc_flat, ENC_SHAPES)
@@ -269,7 +301,7 @@ def train_step(dec_flat, enc_flat, state: dict, materials, mat_idx, gbuf, target
     z, ecache = encoder_forward(enc, f, keep=True)
     x = decoder_inputs(z, mat_idx, gbuf)
     y, dcache = decoder_forward(dec, x, keep=True)
-    loss, dy = loss_and_grad(y, target)
+    loss, dy = loss_and_grad(y, target, loss_mode, np.asarray(gbuf["wi"], np.float64)[:, 2])
     gd, dx = decoder_backward(dec, dcache, dy)
     dz = np.zeros_like(z)
     np.add.at(dz, np.asarray(mat_idx, np.int64), dx[:, :LATENT])

@@ -158,6 +158,33 @@ def test_loss_closed_form_and_gradient(M):
             assert abs(fd - dy[i, j]) < 1e-7
 
 
+def test_rendered_loss_closed_form_and_gradient(M):
+    """The rendered-space loss option: its value on a hand-computed case, zero
+    for the prediction that decodes to the target, no weight on light from
+    below the surface, and central finite differences of its gradient
+    (including past the head clamp, where it is 0)."""
+    tgt = np.array([[0.2, 0.1, 0.05, 0.0], [0.4, 0.3, 0.0, 0.01], [1.0, 1.0, 1.0, 1.0]])
+    wz = np.array([0.5, 1.0, -0.3])
+    y = np.zeros_like(tgt)                       # decodes to C = 0, S = 0
+    loss, _ = M.loss_and_grad(y, tgt, "rendered", wz)
+    want = ((0.2 ** 2 + 0.1 ** 2 + 0.05 ** 2) * 0.25 + (0.4 ** 2 + 0.3 ** 2 + 0.01 ** 2) * 1.0) / 3
+    assert abs(loss - want) < 1e-15
+    perfect = np.concatenate([tgt[:, :2], np.log(100 * tgt[:, 2:] + 1)], 1)
+    assert M.loss_and_grad(perfect, tgt, "rendered", wz)[0] < 1e-30
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(tgt.shape)
+    y[0, 3] = 13.0                               # beyond the clamp
+    _, dy = M.loss_and_grad(y, tgt, "rendered", wz)
+    assert dy[0, 3] == 0.0 and np.all(dy[2] == 0.0)
+    h = 1e-4      # the clamped entry makes the loss ~2e5: a larger step keeps rounding below 1e-6
+    for i in range(3):
+        for j in range(4):
+            yp = y.copy(); yp[i, j] += h
+            ym = y.copy(); ym[i, j] -= h
+            fd = (M.loss_and_grad(yp, tgt, "rendered", wz)[0] - M.loss_and_grad(ym, tgt, "rendered", wz)[0]) / (2 * h)
+            assert abs(fd - dy[i, j]) < 1e-6 * max(1.0, abs(dy[i, j]))
+
+
 def test_head_inverts_specular_mapping(M):
     S = np.array([0.0, 1e-3, 0.05, 2.0])
     y = np.zeros((4, 4))
