@@ -141,6 +141,12 @@ int fabric_sm_count(const fabric_ctx *ctx);
 fabric_status fabric_set_launch_config(fabric_ctx *ctx, int decoder_ctas_per_sm, int decoder_warpgroups,
                                        int reference_lanes);
 
+/* Warpgroups per decoder tile pipeline: 1 (0 = 1) or 2.  With 2, the two
+ * threads of each tile row split the encoding and the epilogues' columns;
+ * this applies with 1 or 2 pipelines per CTA (with 4 the setting is ignored).
+ * FABRIC_ERR_INVALID_ARG outside 0..2. */
+fabric_status fabric_set_decoder_tile_warpgroups(fabric_ctx *ctx, int warpgroups_per_tile);
+
 /* ------------------------------------------------------------------ */
 /* Materials                                                          */
 /* ------------------------------------------------------------------ */
@@ -260,6 +266,17 @@ fabric_status fabric_set_train_materials(fabric_ctx *ctx, const fabric_material 
  */
 fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr,
                                 double *loss_dev, void *stream);
+
+/* Training loss of fabric_train_step (default FABRIC_LOSS_EQ11):
+ *   FABRIC_LOSS_EQ11      the paper's Eq. 11, as above;
+ *   FABRIC_LOSS_RENDERED  this library's option: (1/B) sum over queries and
+ *       the four components of ((c_hat - c) max(<wi . n_s>, 0))^2, where
+ *       c_hat is the decoded component (C = y; S = (exp(min(y, 12)) - 1)/100,
+ *       the inverse of Eq. 9 without the clamp at 0): the error of the
+ *       components as they light the frame under a directional light.
+ * FABRIC_ERR_INVALID_ARG for other values. */
+typedef enum { FABRIC_LOSS_EQ11 = 0, FABRIC_LOSS_RENDERED = 1 } fabric_loss;
+fabric_status fabric_set_train_loss(fabric_ctx *ctx, fabric_loss loss);
 
 /* ------------------------------------------------------------------ */
 /* Building blocks for a torch.autograd.Function                      */

@@ -18,6 +18,7 @@ FABRIC_OK = 0
 STATUS_NAMES = {0: "FABRIC_OK", 1: "FABRIC_ERR_INVALID_ARG", 2: "FABRIC_ERR_CUDA", 3: "FABRIC_ERR_OOM",
                 4: "FABRIC_ERR_TIMEOUT", 5: "FABRIC_ERR_IO", 6: "FABRIC_ERR_UNSUPPORTED", 7: "FABRIC_ERR_DEVICE"}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
+LOSS = {"eq11": 0, "rendered": 1}
 
 
 class FabricMaterial(ctypes.Structure):
@@ -77,6 +78,8 @@ def load(path: str | None = None):
         "fabric_sync_status": (st, [vp, vp]),
         "fabric_sm_count": (i32, [vp]),
         "fabric_set_launch_config": (st, [vp, i32, i32, i32]),
+        "fabric_set_decoder_tile_warpgroups": (st, [vp, i32]),
+        "fabric_set_train_loss": (st, [vp, i32]),
         "fabric_set_materials": (st, [vp, vp, i32]),
         "fabric_set_train_materials": (st, [vp, vp, i32]),
         "fabric_decoder_param_count": (i64, []),

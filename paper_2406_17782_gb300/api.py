@@ -120,10 +120,13 @@ class Fabric:
     def sync_status(self, stream=None):
         self._check(self.lib.fabric_sync_status(self.h, _stream_handle(stream)))
 
-    def set_launch_config(self, decoder_ctas_per_sm: int = 0, decoder_warpgroups: int = 0, reference_lanes: int = 0):
+    def set_launch_config(self, decoder_ctas_per_sm: int = 0, decoder_warpgroups: int = 0, reference_lanes: int = 0,
+                          decoder_tile_warpgroups: int = 0):
         self._check(self.lib.fabric_set_launch_config(self.h, int(decoder_ctas_per_sm), int(decoder_warpgroups),
                                                       int(reference_lanes)))
+        self._check(self.lib.fabric_set_decoder_tile_warpgroups(self.h, int(decoder_tile_warpgroups)))
         self.launch_config = (int(decoder_ctas_per_sm), int(decoder_warpgroups), int(reference_lanes))
+        self.tile_warpgroups = int(decoder_tile_warpgroups)
 
     # ---------------------------------------------------------------- setup
     def set_materials(self, materials):
@@ -213,6 +216,11 @@ class Fabric:
     def plan(self, segments) -> "Plan":
         """Batched draw over (GBuffer, rgb_out, comps_out or None) triples."""
         return Plan(self, segments)
+
+    def set_train_loss(self, loss: str = "eq11"):
+        """'eq11' (the paper's Eq. 11) or 'rendered' (squared error of the
+        components weighted by max(wi.z, 0))."""
+        self._check(self.lib.fabric_set_train_loss(self.h, _abi.LOSS[loss]))
 
     def train_step(self, batch: GBuffer, target: torch.Tensor, lr: float, loss_out=None, stream=None):
         loss = loss_out if loss_out is not None else torch.empty((), dtype=torch.float64, device=self.device)

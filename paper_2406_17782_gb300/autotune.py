@@ -17,7 +17,9 @@ import os
 import torch
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fabric_gb300_autotune.json")
-DECODER_CANDIDATES = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 1), (2, 2), (4, 1)]
+# (tile pipelines per CTA, CTAs per SM, warpgroups per tile pipeline)
+DECODER_CANDIDATES = [(1, 1, 1), (1, 2, 1), (1, 3, 1), (1, 4, 1), (2, 1, 1), (2, 2, 1), (4, 1, 1),
+                      (1, 2, 2), (1, 3, 2), (1, 4, 2), (2, 1, 2), (2, 2, 2)]
 
 
 def _key(fab, kind: str, precision: str, n_mat: int, n: int, extra: str = "") -> str:
@@ -59,24 +61,26 @@ def _current(fab):
 
 def tune_decoder(fab, g, precision: str = "fp16", candidates=None, reps: int = 50,
                  cache_path: str = DEFAULT_CACHE, force: bool = False) -> dict:
-    """Pick (warpgroups per CTA, CTAs per SM) of the decoder for G-buffer `g`
-    (neural state already prepared for `precision`)."""
+    """Pick (tile pipelines per CTA, CTAs per SM, warpgroups per pipeline) of
+    the decoder for G-buffer `g` (neural state already prepared for
+    `precision`)."""
     candidates = candidates or DECODER_CANDIDATES
     cache = _load(cache_path)
     key = _key(fab, "decoder", precision, fab.n_mat, g.n)
     lanes = _current(fab)[2]
-    if not force and key in cache:
-        fab.set_launch_config(cache[key]["ctas_per_sm"], cache[key]["warpgroups"], lanes)
-        return cache[key]
+    if not force and key in cache and "tile_warpgroups" in cache[key]:
+        e = cache[key]
+        fab.set_launch_config(e["ctas_per_sm"], e["warpgroups"], lanes, e["tile_warpgroups"])
+        return e
     out = torch.empty((g.n, 3), dtype=torch.float32, device=fab.device)
     timings = {}
-    for wg, c in candidates:
-        fab.set_launch_config(c, wg, lanes)
-        timings[(wg, c)] = _time(lambda: fab.shade_neural_prepared(g, precision, out_rgb=out), reps)
-    wg, c = min(timings, key=timings.get)
-    fab.set_launch_config(c, wg, lanes)
-    cache[key] = {"warpgroups": wg, "ctas_per_sm": c, "ms": timings[(wg, c)],
-                  "timings": {f"wg{k[0]}_cta{k[1]}": v for k, v in timings.items()}}
+    for wg, c, h in candidates:
+        fab.set_launch_config(c, wg, lanes, h)
+        timings[(wg, c, h)] = _time(lambda: fab.shade_neural_prepared(g, precision, out_rgb=out), reps)
+    wg, c, h = min(timings, key=timings.get)
+    fab.set_launch_config(c, wg, lanes, h)
+    cache[key] = {"warpgroups": wg, "ctas_per_sm": c, "tile_warpgroups": h, "ms": timings[(wg, c, h)],
+                  "timings": {f"wg{k[0]}_cta{k[1]}_h{k[2]}": v for k, v in timings.items()}}
     _store(cache_path, cache)
     return cache[key]
 
@@ -87,16 +91,17 @@ def tune_reference(fab, g, spp_x: int, spp_y: int, candidates=(1, 2, 4, 8, 16, 3
     cache = _load(cache_path)
     key = _key(fab, "reference", "fp32", fab.n_mat, g.n, f"spp{spp_x}x{spp_y}")
     ctas, wg, _ = _current(fab)
+    h = getattr(fab, "tile_warpgroups", 0)
     if not force and key in cache:
-        fab.set_launch_config(ctas, wg, cache[key]["lanes"])
+        fab.set_launch_config(ctas, wg, cache[key]["lanes"], h)
         return cache[key]
     out = torch.empty((g.n, 3), dtype=torch.float32, device=fab.device)
     timings = {}
     for lanes in candidates:
-        fab.set_launch_config(ctas, wg, lanes)
+        fab.set_launch_config(ctas, wg, lanes, h)
         timings[lanes] = _time(lambda: fab.shade_reference(g, spp_x, spp_y, 1, out_rgb=out), reps)
     best = min(timings, key=timings.get)
-    fab.set_launch_config(ctas, wg, best)
+    fab.set_launch_config(ctas, wg, best, h)
     cache[key] = {"lanes": best, "ms": timings[best], "timings": {str(k): v for k, v in timings.items()}}
     _store(cache_path, cache)
     return cache[key]

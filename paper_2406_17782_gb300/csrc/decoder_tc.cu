@@ -267,65 +267,80 @@ struct Point {
   int mat;   // -1: beyond the end
 };
 
-__device__ __forceinline__ Point load_point(const TileView &a, int64_t p) {
+// Load the fields this thread encodes: all of them with one thread per row
+// (H = 1); with two threads per row (H = 2) half 0 takes u, the footprint and
+// the directions, half 1 takes v; both take the material.
+template <int H>
+__device__ __forceinline__ Point load_point(const TileView &a, int64_t p, int h) {
   Point q;
+  q.u = q.v = q.r = q.wi0 = q.wi1 = q.wi2 = q.wo0 = q.wo1 = q.wo2 = 0.0f;
+  q.mat = -1;
   if (p < a.n) {
-    q.u = __ldg(a.u + p);
-    q.v = __ldg(a.v + p);
-    q.r = __ldg(a.radius + p);
-    q.wi0 = __ldg(a.wi + 3 * p);
-    q.wi1 = __ldg(a.wi + 3 * p + 1);
-    q.wi2 = __ldg(a.wi + 3 * p + 2);
-    q.wo0 = __ldg(a.wo + 3 * p);
-    q.wo1 = __ldg(a.wo + 3 * p + 1);
-    q.wo2 = __ldg(a.wo + 3 * p + 2);
     q.mat = __ldg(a.material + p);
-  } else {
-    q.u = q.v = q.r = q.wi0 = q.wi1 = q.wi2 = q.wo0 = q.wo1 = q.wo2 = 0.0f;
-    q.mat = -1;
+    if (H == 1 || h == 0) {
+      q.u = __ldg(a.u + p);
+      q.r = __ldg(a.radius + p);
+      q.wi0 = __ldg(a.wi + 3 * p);
+      q.wi1 = __ldg(a.wi + 3 * p + 1);
+      q.wi2 = __ldg(a.wi + 3 * p + 2);
+      q.wo0 = __ldg(a.wo + 3 * p);
+      q.wo1 = __ldg(a.wo + 3 * p + 1);
+      q.wo2 = __ldg(a.wo + 3 * p + 2);
+    }
+    if (H == 1 || h == 1) q.v = __ldg(a.v + p);
   }
   return q;
 }
 
-// Named barrier ID over the 128 threads of one warpgroup, OR-reducing `pred`.
-template <int ID>
+// Named barrier ID over the PT threads of one tile pipeline, OR-reducing `pred`.
+template <int ID, int PT>
 __device__ __forceinline__ bool bar_or(bool pred) {
   int r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.b32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, %2, 128, p;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
       "selp.s32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((int)pred), "n"(ID)
+      : "r"((int)pred), "n"(ID), "n"(PT)
       : "memory");
   return r != 0;
 }
-// Warpgroup wg synchronises on barrier 1 + wg (barrier 0 is __syncthreads).
+// Pipeline wg synchronises on barrier 1 + wg (barrier 0 is __syncthreads).
+template <int PT>
 __device__ __forceinline__ bool wg_sync_or(int wg, bool pred) {
   switch (wg) {
-    case 0: return bar_or<1>(pred);
-    case 1: return bar_or<2>(pred);
-    case 2: return bar_or<3>(pred);
-    default: return bar_or<4>(pred);
+    case 0: return bar_or<1, PT>(pred);
+    case 1: return bar_or<2, PT>(pred);
+    case 2: return bar_or<3, PT>(pred);
+    default: return bar_or<4, PT>(pred);
   }
 }
 
-template <int PR, int WG, bool MULTI>
-__global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const TcArgs a) {
+// WG tile pipelines per CTA, each of H warpgroups: with H = 2 the two threads
+// of a row (warps w and w + 4 share the tensor-memory lane quadrant) split
+// the encoding and every epilogue's columns, which halves the serial work per
+// thread and doubles the warps that hide the MMA and tcgen05.ld latencies.
+template <int PR, int WG, int H, bool MULTI>
+__global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(const TcArgs a) {
   constexpr bool F16 = PR != kPrBF16;   // layer-1 (and, unless E4M3, every) operand type
   constexpr bool F8 = PR == kPrE4M3;
+  constexpr int PT = kTile * H;         // threads per tile pipeline
+  constexpr int CH = 2 / H;             // 32-column chunks of D per thread
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bar_w = reinterpret_cast<uint64_t *>(smem);
-  uint64_t *bar_mma = bar_w + 1;                         // one per warpgroup
+  uint64_t *bar_mma = bar_w + 1;                         // one per pipeline
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_w + 1 + WG);
   const BlobLayout L = blob_layout(a.n_mat, a.k1, F8);
   uint8_t *wts = smem + 1024;
   const int tid = threadIdx.x;
-  const int wg = tid >> 7;              // warpgroup: its own tile pipeline
-  const int row = tid & (kTile - 1);    // tile row owned by this thread
+  const int wg = tid / PT;              // tile pipeline
+  const int tp = tid % PT;              // thread within the pipeline
+  const int h = H == 1 ? 0 : tp >> 7;   // which half of the row's columns
+  const int row = tp & (kTile - 1);     // tile row owned by this thread
   const int warp = tid >> 5;
+  const bool lead = tp == 0;            // issues the MMAs
   uint64_t *my_bar = bar_mma + wg;
 
   if (tid == 0) {
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot + kColsPerTile * (uint32_t)wg;   // this warpgroup's D column 0, lane 0
+  const uint32_t tmem = *tmem_slot + kColsPerTile * (uint32_t)wg;   // this pipeline's D column 0, lane 0
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;          // this warp's lane quadrant
   const uint32_t t_d = tmem + lane, t_a = tmem + lane + kColA;
 
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
   const int64_t stride = (int64_t)gridDim.x * WG;
   int64_t tile = (int64_t)blockIdx.x * WG + wg;
   TileView view = tile_view<MULTI>(a, tile);
-  Point pt = load_point(view, view.first + row);
+  Point pt = load_point<H>(view, view.first + row, h);
   bool ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
   const float *alb = reinterpret_cast<const float *>(wts + L.alb);
   const float *epi = reinterpret_cast<const float *>(wts + L.epi);   // E4M3 only
@@ -370,49 +385,63 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
     const int64_t p_end = view.n;
     int mat = pt.mat;
     if (mat >= a.n_mat) {
-      atomicOr(a.status, kStatusBadMaterial);
+      if (H == 1 || h == 0) atomicOr(a.status, kStatusBadMaterial);
       mat = -2;
     }
-    // ---- encode this thread's point into its row of the layer-1 A operand
+    // ---- encode this thread's share of its row of the layer-1 A operand
     {
-      uint32_t w[16];
-      if (mat >= 0) {
-        octave_words<F16>(pt.u, w);
-        octave_words<F16>(pt.v, w + 8);
-      } else {
+      uint32_t w[8];
+      if (H == 1 || h == 0) {                        // features 0..15: octaves of u
+        if (mat >= 0) {
+          octave_words<F16>(pt.u, w);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) w[k] = 0u;
+          for (int k = 0; k < 8; ++k) w[k] = 0u;
+        }
+        tc::tmem_st8(t_a, w);
       }
-      tc::tmem_st8(t_a, w);                          // features 0..15 (u)
-      tc::tmem_st8(t_a + 8, w + 8);                  // features 16..31 (v)
-      if (mat >= 0) {
-        const float l = (__logf(fmaxf(pt.r, kRFloor)) - kLogRC0) * kLogRInvC1;
-        w[0] = tc::pack2<F16>(l, pt.wi0);
-        w[1] = tc::pack2<F16>(pt.wi1, pt.wi2);
-        w[2] = tc::pack2<F16>(pt.wo0, pt.wo1);
-        w[3] = tc::pack2<F16>(pt.wo2, mat == 0 ? 1.0f : 0.0f);
-      } else {
-        w[0] = w[1] = w[2] = w[3] = 0u;
+      if (H == 1 || h == 1) {                        // features 16..31: octaves of v
+        if (mat >= 0) {
+          octave_words<F16>(pt.v, w);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) w[k] = 0u;
+        }
+        tc::tmem_st8(t_a + 8, w);
       }
-      // features 40.. are the one-hot material columns (39 is in w[3])
-      const int hot = kQueryFeat + mat;
+      if (H == 1 || h == 0) {
+        if (mat >= 0) {
+          const float l = (__logf(fmaxf(pt.r, kRFloor)) - kLogRC0) * kLogRInvC1;
+          w[0] = tc::pack2<F16>(l, pt.wi0);
+          w[1] = tc::pack2<F16>(pt.wi1, pt.wi2);
+          w[2] = tc::pack2<F16>(pt.wo0, pt.wo1);
+          w[3] = tc::pack2<F16>(pt.wo2, mat == 0 ? 1.0f : 0.0f);
+        } else {
+          w[0] = w[1] = w[2] = w[3] = 0u;
+        }
+        // features 40.. are the one-hot material columns (39 is in w[3])
+        const int hot = kQueryFeat + mat;
 #pragma unroll
-      for (int k = 4; k < 8; ++k) w[k] = (hot == 2 * (16 + k) ? one16 : 0u) | (hot == 2 * (16 + k) + 1 ? one16 << 16 : 0u);
-      tc::tmem_st8(t_a + 16, w);                     // features 32..47
-      for (int c = 3; c < a.k1 / 16; ++c) {          // features 48.. (wider one-hot)
+        for (int k = 4; k < 8; ++k) w[k] = (hot == 2 * (16 + k) ? one16 : 0u) | (hot == 2 * (16 + k) + 1 ? one16 << 16 : 0u);
+        tc::tmem_st8(t_a + 16, w);                   // features 32..47
+        for (int c = 3; c < a.k1 / 16; ++c) {        // features 48.. (wider one-hot)
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          w[k] = (hot == 16 * c + 2 * k ? one16 : 0u) | (hot == 16 * c + 2 * k + 1 ? one16 << 16 : 0u);
-        tc::tmem_st8(t_a + 8 * c, w);
+          for (int k = 0; k < 8; ++k)
+            w[k] = (hot == 16 * c + 2 * k ? one16 : 0u) | (hot == 16 * c + 2 * k + 1 ? one16 << 16 : 0u);
+          tc::tmem_st8(t_a + 8 * c, w);
+        }
       }
       tc::tmem_st_wait();
     }
     // ---- four layers
-#pragma unroll 1
+#pragma unroll
     for (int layer = 0; layer < 4; ++layer) {
       tc::tc_fence_before();
-      if (wg_sync_or(wg, !ok)) goto teardown;
-      if (row == 0) {
+      if (wg_sync_or<PT>(wg, !ok)) {
+        ok = false;
+        goto teardown;
+      }
+      if (lead) {
         tc::tc_fence_after();
         const uint32_t w_addr = layer == 0 ? w1_addr : layer == 1 ? w2_addr : layer == 2 ? w3_addr : w4_addr;
         if (F8 && layer > 0) {
@@ -434,53 +463,65 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
       }
       if (layer == 0) {   // next tile's inputs, in flight during this tile's layers
         view = tile_view<MULTI>(a, tile + stride);
-        pt = load_point(view, view.first + row);
+        pt = load_point<H>(view, view.first + row, h);
       }
-      // one warp sleeps on the barrier; the other three wait at the named
-      // barrier, which costs them no issue slots
-      if (row < 32) ok = tc::mbar_wait_sleep(my_bar, phase, kWaitCycles);
+      // every warp sleeps on the mbarrier until the products land (no
+      // further barrier hop); an expired wait is OR-reduced at the next
+      // named barrier, where the whole pipeline leaves together
+      ok = tc::mbar_wait_sleep(my_bar, phase, kWaitCycles) && ok;
       phase ^= 1u;
-      tc::tc_fence_before();
-      ok = !wg_sync_or(wg, !ok);
       tc::tc_fence_after();
-      if (F8 && layer < 3) {
-        // y = acc * 2^-s_l + b_l (exactly acc for layer 1), ReLU, E4M3
-        const float inv = epi[kF8Inv + layer];
+      if (layer < 3) {
+        const float inv = F8 ? epi[kF8Inv + layer] : 1.0f;
         const float4 *bl = reinterpret_cast<const float4 *>(epi + kF8Bias + 64 * layer);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float acc[32];
-          tc::tmem_ld16(t_d + 32 * half, acc);
-          tc::tmem_ld16(t_d + 32 * half + 16, acc + 16);
-          tc::tmem_ld_wait();
-          uint32_t w[8];
+        for (int cc = 0; cc < CH; ++cc) {
+          const int chunk = h * CH + cc;             // D columns [32 chunk, 32 chunk + 32)
+          if (F8) {
+            // y = acc * 2^-s_l + b_l (exactly acc for layer 1), ReLU, E4M3;
+            // 16 columns of D become 4 columns of A
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float4 b = bl[8 * half + k];
-            w[k] = tc::pack4_e4m3_relu(fmaf(acc[4 * k], inv, b.x), fmaf(acc[4 * k + 1], inv, b.y),
-                                       fmaf(acc[4 * k + 2], inv, b.z), fmaf(acc[4 * k + 3], inv, b.w));
+            for (int q = 0; q < 2; ++q) {
+              float acc[16];
+              tc::tmem_ld16(t_d + 32 * chunk + 16 * q, acc);
+              tc::tmem_ld_wait();
+              uint32_t w[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float4 b = bl[8 * chunk + 4 * q + k];
+                w[k] = tc::pack4_e4m3_relu(fmaf(acc[4 * k], inv, b.x), fmaf(acc[4 * k + 1], inv, b.y),
+                                           fmaf(acc[4 * k + 2], inv, b.z), fmaf(acc[4 * k + 3], inv, b.w));
+              }
+              tc::tmem_st4(t_a + 8 * chunk + 4 * q, w);
+            }
           }
-          tc::tmem_st8(t_a + 8 * half, w);
         }
-        tc::tmem_st_wait();
-      } else if (layer < 3) {
+        if (!F8) {
+          // all of this thread's D columns in flight at once, one wait
+          float acc[32 * CH];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float acc[32];
-          tc::tmem_ld16(t_d + 32 * half, acc);
-          tc::tmem_ld16(t_d + 32 * half + 16, acc + 16);
+          for (int cc = 0; cc < CH; ++cc) {
+            tc::tmem_ld16(t_d + 32 * (h * CH + cc), acc + 32 * cc);
+            tc::tmem_ld16(t_d + 32 * (h * CH + cc) + 16, acc + 32 * cc + 16);
+          }
           tc::tmem_ld_wait();
-          uint32_t w[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) w[k] = tc::pack2_relu<F16>(acc[2 * k], acc[2 * k + 1]);
-          tc::tmem_st8(t_a + 16 * half, w);
-          tc::tmem_st8(t_a + 16 * half + 8, w + 8);
+          for (int cc = 0; cc < CH; ++cc) {
+            const int chunk = h * CH + cc;
+            uint32_t w[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) w[k] = tc::pack2_relu<F16>(acc[32 * cc + 2 * k], acc[32 * cc + 2 * k + 1]);
+            tc::tmem_st8(t_a + 16 * chunk, w);
+            tc::tmem_st8(t_a + 16 * chunk + 8, w + 8);
+          }
         }
-        // constant-one column (bias of layers 2-4) and zero padding, K = 64..79
-        uint32_t w[8] = {one16, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        tc::tmem_st8(t_a + 32, w);
+        if (!F8 && (H == 1 || h == H - 1)) {
+          // constant-one column (bias of layers 2-4) and zero padding, K = 64..79
+          uint32_t w[8] = {one16, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+          tc::tmem_st8(t_a + 32, w);
+        }
         tc::tmem_st_wait();
-      } else {
+      } else if (H == 1 || h == 0) {
         float y[16];
         tc::tmem_ld16(t_d, y);
         tc::tmem_ld_wait();
@@ -494,10 +535,12 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
           if (mat < 0) {
             c4[0] = c4[1] = c4[2] = c4[3] = __int_as_float(0x7FC00000);
           } else {
+            // inverse of Eq. 9; exp(y) - 1 loses only absolute precision
+            // near y = 0, where S itself is ~0
             c4[0] = fmaxf(0.0f, y[0]);
             c4[1] = fmaxf(0.0f, y[1]);
-            c4[2] = fmaxf(0.0f, expm1f(y[2]) * (1.0f / kSpecK));
-            c4[3] = fmaxf(0.0f, expm1f(y[3]) * (1.0f / kSpecK));
+            c4[2] = fmaxf(0.0f, (__expf(y[2]) - 1.0f) * (1.0f / kSpecK));
+            c4[3] = fmaxf(0.0f, (__expf(y[3]) - 1.0f) * (1.0f / kSpecK));
           }
           if (out_comps) reinterpret_cast<float4 *>(out_comps)[p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
           const float4 *al = reinterpret_cast<const float4 *>(alb + (mat < 0 ? 0 : mat) * 12);
@@ -510,6 +553,7 @@ __global__ void __launch_bounds__(kTile * WG, 4 / WG) decoder_tc_kernel(const Tc
     }
   }
 
+  ok = !wg_sync_or<PT>(wg, !ok);   // one verdict per pipeline
 teardown:
   if (!ok) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
@@ -704,31 +748,35 @@ __global__ void __launch_bounds__(128, 1) selftest_f8_kernel(const float *__rest
   }
 }
 
-template <int PR, int WG, bool MULTI>
+template <int PR, int WG, int H, bool MULTI>
 const void *kernel_ptr() {
-  return reinterpret_cast<const void *>(decoder_tc_kernel<PR, WG, MULTI>);
+  return reinterpret_cast<const void *>(decoder_tc_kernel<PR, WG, H, MULTI>);
 }
 
-// Supported tile pipelines per CTA: 1, 2 or 4 (128 tensor-memory columns each).
+// Supported shapes: 1, 2 or 4 tile pipelines per CTA (128 tensor-memory
+// columns each) of one warpgroup, or 1 or 2 pipelines of two warpgroups.
 int norm_wg(int wg) { return wg == 2 || wg == 4 ? wg : 1; }
+int norm_h(int h, int wg) { return (h == 2 && wg <= 2) ? 2 : 1; }
 
 template <int PR, bool MULTI>
-const void *pick_kernel_pm(int wg) {
-  return wg == 1 ? kernel_ptr<PR, 1, MULTI>() : wg == 2 ? kernel_ptr<PR, 2, MULTI>() : kernel_ptr<PR, 4, MULTI>();
+const void *pick_kernel_pm(int wg, int h) {
+  if (h == 2) return wg == 1 ? kernel_ptr<PR, 1, 2, MULTI>() : kernel_ptr<PR, 2, 2, MULTI>();
+  return wg == 1 ? kernel_ptr<PR, 1, 1, MULTI>() : wg == 2 ? kernel_ptr<PR, 2, 1, MULTI>()
+                                                           : kernel_ptr<PR, 4, 1, MULTI>();
 }
 template <bool MULTI>
-const void *pick_kernel_m(int pr, int wg) {
-  return pr == kPrF16 ? pick_kernel_pm<kPrF16, MULTI>(wg)
-                      : pr == kPrE4M3 ? pick_kernel_pm<kPrE4M3, MULTI>(wg) : pick_kernel_pm<kPrBF16, MULTI>(wg);
+const void *pick_kernel_m(int pr, int wg, int h) {
+  return pr == kPrF16 ? pick_kernel_pm<kPrF16, MULTI>(wg, h)
+                      : pr == kPrE4M3 ? pick_kernel_pm<kPrE4M3, MULTI>(wg, h) : pick_kernel_pm<kPrBF16, MULTI>(wg, h);
 }
-const void *pick_kernel(int pr, int wg, bool multi = false) {
-  return multi ? pick_kernel_m<true>(pr, wg) : pick_kernel_m<false>(pr, wg);
+const void *pick_kernel(int pr, int wg, int h, bool multi = false) {
+  return multi ? pick_kernel_m<true>(pr, wg, h) : pick_kernel_m<false>(pr, wg, h);
 }
 
 // CTAs of the decoder that fit on one SM, counted from the kernel's
 // registers (allocated per warp in units of 8), its shared memory (plus the
 // 1 KB the driver reserves per CTA) and the 512 tensor-memory columns.
-int tc_resident_ctas(const void *fn, size_t smem, int wg) {
+int tc_resident_ctas(const void *fn, size_t smem, int wg, int h) {
   int dev = 0, smem_sm = 0, regs_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -742,7 +790,7 @@ int tc_resident_ctas(const void *fn, size_t smem, int wg) {
   }
   cudaGetLastError();
   const int by_smem = (int)(smem_sm / (smem + static_smem + 1024));
-  const int by_regs = regs_sm / (((regs + 7) & ~7) * kTile * wg);
+  const int by_regs = regs_sm / (((regs + 7) & ~7) * kTile * wg * h);
   const int by_tmem = 512 / (int)(kColsPerTile * wg);
   int occ = by_smem < by_regs ? by_smem : by_regs;
   if (occ > by_tmem) occ = by_tmem;
@@ -782,24 +830,25 @@ int tc_default_ctas_per_sm(int n_mat, int precision) {
   if (k1 < 0) return 1;
   const int wg = 1;
   const int pr = prec_code(precision);
-  const void *fn = pick_kernel(pr, wg, false);
+  const void *fn = pick_kernel(pr, wg, 1, false);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  return tc_resident_ctas(fn, tc_smem_bytes(n_mat, k1, pr == kPrE4M3), wg);
+  return tc_resident_ctas(fn, tc_smem_bytes(n_mat, k1, pr == kPrE4M3), wg, 1);
 }
 
 static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count, int ctas_per_sm, int warpgroups,
-                             cudaStream_t s) {
+                             int tile_wgs, cudaStream_t s) {
   const int pr = prec_code(precision);
   const int wg = norm_wg(warpgroups);
+  const int h = norm_h(tile_wgs, wg);
   const size_t smem = tc_smem_bytes(a.n_mat, a.k1, pr == kPrE4M3);
-  const void *fn = pick_kernel(pr, wg, multi);
-  static bool attr_set[3][5][2] = {};
-  if (!attr_set[pr][wg][multi]) {
+  const void *fn = pick_kernel(pr, wg, h, multi);
+  static bool attr_set[3][5][3][2] = {};
+  if (!attr_set[pr][wg][h][multi]) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set[pr][wg][multi] = true;
+    attr_set[pr][wg][h][multi] = true;
   }
-  const int resident = tc_resident_ctas(fn, smem, wg);
+  const int resident = tc_resident_ctas(fn, smem, wg, h);
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : resident;
   if (per_sm > resident) per_sm = resident;
   int64_t grid = (int64_t)sm_count * per_sm;
@@ -807,12 +856,12 @@ static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count,
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   void *args[] = {&a};
-  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kTile * wg), args, smem, s);
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kTile * wg * h), args, smem, s);
 }
 
 cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,
                               float *comps, int *status, int sm_count, int ctas_per_sm, int warpgroups,
-                              cudaStream_t s) {
+                              int tile_wgs, cudaStream_t s) {
   const int k1 = tc_k1(n_mat);
   if (k1 < 0) return cudaErrorInvalidValue;
   TcArgs a = {};
@@ -830,14 +879,14 @@ cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_m
   a.rgb = rgb;
   a.comps = comps;
   a.status = status;
-  return launch_tc(a, false, precision, sm_count, ctas_per_sm, warpgroups, s);
+  return launch_tc(a, false, precision, sm_count, ctas_per_sm, warpgroups, tile_wgs, s);
 }
 
 int64_t tc_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 
 cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_tile0, int n_segs, int64_t n_tiles,
                                        const void *blob, int n_mat, int precision, int *status, int sm_count,
-                                       int ctas_per_sm, int warpgroups, cudaStream_t s) {
+                                       int ctas_per_sm, int warpgroups, int tile_wgs, cudaStream_t s) {
   const int k1 = tc_k1(n_mat);
   if (k1 < 0) return cudaErrorInvalidValue;
   TcArgs a = {};
@@ -849,7 +898,7 @@ cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_t
   a.segs = segs;
   a.seg_tile0 = seg_tile0;
   a.n_segs = n_segs;
-  return launch_tc(a, true, precision, sm_count, ctas_per_sm, warpgroups, s);
+  return launch_tc(a, true, precision, sm_count, ctas_per_sm, warpgroups, tile_wgs, s);
 }
 
 cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, int a_in_tmem, float *d, int *status,

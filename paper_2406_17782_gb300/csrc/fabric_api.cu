@@ -303,6 +303,24 @@ fabric_status fabric_set_launch_config(fabric_ctx *ctx, int decoder_ctas_per_sm,
   return FABRIC_OK;
 }
 
+fabric_status fabric_set_train_loss(fabric_ctx *ctx, fabric_loss loss) {
+  if (!ctx) return FABRIC_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (loss != FABRIC_LOSS_EQ11 && loss != FABRIC_LOSS_RENDERED)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "unknown loss %d", (int)loss);
+  ctx->loss_mode = (int)loss;
+  return FABRIC_OK;
+}
+
+fabric_status fabric_set_decoder_tile_warpgroups(fabric_ctx *ctx, int warpgroups_per_tile) {
+  if (!ctx) return FABRIC_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (warpgroups_per_tile < 0 || warpgroups_per_tile > 2)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "warpgroups per tile in 0..2");
+  ctx->tc_tile_wgs = warpgroups_per_tile;
+  return FABRIC_OK;
+}
+
 fabric_status fabric_sync_status(fabric_ctx *ctx, void *stream) {
   FAB_CHECK_CTX(ctx);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -538,7 +556,7 @@ fabric_status fabric_shade_neural_prepared(fabric_ctx *ctx, const fabric_gbuffer
   }
   FAB_CUDA(ctx,
            launch_decoder_tc(*g, ctx->d_blob, ctx->n_mat, (int)prec, rgb_dev, comps_dev, ctx->d_status, ctx->sm_count,
-                             ctx->tc_ctas_per_sm, ctx->tc_warpgroups, s),
+                             ctx->tc_ctas_per_sm, ctx->tc_warpgroups, ctx->tc_tile_wgs, s),
            "tensor-core decoder launch");
   return FABRIC_OK;
 }

@@ -107,7 +107,8 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   FAB_CUDA(ctx, launch_material_features(ctx->d_train_raw, M, feats, s), "features");
   FAB_CUDA(ctx, launch_encoder_feats(feats, M, ctx->d_enc, z, acts, s), "encoder forward");
   FAB_CUDA(ctx,
-           launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, grad, dz, loss, dwork, ctx->sm_count,
+           launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, ctx->loss_mode, grad, dz, loss, dwork,
+                                   ctx->sm_count,
                                    ctx->d_status, s),
            "decoder forward/backward");
   FAB_CUDA(ctx, launch_encoder_backward(feats, M, ctx->d_enc, acts, dz, grad + kDecParams, ework, s),
@@ -154,7 +155,7 @@ fabric_status fabric_decoder_backward(fabric_ctx *ctx, const fabric_gbuffer *g, 
   void *work = scratch(ctx, decoder_backward_work_bytes(g->n, ctx->sm_count));
   if (!work) return fail(ctx, FABRIC_ERR_OOM, "scratch");
   FAB_CUDA(ctx,
-           launch_decoder_backward(*g, latents_dev, n_lat, dec_dev, dy_dev, nullptr, ddec_dev, dlatents_dev, nullptr,
+           launch_decoder_backward(*g, latents_dev, n_lat, dec_dev, dy_dev, nullptr, 0, ddec_dev, dlatents_dev, nullptr,
                                    work, ctx->sm_count, ctx->d_status, s),
            "decoder backward");
   return FABRIC_OK;

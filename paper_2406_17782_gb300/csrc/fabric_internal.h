@@ -123,6 +123,8 @@ struct fabric_ctx {
   // launch configuration (0 = automatic)
   int tc_ctas_per_sm = 0;
   int tc_warpgroups = 0;
+  int tc_tile_wgs = 0;
+  int loss_mode = 0;          // FABRIC_LOSS_EQ11 or FABRIC_LOSS_RENDERED        // warpgroups per decoder tile pipeline (0 or 1: one, 2: two)
   int ref_lanes = 0;
 };
 
@@ -149,12 +151,12 @@ cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMate
                            int precision, void *blob, cudaStream_t s);
 int tc_default_ctas_per_sm(int n_mat, int precision);
 cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,
-                              float *comps, int *status, int sm_count, int ctas_per_sm, int warpgroups,
+                              float *comps, int *status, int sm_count, int ctas_per_sm, int warpgroups, int tile_wgs,
                               cudaStream_t s);
 int64_t tc_tiles(int64_t n);
 cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_tile0, int n_segs, int64_t n_tiles,
                                        const void *blob, int n_mat, int precision, int *status, int sm_count,
-                                       int ctas_per_sm, int warpgroups, cudaStream_t s);
+                                       int ctas_per_sm, int warpgroups, int tile_wgs, cudaStream_t s);
 cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, int a_in_tmem, float *d, int *status,
                                 cudaStream_t s);
 cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *z, cudaStream_t s);
@@ -167,7 +169,7 @@ cudaError_t launch_material_features(const fabric_material *raw, int n, float *f
 cudaError_t launch_decoder_raw(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                                float *y_raw, int *status, cudaStream_t s);
 cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
-                                    const float *dy, const float *target, float *ddec, float *dlat,
+                                    const float *dy, const float *target, int loss_mode, float *ddec, float *dlat,
                                     double *loss, void *work, int sm_count, int *status, cudaStream_t s);
 size_t decoder_backward_work_bytes(int64_t n, int sm_count);
 cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, int64_t step,

@@ -71,7 +71,7 @@ fabric_status fabric_plan_shade(fabric_ctx *ctx, const fabric_plan *plan, fabric
   if (plan->n_tiles == 0) return FABRIC_OK;
   const cudaError_t e = launch_decoder_tc_segments(plan->d_segs, plan->d_tile0, plan->n_segs, plan->n_tiles,
                                                    ctx->d_blob, ctx->n_mat, (int)prec, ctx->d_status, ctx->sm_count,
-                                                   ctx->tc_ctas_per_sm, ctx->tc_warpgroups,
+                                                   ctx->tc_ctas_per_sm, ctx->tc_warpgroups, ctx->tc_tile_wgs,
                                                    static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batched decoder launch");
   return FABRIC_OK;

@@ -55,7 +55,7 @@ extern "C" fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabr
   cudaError_t e = launch_tc_pack(ctx->d_dec, latents_dev, ctx->d_mat, ctx->n_mat, (int)prec, blob, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pack");
   e = launch_decoder_tc(*g, blob, ctx->n_mat, (int)prec, rgb_dev, comps_dev, ctx->d_status, ctx->sm_count,
-                        ctx->tc_ctas_per_sm, ctx->tc_warpgroups, s);
+                        ctx->tc_ctas_per_sm, ctx->tc_warpgroups, ctx->tc_tile_wgs, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core decoder launch");
   return FABRIC_OK;
 }

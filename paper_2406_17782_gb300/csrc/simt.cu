@@ -13,6 +13,7 @@ namespace {
 
 constexpr float kLambdaS = 0.4f;      // Eq. 11
 constexpr float kLambdaC = 0.1f;
+constexpr float kYClamp = 12.0f;      // head pre-activation limit of the rendered-space loss
 constexpr float kLeaky = 0.01f;       // encoder residual-block activation slope
 
 // ---------------------------------------------------------------------------
@@ -134,6 +135,7 @@ struct BwdArgs {
   const float *dec;
   const float *dy;       // [n][4] or null
   const float *target;   // [n][4] or null
+  int loss_mode;         // FABRIC_LOSS_EQ11 or FABRIC_LOSS_RENDERED
   float inv_batch;       // 1/B for the loss
   float *partial;        // [grid][kDecParams]
   double *loss_partial;  // [grid]
@@ -255,7 +257,21 @@ __global__ void __launch_bounds__(kBwdThreads) decoder_bwd_kernel(const BwdArgs 
       const bool valid = X[kDecIn * kRS + r] > 0.0f;
       float d = 0.0f;
       if (valid) {
-        if (a.target) {
+        if (a.target && a.loss_mode == FABRIC_LOSS_RENDERED) {
+          // ((c_hat - c) max(<wi.n_s>, 0))^2, c_hat = y (C) or (exp(min(y, 12)) - 1) / k (S)
+          const float tg = a.target[4 * p + k];
+          const float wz = fmaxf(a.g.wi[3 * p + 2], 0.0f);
+          const float y = Y[k * kRS + r];
+          float c = y, dc = 1.0f;
+          if (k >= 2) {
+            const float e = expf(fminf(y, kYClamp));
+            c = (e - 1.0f) * (1.0f / kSpecK);
+            dc = y < kYClamp ? e * (1.0f / kSpecK) : 0.0f;
+          }
+          const float diff = (c - tg) * wz;
+          d = 2.0f * diff * wz * dc * a.inv_batch;
+          loss_acc += (double)diff * (double)diff * (double)a.inv_batch;
+        } else if (a.target) {
           const float tg = a.target[4 * p + k];
           const float tt = k < 2 ? tg : logf(kSpecK * tg + 1.0f);   // g(x) = ln(k x + 1), Eq. 9
           const float lam = k < 2 ? kLambdaC : kLambdaS;
@@ -598,8 +614,8 @@ size_t decoder_backward_work_bytes(int64_t n, int sm_count) {
 }
 
 cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
-                                    const float *dy, const float *target, float *ddec, float *dlat, double *loss,
-                                    void *work, int sm_count, int *status, cudaStream_t s) {
+                                    const float *dy, const float *target, int loss_mode, float *ddec, float *dlat,
+                                    double *loss, void *work, int sm_count, int *status, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(decoder_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -621,6 +637,7 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
   a.dec = dec;
   a.dy = dy;
   a.target = target;
+  a.loss_mode = loss_mode;
   a.inv_batch = 1.0f / (float)(g.n > 0 ? g.n : 1);
   a.partial = partial;
   a.loss_partial = loss_part;

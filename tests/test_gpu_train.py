@@ -114,7 +114,8 @@ def test_autograd_functions_against_finite_differences(fab):
         assert abs(fd - an) <= rtol * max(abs(an), 1.0), (which, fd, an)
 
 
-def test_train_steps_match_fp64_oracle(fab):
+@pytest.mark.parametrize("loss_mode", ["eq11", "rendered"])
+def test_train_steps_match_fp64_oracle(fab, loss_mode):
     mats = W.training_materials(2)
     g = batch(1024, len(mats), stream="parity-steps")
     rng = np.random.default_rng(3)
@@ -127,11 +128,16 @@ def test_train_steps_match_fp64_oracle(fab):
     lr = 1e-3
     state = {}
     od, oe = dec.astype(np.float64), enc.astype(np.float64)
-    for step in range(3):
-        loss = fab.train_step(gd, tt, lr)
-        fab.sync_status()
-        lo, od, oe = M.train_step(od, oe, state, mats, g["material"], g, target.astype(np.float64), lr)
-        assert abs(float(loss.item()) - lo) <= 1e-5 * abs(lo), (step, float(loss.item()), lo)
+    fab.set_train_loss(loss_mode)
+    try:
+        for step in range(3):
+            loss = fab.train_step(gd, tt, lr)
+            fab.sync_status()
+            lo, od, oe = M.train_step(od, oe, state, mats, g["material"], g, target.astype(np.float64), lr,
+                                      loss_mode=loss_mode)
+            assert abs(float(loss.item()) - lo) <= 1e-5 * abs(lo), (step, float(loss.item()), lo)
+    finally:
+        fab.set_train_loss("eq11")
     d, e = fab.get_params()
     assert np.max(np.abs(d - od)) < 1e-4
     assert np.max(np.abs(e - oe)) < 1e-4
