@@ -45,7 +45,7 @@ FLOP_PER_POINT = 2 * (39 * 64 + 64 * 64 + 64 * 64 + 64 * 4)      # 21,888 (layer
 BYTES_PER_POINT = 38 + 12                                          # G-buffer record in, RGB out
 # DRAM bytes (read + write) of one FP16 decoder launch on this frame, from the
 # ncu capture summarised in profiles/decoder_tc_1080p_fp16.md (same kernel)
-TRAFFIC_FP16 = 78_853_376 + 5_593_600
+TRAFFIC_FP16 = 78_858_240 + 5_398_784
 WORKLOAD = "1920x1080 G-buffer, 8 weave materials (one per 240-px band), random-init decoder"
 
 
@@ -144,6 +144,19 @@ def oracle_reference_rate(points: int, spp: int = 16):
     t = time.perf_counter()
     oracle.shade_reference(mats, sub, spp, spp, 7, nthreads=0, pixel_index=idx)
     return points / (time.perf_counter() - t)
+
+
+def max_over_ranks(elapsed_ms: float, torch, dist, device) -> float:
+    """The slowest rank's time: every rank gets the MAX over the group."""
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, points_per_rank: int, steps: int, elapsed_ms: float) -> float:
+    """Whole-job points/s: every rank shades its own frame per step (weak
+    scaling, replicas), timed by the slowest rank."""
+    return world * points_per_rank * steps / (elapsed_ms * 1e-3)
 
 
 def run_reference_arm(args, rank: int, world: int):
@@ -254,12 +267,10 @@ def main():
         dist.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
     if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(elapsed_ms, torch, dist, "cuda")
     fab.sync_status()
     ms_step = elapsed_ms / args.steps
-    value = world * N_POINTS * args.steps / (elapsed_ms * 1e-3)
+    value = job_throughput(world, N_POINTS, args.steps, elapsed_ms)
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -318,6 +329,64 @@ def timed(torch, stream, fn, reps):
     return ev0.elapsed_time(ev1) / reps
 
 
+def measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream):
+    """Latent interpolation and extrapolation (Sec. 6.4) with the trained
+    network: for the frame's eight materials with roughness (then height
+    scale) set to 0.2 and 0.8, latents at 0.3 and 0.6 (interpolated) and 0.9
+    (extrapolated) are mixed linearly from the two encoded endpoints and
+    compared, as rendered frames, with the encoder's own latent at that value
+    and with the reference at 1024 spp.  Also the editing latency: encoder
+    plus latent fold and operand packing, per edit of all eight materials."""
+    from paper_2406_17782_gb300 import train as T
+    base = W.frame_materials()
+    g = gbufs[0]
+    wz = g.wi[:, 2]
+    n = g.n * 3
+
+    def rmse(a, b):
+        st = fab.error_stats(a, b, weights=wz, group=3, weight_stride=3).cpu().numpy()
+        return math.sqrt(float(st[0]) / n)
+
+    def with_param(name, val):
+        m = base.copy()
+        m[name][:] = val
+        return m
+
+    out = {}
+    for name in ("alpha", "beta"):
+        z_lo = fab.encode_params(with_param(name, 0.2))
+        z_hi = fab.encode_params(with_param(name, 0.8))
+        rows = []
+        for t in (0.3, 0.6, 0.9):
+            m = with_param(name, t)
+            fab.set_materials(m)
+            gt, _ = fab.shade_reference(g, 32, 32, 0x6721)
+            z_mix = z_lo + (t - 0.2) / 0.6 * (z_hi - z_lo)
+            a, _ = fab.shade_neural(g, z_mix, "fp16")
+            b, _ = fab.shade_neural(g, fab.encode_params(m), "fp16")
+            rows.append({"value": t, "mixed_vs_encoded": rmse(a, b), "mixed_vs_reference": rmse(a, gt),
+                         "encoded_vs_reference": rmse(b, gt)})
+        out[name] = rows
+    fab.set_materials(base)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    arr = base.copy()
+    for _ in range(3):
+        fab.prepare_neural(fab.encode_params(arr), "fp16")
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(100):
+        arr["alpha"][:, 0] = 0.1 + 0.008 * k
+        fab.prepare_neural(fab.encode_params(arr), "fp16")
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fab.sync_status()
+    out["edit_ms"] = ev0.elapsed_time(ev1) / 100
+    out["edit_note"] = ("host upload of 8 material records + encoder + latent fold and operand packing, "
+                        "per edit, CUDA events")
+    out["metric"] = "RMSE of the rendered 1080p frame (as in the quality section)"
+    return out
+
+
 def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     """Train the decoder and encoder with the library's kernels on data from
     the reference kernel (once with the paper's Eq. 11 loss, once with the
@@ -337,7 +406,7 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     runs = {}
     ladder = None
     for loss in ("eq11", "rendered"):
-        fab.set_params(W.decoder_init(), W.encoder_init())
+        fab.set_params(W.decoder_init(weight_bound="small"), W.encoder_init(weight_bound="small"))
         fab.set_train_loss(loss)
         t0 = time.time()
         T.train(fab, tm, g_tr, target, args.quality_steps, 65536, args.quality_lr, log_every=1000, verbose=False)
@@ -372,7 +441,9 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
             "train_seconds": t_train,
         }
     del g_tr, target
+    interp = measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream)
     return {
+        "interpolation": interp,
         "metric": "RMSE of the 1080p frame, f_P <wi.n> per RGB channel (unit directional light), "
                   "against the reference at 1024 spp",
         "gt_rms": gt_rms,

@@ -1,0 +1,74 @@
+"""Run one kernel of the library a few times on the standard 1080p workload,
+for profilers (ncu) and quick timing:
+
+  python -m paper_2406_17782_gb300.profile_case reference [--spp 16] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case decoder [--precision fp16] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case train [--batch 65536] [--reps 3]
+
+The workload is the 1920 x 1080 G-buffer of eight weave materials (random-init
+networks); the training case uses a batch of queries over 256 training
+materials with targets from the reference kernel at 4 x 4 samples.  Prints the
+mean time per launch (CUDA events) as one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+from .api import Fabric, GBuffer  # noqa: E402
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["reference", "decoder", "train"])
+    ap.add_argument("--spp", type=int, default=16, help="samples per axis (reference)")
+    ap.add_argument("--precision", default="fp16")
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args(argv)
+    fab = Fabric(0)
+    mats = W.frame_materials()
+    fab.set_materials(mats)
+    fab.set_params(W.decoder_init(), W.encoder_init())
+    if args.case == "train":
+        tm = W.training_materials(32)
+        q = W.training_queries(args.batch, len(tm), stream="profile-train")
+        g = GBuffer.from_numpy(q)
+        target = torch.empty((args.batch, 4), dtype=torch.float32, device=fab.device)
+        fab.set_materials(tm)
+        fab.shade_reference(g, 4, 4, 3, out_comps=target)
+        fab.set_train_materials(tm)
+        fn = lambda: fab.train_step(g, target, 1e-3)
+    else:
+        g = GBuffer.from_numpy(W.frame_gbuffer())
+        rgb = torch.empty((g.n, 3), dtype=torch.float32, device=fab.device)
+        if args.case == "reference":
+            fn = lambda: fab.shade_reference(g, args.spp, args.spp, 11, out_rgb=rgb)
+        else:
+            fab.prepare_neural(fab.encode_params(mats), args.precision)
+            fn = lambda: fab.shade_neural_prepared(g, args.precision, out_rgb=rgb)
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    fab.sync_status()
+    print(json.dumps({"case": args.case, "ms_per_launch": e0.elapsed_time(e1) / args.reps, "reps": args.reps,
+                      "points": g.n}))
+
+
+if __name__ == "__main__":
+    main()

@@ -7,11 +7,13 @@ Data: `--queries` training queries over 32 parameter sets x 8 weaves (256
 materials), half frame-like and half drawn from the paper's Table 2; targets
 are the four components of the reference integral at 64 x 32 = 2048 samples
 (the paper's data sample count).  Training: Adam, batch 65536, learning rate
-1e-3 decayed by cosine to 1e-5, Eq. 11 loss, all in the library's kernels
+1e-3 decayed by cosine to 1e-5, all in the library's kernels
 (fabric_train_step); the dataset is shuffled once per epoch and batches are
-contiguous slices of it.  Evaluation: RMSE over the linear RGB of the
-1920 x 1080 frame of eight weaves against the reference integral at
-32 x 32 = 1024 samples (independent seed).
+contiguous slices of it.  Initial weights U(+-1/sqrt(fan_in)); loss Eq. 11
+(--loss eq11) or, by default, its rendered-space option.  Evaluation: RMSE
+of the 1920 x 1080 frame of eight weaves as lit by a unit directional light
+(f_P <wi.n_s> per RGB channel) against the reference integral at 32 x 32 =
+1024 samples (independent seed).
 """
 from __future__ import annotations
 
@@ -132,9 +134,11 @@ def main(argv=None):
     ap.add_argument("--spp", type=int, nargs=2, default=[64, 32])
     ap.add_argument("--frame-share", type=float, default=0.5)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--loss", default="rendered", choices=["eq11", "rendered"])
     args = ap.parse_args(argv)
     fab = Fabric(0)
-    fab.set_params(W.decoder_init(), W.encoder_init())
+    fab.set_params(W.decoder_init(weight_bound="small"), W.encoder_init(weight_bound="small"))
+    fab.set_train_loss(args.loss)
     mats = W.training_materials(32)
     t = time.time()
     g, target = generate_dataset(fab, mats, args.queries, tuple(args.spp), frame_share=args.frame_share)

@@ -286,14 +286,17 @@ def batched_4k(config: int = 5, width: int = 3840, height: int = 2160, tile: int
     return segs, sum(len(s["u"]) for s in segs)
 
 
-def init_params(n: int, fan_ins, sizes, seed: int) -> np.ndarray:
-    """Uniform initialisation: weights U(+-sqrt(6 / fan_in)), biases
-    U(+-1/sqrt(fan_in)); `sizes` lists (n_weights, n_bias) per layer in the
-    flat order, `fan_ins` the layer fan-ins."""
+def init_params(n: int, fan_ins, sizes, seed: int, weight_bound: str = "he") -> np.ndarray:
+    """Uniform initialisation: weights U(+-sqrt(6 / fan_in)) ("he") or
+    U(+-1/sqrt(fan_in)) ("small", the default of common deep-learning
+    libraries' linear layers), biases U(+-1/sqrt(fan_in)); `sizes` lists
+    (n_weights, n_bias) per layer in the flat order, `fan_ins` the layer
+    fan-ins."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE, seed])))
     out = []
     for (nw, nb), fi in zip(sizes, fan_ins):
-        out.append(rng.uniform(-math.sqrt(6.0 / fi), math.sqrt(6.0 / fi), nw))
+        bound = math.sqrt(6.0 / fi) if weight_bound == "he" else 1.0 / math.sqrt(fi)
+        out.append(rng.uniform(-bound, bound, nw))
         out.append(rng.uniform(-1.0 / math.sqrt(fi), 1.0 / math.sqrt(fi), nb))
     flat = np.concatenate(out).astype(np.float32)
     assert len(flat) == n
@@ -304,14 +307,16 @@ DEC_LAYERS = [(64, 71), (64, 64), (64, 64), (4, 64)]       # (out, in)
 ENC_LAYERS = [(128, 14), (128, 128), (32, 128)]
 
 
-def decoder_init(seed: int = 3) -> np.ndarray:
+def decoder_init(seed: int = 3, weight_bound: str = "he") -> np.ndarray:
+    """Random decoder parameters: "he" for the parity tests and the timed
+    frame, "small" as the starting point of training."""
     return init_params(sum(o * i + o for o, i in DEC_LAYERS), [i for _, i in DEC_LAYERS],
-                       [(o * i, o) for o, i in DEC_LAYERS], seed)
+                       [(o * i, o) for o, i in DEC_LAYERS], seed, weight_bound)
 
 
-def encoder_init(seed: int = 4) -> np.ndarray:
+def encoder_init(seed: int = 4, weight_bound: str = "he") -> np.ndarray:
     return init_params(sum(o * i + o for o, i in ENC_LAYERS), [i for _, i in ENC_LAYERS],
-                       [(o * i, o) for o, i in ENC_LAYERS], seed)
+                       [(o * i, o) for o, i in ENC_LAYERS], seed, weight_bound)
 
 
 def random_latents(n_mat: int, seed: int = 5, scale: float = 1.0) -> np.ndarray:
