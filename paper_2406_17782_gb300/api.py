@@ -76,11 +76,12 @@ class GBuffer:
         return sum(getattr(self, k).numel() * getattr(self, k).element_size()
                    for k in ("u", "v", "radius", "wi", "wo", "material"))
 
-    def struct(self) -> FabricGBuffer:
+    def struct(self, host: bool = False) -> FabricGBuffer:
         for k in ("u", "v", "radius", "wi", "wo", "material"):
             t = getattr(self, k)
-            if not t.is_cuda or not t.is_contiguous():
-                raise ValueError(f"G-buffer field {k} must be a contiguous CUDA tensor")
+            if t.is_cuda == host or not t.is_contiguous():
+                where = "host" if host else "CUDA"
+                raise ValueError(f"G-buffer field {k} must be a contiguous {where} tensor")
         return FabricGBuffer(self.u.data_ptr(), self.v.data_ptr(), self.radius.data_ptr(), self.wi.data_ptr(),
                              self.wo.data_ptr(), self.material.data_ptr(), self.n)
 
@@ -212,6 +213,20 @@ class Fabric:
         self._check(self.lib.fabric_shade_neural_prepared(self.h, ctypes.byref(gs), _abi.PREC[precision],
                                                           _ptr(rgb), _ptr(cp), _stream_handle(stream)))
         return rgb, cp
+
+    def shade_neural_host(self, g: GBuffer, precision: str = "fp16", out_rgb=None, out_comps=None,
+                          chunk_points: int = 0, stream=None):
+        """Draw a G-buffer held in host memory (CPU tensors, ideally pinned)
+        into host outputs, with chunked, overlapped copies and decoder
+        launches (fabric_shade_neural_host).  Asynchronous on `stream`."""
+        rgb = out_rgb if out_rgb is not None else torch.empty((g.n, 3), dtype=torch.float32).pin_memory()
+        for t in (rgb, out_comps):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("shade_neural_host writes contiguous host tensors")
+        gs = g.struct(host=True)
+        self._check(self.lib.fabric_shade_neural_host(self.h, ctypes.byref(gs), _abi.PREC[precision], _ptr(rgb),
+                                                      _ptr(out_comps), int(chunk_points), _stream_handle(stream)))
+        return rgb, out_comps
 
     def plan(self, segments) -> "Plan":
         """Batched draw over (GBuffer, rgb_out, comps_out or None) triples."""

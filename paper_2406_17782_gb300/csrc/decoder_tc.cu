@@ -855,8 +855,20 @@ static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count,
   const int64_t need = (a.n_tiles + wg - 1) / wg;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
+  // Pad the dynamic shared memory so that no SM can take more than per_sm
+  // CTAs: one more would wait in tcgen05.alloc until a resident CTA (which
+  // runs to the end of the grid's work) frees its tensor memory.
+  size_t launch_smem = smem;
+  {
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const size_t floor_smem = (size_t)smem_sm / (size_t)(per_sm + 1) - 1024 + 1;   // (per_sm + 1) CTAs overflow
+    const size_t roomy = (size_t)smem_sm / (size_t)per_sm - 1024;                     // per_sm CTAs still fit
+    if (floor_smem > launch_smem && floor_smem <= roomy && floor_smem <= 200 * 1024) launch_smem = floor_smem;
+  }
   void *args[] = {&a};
-  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kTile * wg * h), args, smem, s);
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kTile * wg * h), args, launch_smem, s);
 }
 
 cudaError_t launch_decoder_tc(const fabric_gbuffer &g, const void *blob, int n_mat, int precision, float *rgb,

@@ -279,6 +279,7 @@ void fabric_destroy(fabric_ctx *ctx) {
   cudaFree(ctx->d_enc_raw);
   cudaFree(ctx->d_blob);
   cudaFree(ctx->d_err_work);
+  host_pipeline_release(ctx);
   delete ctx;
 }
 

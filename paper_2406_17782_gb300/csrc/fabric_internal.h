@@ -123,9 +123,17 @@ struct fabric_ctx {
   // launch configuration (0 = automatic)
   int tc_ctas_per_sm = 0;
   int tc_warpgroups = 0;
-  int tc_tile_wgs = 0;
-  int loss_mode = 0;          // FABRIC_LOSS_EQ11 or FABRIC_LOSS_RENDERED        // warpgroups per decoder tile pipeline (0 or 1: one, 2: two)
+  int tc_tile_wgs = 0;         // warpgroups per decoder tile pipeline (0 or 1: one, 2: two)
+  int loss_mode = 0;           // FABRIC_LOSS_EQ11 or FABRIC_LOSS_RENDERED
   int ref_lanes = 0;
+  // host-buffer pipeline (fabric_shade_neural_host): per-slot stream, event
+  // and device staging for one chunk's G-buffer and outputs
+  static constexpr int kHostSlots = 3;
+  cudaStream_t host_stream[kHostSlots] = {};
+  cudaEvent_t host_done[kHostSlots] = {};
+  cudaEvent_t host_start = nullptr;
+  void *host_stage = nullptr;   // kHostSlots x host_slot_bytes
+  size_t host_slot_bytes = 0;
 };
 
 namespace fab {
@@ -137,6 +145,8 @@ void *scratch(fabric_ctx *ctx, size_t bytes);
 bool build_material(const fabric_material &m, DevMaterial *out, std::string *why);
 bool check_gbuffer(fabric_ctx *ctx, const fabric_gbuffer *g);
 bool is_aligned16(const void *p);
+// Free the host-pipeline streams, events and staging of a context.
+void host_pipeline_release(fabric_ctx *ctx);
 
 // Launchers implemented in the kernel translation units.
 cudaError_t launch_reference(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, int spp_x, int spp_y,
