@@ -349,20 +349,24 @@ int64_t fabric_plan_points(const fabric_plan *plan);
 void fabric_plan_destroy(fabric_plan *plan);
 
 /*
- * Neural shading of a G-buffer in HOST memory (pinned memory lets the copies
- * overlap; pageable memory works but serialises them), with the prepared
- * state of fabric_prepare_neural for `prec`.  g_host's pointers and
- * rgb_host [n][3] (and comps_host [n][4], or NULL) are host pointers that
- * must stay valid until `stream` has passed this call.  The frame is cut
- * into chunks of chunk_points (0 = 262144; rounded up to a multiple of 128)
- * that cycle through three context-owned device staging slots on their own
- * streams, so that one chunk's upload, the next one's decoder and a third
- * one's download overlap.  Asynchronous on `stream`: the chunks start after
- * the work queued on it, and it waits for all of them.  The staging (about
- * 90 bytes per chunk point per slot) is allocated on first use and grown
- * when a larger chunk is asked for; calls on several streams of one context
- * share the slots and are serialised by them.  Errors as for
- * fabric_shade_neural_prepared.
+ * Neural shading of a G-buffer in HOST memory, with the prepared state of
+ * fabric_prepare_neural for `prec`.  g_host's pointers and rgb_host [n][3]
+ * (and comps_host [n][4], 16-byte aligned, or NULL) are host pointers that
+ * must stay valid until `stream` has passed this call.  Asynchronous on
+ * `stream`.
+ *  - chunk_points = 0 and every buffer page-locked and mapped (as
+ *    cudaHostAlloc gives it): the decoder reads the G-buffer and writes the
+ *    outputs directly over the host link, one launch on `stream`.
+ *  - otherwise: the frame is cut into chunks of chunk_points (0 = 262144;
+ *    rounded up to a multiple of 128) that cycle through three
+ *    context-owned device staging slots on their own streams, so that one
+ *    chunk's upload, the next one's decoder and a third one's download
+ *    overlap (pageable memory works but serialises the copies).  The chunks
+ *    start after the work queued on `stream`, and it waits for all of them.
+ *    The staging (about 90 bytes per chunk point per slot) is allocated on
+ *    first use and grown when a larger chunk is asked for; calls on several
+ *    streams of one context share the slots and are serialised by them.
+ * Errors as for fabric_shade_neural_prepared.
  */
 fabric_status fabric_shade_neural_host(fabric_ctx *ctx, const fabric_gbuffer *g_host, fabric_precision prec,
                                        float *rgb_host, float *comps_host, int64_t chunk_points, void *stream);

@@ -1,10 +1,12 @@
 // host_pipeline.cu -- fabric_shade_neural_host: neural shading of a G-buffer
-// that lives in host memory.  The frame is cut into chunks that cycle through
-// three context-owned device staging slots, each with its own stream, so
-// that the host-to-device copy of one chunk, the decoder on the next and the
-// device-to-host copy of a third overlap (two copy engines and the SMs run
-// at once).  The caller's stream orders the whole call: the slots start
-// after the work already queued on it, and it waits for all of them.
+// that lives in host memory.  When all buffers are mapped page-locked host
+// memory the decoder reads and writes them directly over the host link (one
+// launch on the caller's stream).  Otherwise, or when a chunk size is given,
+// the frame is cut into chunks that cycle through three context-owned device
+// staging slots, each with its own stream, so that the host-to-device copy of
+// one chunk, the decoder on the next and the device-to-host copy of a third
+// overlap; the caller's stream orders the whole call (the slots start after
+// the work already queued on it, and it waits for all of them).
 #include "fabric_internal.h"
 
 namespace {
@@ -60,6 +62,17 @@ fabric_status ensure_slots(fabric_ctx *ctx, int64_t chunk) {
   return FABRIC_OK;
 }
 
+// Device address of host memory that the GPU may read and write directly
+// (page-locked memory mapped into the unified address space), else null.
+void *mapped(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 }  // namespace
 
 void fab::host_pipeline_release(fabric_ctx *ctx) {
@@ -85,14 +98,42 @@ extern "C" fabric_status fabric_shade_neural_host(fabric_ctx *ctx, const fabric_
   if (!g_host->u || !g_host->v || !g_host->radius || !g_host->wi || !g_host->wo || !g_host->material || !rgb_host)
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "a G-buffer field or the rgb output is NULL");
   if (chunk_points < 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "chunk_points < 0");
+  if (comps_host && !is_aligned16(comps_host))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (chunk_points == 0) {
+    // Direct: when every buffer is mapped page-locked memory the decoder
+    // reads the G-buffer and writes its outputs over the host link itself,
+    // in one launch and without staging copies.
+    fabric_gbuffer d;
+    d.u = static_cast<const float *>(mapped(g_host->u));
+    d.v = static_cast<const float *>(mapped(g_host->v));
+    d.radius = static_cast<const float *>(mapped(g_host->radius));
+    d.wi = static_cast<const float *>(mapped(g_host->wi));
+    d.wo = static_cast<const float *>(mapped(g_host->wo));
+    d.material = static_cast<const uint16_t *>(mapped(g_host->material));
+    d.n = g_host->n;
+    float *rgb = static_cast<float *>(mapped(rgb_host));
+    float *comps = comps_host ? static_cast<float *>(mapped(comps_host)) : nullptr;
+    if (d.u && d.v && d.radius && d.wi && d.wo && d.material && rgb && (comps || !comps_host)) {
+      if (prec == FABRIC_PREC_FP32)
+        e = launch_decoder_fp32(d, ctx->d_mat, ctx->n_mat, ctx->prepared_latents, ctx->d_dec, rgb, comps, nullptr,
+                                ctx->d_status, caller);
+      else
+        e = launch_decoder_tc(d, ctx->d_blob, ctx->n_mat, (int)prec, rgb, comps, ctx->d_status, ctx->sm_count,
+                              ctx->tc_ctas_per_sm, ctx->tc_warpgroups, ctx->tc_tile_wgs, caller);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "decoder launch");
+      return FABRIC_OK;
+    }
+  }
   int64_t chunk = chunk_points ? chunk_points : kDefaultChunk;
   chunk = (chunk + 127) / 128 * 128;
   if (chunk > g_host->n) chunk = (g_host->n + 127) / 128 * 128;
   fabric_status st = ensure_slots(ctx, chunk);
   if (st != FABRIC_OK) return st;
   const SlotLayout L = slot_layout(chunk);
-  cudaStream_t caller = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaEventRecord(ctx->host_start, caller);
+  e = cudaEventRecord(ctx->host_start, caller);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host pipeline start");
   for (int k = 0; k < fabric_ctx::kHostSlots; ++k) {
     e = cudaStreamWaitEvent(ctx->host_stream[k], ctx->host_start, 0);

@@ -1,8 +1,9 @@
-"""fabric_shade_neural_host: a G-buffer in host memory, chunked through
-three device staging slots on their own streams, must give exactly the
-outputs of the device-resident call (the same kernels on the same points),
-for ragged sizes, any chunk size, pinned or pageable memory and every
-precision; and it must refuse what it cannot do."""
+"""fabric_shade_neural_host: a G-buffer in host memory, read directly by the
+decoder (mapped page-locked memory) or chunked through three device staging
+slots on their own streams, must give exactly the outputs of the
+device-resident call (the same kernels on the same points), for ragged
+sizes, any chunk size, pinned or pageable memory and every precision; and
+it must refuse what it cannot do."""
 import numpy as np
 import pytest
 import torch
@@ -24,8 +25,12 @@ def frame(fab):
     return lat, host
 
 
+# chunk 0 with page-locked buffers takes the direct path (the decoder reads
+# and writes host memory itself); a chunk size, or pageable memory, the
+# staged three-stream path
 @pytest.mark.parametrize("prec,chunk,pin", [("fp16", 0, True), ("fp16", 1000, True), ("fp16", 65536, False),
-                                            ("bf16", 0, True), ("fp8", 100_000, True), ("fp32", 50_000, True)])
+                                            ("fp16", 0, False), ("bf16", 0, True), ("fp8", 100_000, True),
+                                            ("fp8", 0, True), ("fp32", 50_000, True), ("fp32", 0, True)])
 def test_host_call_equals_device_call(fab, frame, prec, chunk, pin):
     lat, host = frame
     fab.prepare_neural(lat, prec)
