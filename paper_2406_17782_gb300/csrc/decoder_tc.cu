@@ -497,13 +497,11 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
           }
         }
         if (!F8) {
-          // all of this thread's D columns in flight at once, one wait
+          // all of this thread's D columns in flight at once (32 columns per
+          // tcgen05.ld), one wait, 16 columns of A per tcgen05.st
           float acc[32 * CH];
 #pragma unroll
-          for (int cc = 0; cc < CH; ++cc) {
-            tc::tmem_ld16(t_d + 32 * (h * CH + cc), acc + 32 * cc);
-            tc::tmem_ld16(t_d + 32 * (h * CH + cc) + 16, acc + 32 * cc + 16);
-          }
+          for (int cc = 0; cc < CH; ++cc) tc::tmem_ld32(t_d + 32 * (h * CH + cc), acc + 32 * cc);
           tc::tmem_ld_wait();
 #pragma unroll
           for (int cc = 0; cc < CH; ++cc) {
@@ -511,8 +509,7 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
             uint32_t w[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) w[k] = tc::pack2_relu<F16>(acc[32 * cc + 2 * k], acc[32 * cc + 2 * k + 1]);
-            tc::tmem_st8(t_a + 16 * chunk, w);
-            tc::tmem_st8(t_a + 16 * chunk + 8, w + 8);
+            tc::tmem_st16(t_a + 16 * chunk, w);
           }
         }
         if (!F8 && (H == 1 || h == H - 1)) {
@@ -522,8 +519,8 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
         }
         tc::tmem_st_wait();
       } else if (H == 1 || h == 0) {
-        float y[16];
-        tc::tmem_ld16(t_d, y);
+        float y[4];
+        tc::tmem_ld4(t_d, y);
         tc::tmem_ld_wait();
         if (F8) {
           const float inv = epi[kF8Inv + 3];
