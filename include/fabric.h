@@ -55,9 +55,11 @@ typedef enum {
 /*
  * Material record (host memory, 84 bytes, no padding): the shading-model
  * parameters of Table 1 plus the procedural weave of Sec. 5.1.
- *   pattern_id  built-in weave 0..7: plain, 2/1 twill, 3/1 twill, 4/1 satin
+ *   pattern_id  built-in weave 0..11: plain, 2/1 twill, 3/1 twill, 4/1 satin
  *               (warp-faced), 5-harness satin (weft-faced), 2x2 basket,
- *               herringbone, warp rib
+ *               herringbone, warp rib, 4/1 twill, 7/1 twill, 8-harness
+ *               satin (weft-faced), 5-harness satin with doubled picks
+ *               (10 x 5); the encoder's one-hot has 16 slots
  *   twist_deg   ply twist psi, degrees (Table 2)
  *   incl_deg    yarn inclination u, degrees (Table 2)
  *   alpha, beta roughness and height-field scale, [0] warp, [1] weft (Table 1)

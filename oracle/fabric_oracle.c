@@ -65,18 +65,18 @@ enum { M_PAT = 0, M_PSI, M_INCL, M_ALPHA_W, M_ALPHA_F, M_BETA_W, M_BETA_F,
        M_KD_W, M_KD_F = 10, M_KS_W = 13, M_KS_F = 16, M_GAP = 19, M_WBLEND = 20,
        M_STRIDE = 21 };
 
-#define ORA_NPAT 8
+#define ORA_NPAT 12
 #define ORA_MAXDIM 16
 
 /* ---------------------------- weave patterns ----------------------------- */
-/* Textile definitions of the eight weaves; row i runs along v (weft index),  */
+/* Textile definitions of the twelve weaves; row i runs along v (weft index),*/
 /* column j along u (warp index); 1 = warp over weft.                         */
 static int pat_rows(int pid) {
-  static const int R[ORA_NPAT] = {2, 3, 4, 5, 5, 4, 4, 4};
+  static const int R[ORA_NPAT] = {2, 3, 4, 5, 5, 4, 4, 4, 5, 8, 8, 10};
   return R[pid];
 }
 static int pat_cols(int pid) {
-  static const int C[ORA_NPAT] = {2, 3, 4, 5, 5, 4, 8, 2};
+  static const int C[ORA_NPAT] = {2, 3, 4, 5, 5, 4, 8, 2, 5, 8, 8, 5};
   return C[pid];
 }
 static int imod(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
@@ -92,6 +92,10 @@ static int pat_bit(int pid, int i, int j) {
     case 6: return j < 4 ? imod(i - j, 4) < 2            /* herringbone: 2/2 twill */
                          : imod(i + j, 4) < 2;           /*   reversed at j = 4 */
     case 7: return ((i / 2) + j) % 2 == 0;               /* warp rib */
+    case 8: return imod(i - j, 5) < 4;                   /* 4/1 twill (5 x 5) */
+    case 9: return imod(i - j, 8) < 7;                   /* 7/1 twill (8 x 8) */
+    case 10: return imod(i - 3 * j, 8) == 0;             /* 8-harness satin, weft-faced */
+    case 11: return imod(i / 2 - 3 * j, 5) == 0;         /* 5-harness satin, picks doubled (10 x 5) */
   }
   return 0;
 }

@@ -12,7 +12,7 @@ out step by step.
 Parameter layout (flat float vectors, shared as an interface with the CUDA
 library, each side implementing it on its own):
   decoder: W1[64][71] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[4][64] b4[4]
-  encoder: E1[128][14] e1[128] E2[128][128] e2[128] E3[32][128] e3[32]
+  encoder: E1[128][22] e1[128] E2[128][128] e2[128] E3[32][128] e3[32]
 Weights are [out][in] (row = output unit).
 """
 from __future__ import annotations
@@ -27,7 +27,8 @@ N_QFEAT = 2 * 2 * N_FREQ + 1 + 3 + 3      # 39 query features
 N_IN = LATENT + N_QFEAT                   # 71
 HIDDEN = 64
 N_OUT = 4                                 # C_warp, C_weft, S_warp, S_weft (Eq. 7)
-ENC_IN = 14
+N_PATTERN_SLOTS = 16                      # one-hot width of the weave id (ids 0..11 in use)
+ENC_IN = N_PATTERN_SLOTS + 6
 ENC_HIDDEN = 128
 
 DEC_SHAPES = [("W1", (HIDDEN, N_IN)), ("b1", (HIDDEN,)),
@@ -185,18 +186,19 @@ def lrelu(x):
 
 
 def encoder_features(materials) -> np.ndarray:
-    """14 inputs: one-hot pattern (8) | psi / 30 deg | u / 45 deg |
+    """22 inputs: one-hot weave id (16 slots) | psi / 30 deg | u / 45 deg |
     alpha_warp | beta_warp | alpha_weft | beta_weft.  Albedos are not inputs
     (they enter only through Eq. 8)."""
     m = np.atleast_1d(materials)
     f = np.zeros((len(m), ENC_IN))
     f[np.arange(len(m)), m["pattern"].astype(np.int64)] = 1.0
-    f[:, 8] = m["twist_deg"].astype(np.float64) / 30.0
-    f[:, 9] = m["incl_deg"].astype(np.float64) / 45.0
-    f[:, 10] = m["alpha"][:, 0].astype(np.float64)
-    f[:, 11] = m["beta"][:, 0].astype(np.float64)
-    f[:, 12] = m["alpha"][:, 1].astype(np.float64)
-    f[:, 13] = m["beta"][:, 1].astype(np.float64)
+    b = N_PATTERN_SLOTS
+    f[:, b + 0] = m["twist_deg"].astype(np.float64) / 30.0
+    f[:, b + 1] = m["incl_deg"].astype(np.float64) / 45.0
+    f[:, b + 2] = m["alpha"][:, 0].astype(np.float64)
+    f[:, b + 3] = m["beta"][:, 0].astype(np.float64)
+    f[:, b + 4] = m["alpha"][:, 1].astype(np.float64)
+    f[:, b + 5] = m["beta"][:, 1].astype(np.float64)
     return f
 
 

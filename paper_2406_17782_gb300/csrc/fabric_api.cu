@@ -58,7 +58,7 @@ struct Weave {
   const char *cells[kMaxPatternDim];
 };
 
-static const Weave kWeaves[8] = {
+static const Weave kWeaves[kNumWeaves] = {
     {2, 2, {"10", "01"}},                                            // plain
     {3, 3, {"101", "110", "011"}},                                   // 2/1 twill
     {4, 4, {"1011", "1101", "1110", "0111"}},                        // 3/1 twill
@@ -67,6 +67,13 @@ static const Weave kWeaves[8] = {
     {4, 4, {"1100", "1100", "0011", "0011"}},                        // 2x2 basket
     {4, 8, {"10011100", "11001001", "01100011", "00110110"}},        // herringbone
     {4, 2, {"10", "10", "01", "01"}},                                // warp rib
+    {5, 5, {"10111", "11011", "11101", "11110", "01111"}},           // 4/1 twill
+    {8, 8, {"10111111", "11011111", "11101111", "11110111",          // 7/1 twill
+            "11111011", "11111101", "11111110", "01111111"}},
+    {8, 8, {"10000000", "00010000", "00000010", "01000000",          // 8-harness satin, weft-faced
+            "00001000", "00000001", "00100000", "00000100"}},
+    {10, 5, {"10000", "10000", "00100", "00100", "00001",            // 5-harness satin, picks doubled
+             "00001", "01000", "01000", "00010", "00010"}},
 };
 
 // Offset and length of the float through cell `pos` of a cyclic line whose
@@ -89,8 +96,8 @@ static void float_run(const bool *on, int n, int pos, int *len, int *off) {
 
 bool build_material(const fabric_material &m, DevMaterial *d, std::string *why) {
   char buf[256];
-  if (m.pattern_id < 0 || m.pattern_id > 7) {
-    snprintf(buf, sizeof(buf), "unknown pattern_id %d (built-in weaves are 0..7)", m.pattern_id);
+  if (m.pattern_id < 0 || m.pattern_id >= kNumWeaves) {
+    snprintf(buf, sizeof(buf), "unknown pattern_id %d (built-in weaves are 0..%d)", m.pattern_id, kNumWeaves - 1);
     *why = buf;
     return false;
   }

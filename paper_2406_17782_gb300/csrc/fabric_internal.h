@@ -17,7 +17,9 @@ constexpr int kHidden = 64;
 constexpr int kQueryFeat = 39;          // enc(u) 16 | enc(v) 16 | l | wi 3 | wo 3
 constexpr int kDecIn = kLatent + kQueryFeat;
 constexpr int kOut = 4;
-constexpr int kEncIn = 14;
+constexpr int kPatternSlots = 16;   // one-hot width of the weave id in the encoder input
+constexpr int kNumWeaves = 12;      // built-in weave tables
+constexpr int kEncIn = kPatternSlots + 6;
 constexpr int kEncHidden = 128;
 constexpr int kMaxPatternDim = 16;
 

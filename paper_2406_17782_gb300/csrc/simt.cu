@@ -119,13 +119,14 @@ __global__ void __launch_bounds__(kFwdThreads) decoder_fp32_kernel(const FwdArgs
 }
 
 // ---------------------------------------------------------------------------
-// Decoder forward + backward over tiles of kTR rows (128 threads per CTA).
+// Decoder forward + backward over tiles of kTR rows (kBwdThreads per CTA).
 // Either dy is given, or it comes from the Eq. 11 loss against `target`.
 // Per-CTA parameter-gradient partials stay in shared memory and are written
 // out once; dlat_rows receives each row's gradient w.r.t. its latent.
 // ---------------------------------------------------------------------------
 constexpr int kTR = 32;
-constexpr int kBwdThreads = 128;
+constexpr int kBwdThreads = 256;
+constexpr int kBwdWarps = kBwdThreads / 32;
 constexpr int kRS = kTR + 1;   // row stride (bank-conflict padding)
 
 struct BwdArgs {
@@ -145,9 +146,9 @@ struct BwdArgs {
 
 __device__ __forceinline__ void layer_fwd(const float *W, const float *b, int n_out, int n_in, const float *in,
                                           bool relu_in, float *out) {
-  // thread -> (output group, row): row r = lane, outputs o = og, og + 4, ...
+  // thread -> (output group, row): row r = lane, outputs o = og, og + kBwdWarps, ...
   const int r = threadIdx.x & 31, og = threadIdx.x >> 5;
-  for (int o = og; o < n_out; o += 4) {
+  for (int o = og; o < n_out; o += kBwdWarps) {
     float acc = b[o];
     const float *w = W + o * n_in;
     for (int i = 0; i < n_in; ++i) {
@@ -163,7 +164,7 @@ __device__ __forceinline__ void layer_fwd(const float *W, const float *b, int n_
 __device__ __forceinline__ void layer_bwd_input(const float *W, int n_out, int n_in, const float *dout,
                                                 const float *pre, float *din, int i_limit) {
   const int r = threadIdx.x & 31, ig = threadIdx.x >> 5;
-  for (int i = ig; i < i_limit; i += 4) {
+  for (int i = ig; i < i_limit; i += kBwdWarps) {
     float acc = 0.0f;
     for (int o = 0; o < n_out; ++o) acc = fmaf(W[o * n_in + i], dout[o * kRS + r], acc);
     if (pre) acc = pre[i * kRS + r] > 0.0f ? acc : 0.0f;
@@ -264,9 +265,11 @@ __global__ void __launch_bounds__(kBwdThreads) decoder_bwd_kernel(const BwdArgs 
           const float y = Y[k * kRS + r];
           float c = y, dc = 1.0f;
           if (k >= 2) {
-            const float e = expf(fminf(y, kYClamp));
-            c = (e - 1.0f) * (1.0f / kSpecK);
-            dc = y < kYClamp ? e * (1.0f / kSpecK) : 0.0f;
+            // expm1: near y = 0, exp(y) - 1 in FP32 would lose the relative
+            // precision of the small S values the loss compares
+            const float ys = fminf(y, kYClamp);
+            c = expm1f(ys) * (1.0f / kSpecK);
+            dc = y < kYClamp ? expf(ys) * (1.0f / kSpecK) : 0.0f;
           }
           const float diff = (c - tg) * wz;
           d = 2.0f * diff * wz * dc * a.inv_batch;
@@ -375,13 +378,13 @@ __global__ void __launch_bounds__(256) latent_segment_kernel(const uint16_t *__r
 __device__ __forceinline__ float lrelu(float x) { return x > 0.0f ? x : kLeaky * x; }
 
 __device__ void material_features(const fabric_material &m, float *f) {
-  for (int k = 0; k < 8; ++k) f[k] = (m.pattern_id == k) ? 1.0f : 0.0f;
-  f[8] = m.twist_deg / 30.0f;
-  f[9] = m.incl_deg / 45.0f;
-  f[10] = m.alpha[0];
-  f[11] = m.beta[0];
-  f[12] = m.alpha[1];
-  f[13] = m.beta[1];
+  for (int k = 0; k < kPatternSlots; ++k) f[k] = (m.pattern_id == k) ? 1.0f : 0.0f;
+  f[kPatternSlots + 0] = m.twist_deg / 30.0f;
+  f[kPatternSlots + 1] = m.incl_deg / 45.0f;
+  f[kPatternSlots + 2] = m.alpha[0];
+  f[kPatternSlots + 3] = m.beta[0];
+  f[kPatternSlots + 4] = m.alpha[1];
+  f[kPatternSlots + 5] = m.beta[1];
 }
 
 __global__ void material_features_kernel(const fabric_material *__restrict__ raw, int n, float *__restrict__ f) {

@@ -46,8 +46,8 @@ def test_struct_layouts_match_header(lib):
 def test_param_counts(lib):
     import oracle
     assert lib.fabric_decoder_param_count() == oracle.mlp.n_params(oracle.mlp.DEC_SHAPES) == 13188
-    assert lib.fabric_encoder_param_count() == oracle.mlp.n_params(oracle.mlp.ENC_SHAPES) == 22560
-    assert len(W.decoder_init()) == 13188 and len(W.encoder_init()) == 22560
+    assert lib.fabric_encoder_param_count() == oracle.mlp.n_params(oracle.mlp.ENC_SHAPES) == 23584
+    assert len(W.decoder_init()) == 13188 and len(W.encoder_init()) == 23584
 
 
 def test_status_strings_and_null_context(lib):

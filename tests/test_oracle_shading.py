@@ -55,24 +55,29 @@ def test_mix64_matches_published_splitmix64(oracle_mod):
 
 # ---------------------------------------------------------------- patterns
 def test_weave_definitions(oracle_mod):
-    P = {pid: oracle_mod.pattern_info(pid)[0].astype(int) for pid in range(8)}
+    P = {pid: oracle_mod.pattern_info(pid)[0].astype(int) for pid in range(12)}
     # plain: alternates along both axes
     assert P[0].shape == (2, 2)
     assert np.all(P[0] != np.roll(P[0], 1, 0)) and np.all(P[0] != np.roll(P[0], 1, 1))
     # twills: each row is the row above shifted by one column (diagonal)
-    for pid, (n, over) in {1: (3, 2), 2: (4, 3)}.items():
+    for pid, (n, over) in {1: (3, 2), 2: (4, 3), 8: (5, 4), 9: (8, 7)}.items():
         assert P[pid].shape == (n, n)
         assert np.all(P[pid].sum(1) == over) and np.all(P[pid].sum(0) == over)
         assert np.array_equal(np.roll(np.roll(P[pid], 1, 0), 1, 1), P[pid])
     # satins: one interlacing per row and column, never in adjacent columns of
     # consecutive rows (no twill line)
-    for pid, faced in {3: 0, 4: 1}.items():
+    for pid, faced, n in ((3, 0, 5), (4, 1, 5), (10, 1, 8)):
         A = P[pid] if faced == 1 else 1 - P[pid]
-        assert A.shape == (5, 5)
+        assert A.shape == (n, n)
         assert np.all(A.sum(0) == 1) and np.all(A.sum(1) == 1)
         cols = A.argmax(1)
-        steps = (np.roll(cols, -1) - cols) % 5
-        assert np.all((steps != 1) & (steps != 4))
+        steps = (np.roll(cols, -1) - cols) % n
+        assert np.all((steps != 1) & (steps != n - 1))
+    # satin with doubled picks (10 x 5): every pick repeated, and the
+    # undoubled rows form the weft-faced 5-harness satin above
+    D = P[11]
+    assert D.shape == (10, 5)
+    assert np.array_equal(D[0::2], D[1::2]) and np.array_equal(D[0::2], P[4])
     # basket 2x2: constant 2x2 blocks forming a checkerboard
     B = P[5]
     assert np.array_equal(B, np.kron(np.array([[1, 0], [0, 1]]), np.ones((2, 2), int)))
@@ -89,7 +94,7 @@ def test_weave_definitions(oracle_mod):
 
 
 def test_float_run_tables_bruteforce(oracle_mod):
-    for pid in range(8):
+    for pid in range(12):
         bits, runlen, runoff = oracle_mod.pattern_info(pid)
         R, C = bits.shape
         for i in range(R):
@@ -156,9 +161,9 @@ def test_nonnegative_and_finite(oracle_mod):
 
 def test_weave_periodicity_bitwise(oracle_mod):
     rng = np.random.default_rng(2)
-    mats = W.random_materials(rng, range(8))
-    n = 200
-    g = _rand_gbuf(rng, n, 8, uv_max=20.0)
+    mats = W.random_materials(rng, range(12))
+    n = 300
+    g = _rand_gbuf(rng, n, 12, uv_max=20.0)
     # uv with at most 16 fractional bits so that +1 / +2 periods are exact
     g["u"] = (np.round(g["u"] * 65536) / 65536).astype(np.float32)
     g["v"] = (np.round(g["v"] * 65536) / 65536).astype(np.float32)
@@ -181,7 +186,7 @@ def _flat_expected(wi, wo, w):
     return C, S
 
 
-@pytest.mark.parametrize("pid", range(8))
+@pytest.mark.parametrize("pid", range(12))
 def test_point_closed_form_flat_isotropic(oracle_mod, pid):
     rng = np.random.default_rng(10 + pid)
     m = mat_row(oracle_mod, pattern=pid, alpha=[1.0, 1.0], beta=[0.0, 0.0], incl_deg=0.0,
@@ -461,7 +466,7 @@ def test_whole_period_flat_isotropic_coverage_closed_form(oracle_mod):
     so the whole-period value is that form weighted by each yarn's visible
     area fraction, counted exactly from the weave and the fixed-point gap."""
     rng = np.random.default_rng(14)
-    for pid in range(8):
+    for pid in range(12):
         m = mat_row(oracle_mod, pattern=pid, alpha=[1.0, 1.0], beta=[0.0, 0.0], incl_deg=0.0)
         bits = oracle_mod.pattern_info(pid)[0]
         Gf = math.floor(0.5 * float(np.float32(0.2)) * 2 ** 32)
@@ -470,7 +475,7 @@ def test_whole_period_flat_isotropic_coverage_closed_form(oracle_mod):
         cov_warp = (nw * (1 - gap_frac) + (bits.size - nw) * gap_frac) / bits.size
         wi, wo = W.hemisphere_uniform(rng, 2).astype(np.float64)
         Cx, Sx = _flat_expected(wi, wo, 0.5)
-        # 1200 = 10 x lcm(2,3,4,5,8): no lattice point lies on a cell or gap edge
+        # 1200 = 10 x lcm(2,3,4,5,8,10): no lattice point lies on a cell or gap edge
         q = oracle_mod.period_quadrature(m, wi, wo, 1200)
         got = q[:4] / q[4]
         want = np.array([cov_warp * Cx, (1 - cov_warp) * Cx, cov_warp * Sx, (1 - cov_warp) * Sx])

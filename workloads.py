@@ -304,7 +304,7 @@ def init_params(n: int, fan_ins, sizes, seed: int, weight_bound: str = "he") -> 
 
 
 DEC_LAYERS = [(64, 71), (64, 64), (64, 64), (4, 64)]       # (out, in)
-ENC_LAYERS = [(128, 14), (128, 128), (32, 128)]
+ENC_LAYERS = [(128, 22), (128, 128), (32, 128)]
 
 
 def decoder_init(seed: int = 3, weight_bound: str = "he") -> np.ndarray:
