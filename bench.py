@@ -513,8 +513,11 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     side = torch.cuda.Stream()
     b4k = {"points": n_b, "segments": len(segs), "launches_per_replay": 1,
            "note": "3840x2160 tile-interleaved + 256 ragged tiles (256..65536 pts), CUDA graph replay"}
+    from paper_2406_17782_gb300 import autotune
+    saved = fab.launch_config, getattr(fab, "tile_warpgroups", 0)
     for prec in ("fp16", "bf16", "fp8"):
         fab.prepare_neural(latents, prec)
+        tuned = autotune.tune_plan(fab, plan, prec)
         plan.shade(prec)
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
@@ -525,8 +528,11 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
         graph.replay()
         ms_b = timed(torch, stream, lambda k: graph.replay(), 50)
         fab.sync_status()
-        b4k[prec] = {"ms_per_replay": ms_b, "pts_per_s": n_b / (ms_b * 1e-3)}
+        b4k[prec] = {"ms_per_replay": ms_b, "pts_per_s": n_b / (ms_b * 1e-3),
+                     "launch": {"pipelines_per_cta": tuned["warpgroups"], "ctas_per_sm": tuned["ctas_per_sm"],
+                                "warpgroups_per_pipeline": tuned["tile_warpgroups"]}}
         del graph
+    fab.set_launch_config(saved[0][0], saved[0][1], saved[0][2], saved[1])
     g4k = segs[0][0]
     out4k = segs[0][1]
     fab.shade_reference(g4k, 16, 16, 11, out_rgb=out4k)

@@ -318,6 +318,7 @@ class Plan:
         fab._check(fab.lib.fabric_plan_create(fab.h, arr, len(arr), ctypes.byref(h)))
         self.h = h
         self.points = int(fab.lib.fabric_plan_points(h))
+        self.n_segs = len(self.segments)
 
     def shade(self, precision: str = "fp16", stream=None):
         self.fab._check(self.fab.lib.fabric_plan_shade(self.fab.h, self.h, _abi.PREC[precision],

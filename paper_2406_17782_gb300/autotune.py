@@ -85,6 +85,31 @@ def tune_decoder(fab, g, precision: str = "fp16", candidates=None, reps: int = 5
     return cache[key]
 
 
+def tune_plan(fab, plan, precision: str = "fp16", candidates=None, reps: int = 20,
+              cache_path: str = DEFAULT_CACHE, force: bool = False) -> dict:
+    """Pick the decoder's launch shape for a batched plan (its segments'
+    tile count decides how the persistent CTAs share the work), with the
+    neural state already prepared for `precision`."""
+    candidates = candidates or DECODER_CANDIDATES
+    cache = _load(cache_path)
+    key = _key(fab, "plan", precision, fab.n_mat, plan.points, f"segs{plan.n_segs}")
+    lanes = _current(fab)[2]
+    if not force and key in cache and "tile_warpgroups" in cache[key]:
+        e = cache[key]
+        fab.set_launch_config(e["ctas_per_sm"], e["warpgroups"], lanes, e["tile_warpgroups"])
+        return e
+    timings = {}
+    for wg, c, h in candidates:
+        fab.set_launch_config(c, wg, lanes, h)
+        timings[(wg, c, h)] = _time(lambda: plan.shade(precision), reps)
+    wg, c, h = min(timings, key=timings.get)
+    fab.set_launch_config(c, wg, lanes, h)
+    cache[key] = {"warpgroups": wg, "ctas_per_sm": c, "tile_warpgroups": h, "ms": timings[(wg, c, h)],
+                  "timings": {f"wg{k[0]}_cta{k[1]}_h{k[2]}": v for k, v in timings.items()}}
+    _store(cache_path, cache)
+    return cache[key]
+
+
 def tune_reference(fab, g, spp_x: int, spp_y: int, candidates=(1, 2, 4, 8, 16, 32), reps: int = 3,
                    cache_path: str = DEFAULT_CACHE, force: bool = False) -> dict:
     """Pick the reference kernel's lanes per point for `g` at spp_x x spp_y."""
