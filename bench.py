@@ -570,8 +570,15 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
         fab.train_step(gq, target, 1e-3)
     ms_train = timed(torch, stream, lambda k: fab.train_step(gq, target, 1e-3), 20)
     fab.sync_status()
+    fab.set_train_precision("bf16")
+    for _ in range(3):
+        fab.train_step(gq, target, 1e-3)
+    ms_train_tc = timed(torch, stream, lambda k: fab.train_step(gq, target, 1e-3), 20)
+    fab.sync_status()
+    fab.set_train_precision("fp32")
     out["train"] = {"ms_per_step": ms_train, "batch": 65536, "samples_per_s": 65536 / (ms_train * 1e-3),
-                    "materials": len(tm)}
+                    "materials": len(tm), "path": "FP32 SIMT forward/backward",
+                    "bf16_tensor_core": {"ms_per_step": ms_train_tc, "samples_per_s": 65536 / (ms_train_tc * 1e-3)}}
     if not args.no_quality:
         out["quality"] = measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream)
     # the FP64 oracle on the host cores, bounded sample

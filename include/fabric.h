@@ -280,6 +280,15 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
 typedef enum { FABRIC_LOSS_EQ11 = 0, FABRIC_LOSS_RENDERED = 1 } fabric_loss;
 fabric_status fabric_set_train_loss(fabric_ctx *ctx, fabric_loss loss);
 
+/* Arithmetic of the decoder's forward and backward in fabric_train_step
+ * (default FABRIC_PREC_FP32): FABRIC_PREC_FP32 runs them as FP32 SIMT
+ * kernels; FABRIC_PREC_BF16 runs every product on the tensor cores with BF16
+ * operands and FP32 accumulation (the weight gradients accumulate over each
+ * CTA's queries in tensor memory).  Both keep FP32 master parameters, the
+ * encoder in FP32, FP64 loss sums and fixed-order reductions, so both are
+ * bitwise repeatable.  FABRIC_ERR_INVALID_ARG for other precisions. */
+fabric_status fabric_set_train_precision(fabric_ctx *ctx, fabric_precision prec);
+
 /* ------------------------------------------------------------------ */
 /* Building blocks for a torch.autograd.Function                      */
 /* ------------------------------------------------------------------ */

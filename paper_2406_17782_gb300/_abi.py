@@ -80,6 +80,7 @@ def load(path: str | None = None):
         "fabric_set_launch_config": (st, [vp, i32, i32, i32]),
         "fabric_set_decoder_tile_warpgroups": (st, [vp, i32]),
         "fabric_set_train_loss": (st, [vp, i32]),
+        "fabric_set_train_precision": (st, [vp, i32]),
         "fabric_shade_neural_host": (st, [vp, vp, i32, vp, vp, i64, vp]),
         "fabric_set_materials": (st, [vp, vp, i32]),
         "fabric_set_train_materials": (st, [vp, vp, i32]),

@@ -237,6 +237,11 @@ class Fabric:
         components weighted by max(wi.z, 0))."""
         self._check(self.lib.fabric_set_train_loss(self.h, _abi.LOSS[loss]))
 
+    def set_train_precision(self, precision: str = "fp32"):
+        """'fp32' (SIMT kernels) or 'bf16' (tensor cores) for the decoder's
+        training forward and backward."""
+        self._check(self.lib.fabric_set_train_precision(self.h, _abi.PREC[precision]))
+
     def train_step(self, batch: GBuffer, target: torch.Tensor, lr: float, loss_out=None, stream=None):
         loss = loss_out if loss_out is not None else torch.empty((), dtype=torch.float64, device=self.device)
         tb = FabricTrainBatch(batch.struct(), target.contiguous().data_ptr())

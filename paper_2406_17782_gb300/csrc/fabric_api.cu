@@ -311,6 +311,15 @@ fabric_status fabric_set_launch_config(fabric_ctx *ctx, int decoder_ctas_per_sm,
   return FABRIC_OK;
 }
 
+fabric_status fabric_set_train_precision(fabric_ctx *ctx, fabric_precision prec) {
+  if (!ctx) return FABRIC_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (prec != FABRIC_PREC_FP32 && prec != FABRIC_PREC_BF16)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "training runs in FP32 or BF16 (got %d)", (int)prec);
+  ctx->train_prec = (int)prec;
+  return FABRIC_OK;
+}
+
 fabric_status fabric_set_train_loss(fabric_ctx *ctx, fabric_loss loss) {
   if (!ctx) return FABRIC_ERR_INVALID_ARG;
   ctx->last_error.clear();

@@ -91,7 +91,8 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
                       align_up((size_t)M * 2 * kEncHidden * 4) +
                       align_up(((size_t)kDecParams + kEncParams) * 4) + align_up((size_t)M * kLatent * 4) +
                       align_up(encoder_backward_work_floats(M) * 4) +
-                      align_up(decoder_backward_work_bytes(q.n, ctx->sm_count)) + align_up(8);
+                      align_up(decoder_backward_work_bytes(q.n, ctx->sm_count)) + align_up(8) +
+                      align_up(train_tc_blob_bytes());
   void *base = scratch(ctx, need);
   if (!base) return fail(ctx, FABRIC_ERR_OOM, "training scratch (%zu bytes)", need);
   Carve c{static_cast<uint8_t *>(base)};
@@ -103,14 +104,31 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   float *ework = c.take<float>(encoder_backward_work_floats(M));
   void *dwork = c.take<uint8_t>(decoder_backward_work_bytes(q.n, ctx->sm_count));
   double *loss_tmp = c.take<double>(1);
+  void *tc_blob = c.take<uint8_t>(train_tc_blob_bytes());
   double *loss = loss_dev ? loss_dev : loss_tmp;
   FAB_CUDA(ctx, launch_material_features(ctx->d_train_raw, M, feats, s), "features");
   FAB_CUDA(ctx, launch_encoder_feats(feats, M, ctx->d_enc, z, acts, s), "encoder forward");
-  FAB_CUDA(ctx,
-           launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, ctx->loss_mode, grad, dz, loss, dwork,
-                                   ctx->sm_count,
-                                   ctx->d_status, s),
-           "decoder forward/backward");
+  if (ctx->train_prec == FABRIC_PREC_BF16) {
+    // the work area holds [grid][kDecParams] partials, [grid] loss partials
+    // and [n][32] latent-gradient rows, as for the FP32 path
+    const int grid = train_tc_grid(q.n, ctx->sm_count);
+    uint8_t *w = static_cast<uint8_t *>(dwork);
+    float *partial = reinterpret_cast<float *>(w);
+    size_t off = ((size_t)grid * kDecParams * 4 + 15) & ~size_t(15);
+    double *loss_part = reinterpret_cast<double *>(w + off);
+    off = (off + (size_t)grid * 8 + 15) & ~size_t(15);
+    float *rows = reinterpret_cast<float *>(w + off);
+    FAB_CUDA(ctx,
+             launch_train_tc(q, z, M, ctx->d_dec, batch->target, ctx->loss_mode, tc_blob, partial, loss_part, rows,
+                             ctx->sm_count, ctx->d_status, s),
+             "tensor-core decoder forward/backward");
+    FAB_CUDA(ctx, launch_decoder_grad_finish(q, M, partial, grid, loss_part, rows, grad, loss, dz, s), "gradient sums");
+  } else {
+    FAB_CUDA(ctx,
+             launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, ctx->loss_mode, grad, dz, loss,
+                                     dwork, ctx->sm_count, ctx->d_status, s),
+             "decoder forward/backward");
+  }
   FAB_CUDA(ctx, launch_encoder_backward(feats, M, ctx->d_enc, acts, dz, grad + kDecParams, ework, s),
            "encoder backward");
   ctx->adam_step += 1;

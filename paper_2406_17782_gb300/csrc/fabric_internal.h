@@ -127,6 +127,7 @@ struct fabric_ctx {
   int tc_warpgroups = 0;
   int tc_tile_wgs = 0;         // warpgroups per decoder tile pipeline (0 or 1: one, 2: two)
   int loss_mode = 0;           // FABRIC_LOSS_EQ11 or FABRIC_LOSS_RENDERED
+  int train_prec = 0;          // FABRIC_PREC_FP32 (SIMT) or FABRIC_PREC_BF16 (tensor cores)
   int ref_lanes = 0;
   // host-buffer pipeline (fabric_shade_neural_host): per-slot stream, event
   // and device staging for one chunk's G-buffer and outputs
@@ -184,6 +185,18 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
                                     const float *dy, const float *target, int loss_mode, float *ddec, float *dlat,
                                     double *loss, void *work, int sm_count, int *status, cudaStream_t s);
 size_t decoder_backward_work_bytes(int64_t n, int sm_count);
+// The fixed-order sums after a backward pass that wrote per-CTA partials:
+// parameter gradients, the loss, and the per-material latent gradients.
+cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid,
+                                      const double *loss_part, const float *rows, float *ddec, double *loss,
+                                      float *dlat, cudaStream_t s);
+// Tensor-core (BF16) decoder training forward + backward: per-CTA gradient
+// partials [grid][kDecParams], loss partials [grid], latent-gradient rows [n][32].
+size_t train_tc_blob_bytes();
+int train_tc_grid(int64_t n, int sm_count);
+cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
+                            const float *target, int loss_mode, void *blob, float *partial, double *loss_partial,
+                            float *dlat_rows, int sm_count, int *status, cudaStream_t s);
 cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, int64_t step,
                         cudaStream_t s);
 cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,

@@ -7,30 +7,12 @@
 #include <cmath>
 
 #include "fabric_internal.h"
+#include "train_common.cuh"
 
 namespace fab {
 namespace {
 
-constexpr float kLambdaS = 0.4f;      // Eq. 11
-constexpr float kLambdaC = 0.1f;
-constexpr float kYClamp = 12.0f;      // head pre-activation limit of the rendered-space loss
 constexpr float kLeaky = 0.01f;       // encoder residual-block activation slope
-
-// ---------------------------------------------------------------------------
-// query features (FP32, accurate sinpi/cospi per octave)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void octaves_accurate(float x, float *f16) {
-  const float f0 = x - floorf(x);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const float sc = f0 * (float)(1 << k);
-    const float fk = sc - floorf(sc);
-    float s, c;
-    sincospif(2.0f * fk, &s, &c);
-    f16[2 * k] = s;
-    f16[2 * k + 1] = c;
-  }
-}
 
 // Writes the 71 decoder inputs of point p into x[i * stride + r].
 __device__ __forceinline__ void build_inputs(const fabric_gbuffer &g, int64_t p, const float *lat, float *x,
@@ -258,29 +240,9 @@ __global__ void __launch_bounds__(kBwdThreads) decoder_bwd_kernel(const BwdArgs 
       const bool valid = X[kDecIn * kRS + r] > 0.0f;
       float d = 0.0f;
       if (valid) {
-        if (a.target && a.loss_mode == FABRIC_LOSS_RENDERED) {
-          // ((c_hat - c) max(<wi.n_s>, 0))^2, c_hat = y (C) or (exp(min(y, 12)) - 1) / k (S)
-          const float tg = a.target[4 * p + k];
-          const float wz = fmaxf(a.g.wi[3 * p + 2], 0.0f);
-          const float y = Y[k * kRS + r];
-          float c = y, dc = 1.0f;
-          if (k >= 2) {
-            // expm1: near y = 0, exp(y) - 1 in FP32 would lose the relative
-            // precision of the small S values the loss compares
-            const float ys = fminf(y, kYClamp);
-            c = expm1f(ys) * (1.0f / kSpecK);
-            dc = y < kYClamp ? expf(ys) * (1.0f / kSpecK) : 0.0f;
-          }
-          const float diff = (c - tg) * wz;
-          d = 2.0f * diff * wz * dc * a.inv_batch;
-          loss_acc += (double)diff * (double)diff * (double)a.inv_batch;
-        } else if (a.target) {
-          const float tg = a.target[4 * p + k];
-          const float tt = k < 2 ? tg : logf(kSpecK * tg + 1.0f);   // g(x) = ln(k x + 1), Eq. 9
-          const float lam = k < 2 ? kLambdaC : kLambdaS;
-          const float diff = Y[k * kRS + r] - tt;
-          d = 2.0f * lam * diff * a.inv_batch;
-          loss_acc += (double)lam * (double)diff * (double)diff * (double)a.inv_batch;
+        if (a.target) {
+          d = loss_grad(k, Y[k * kRS + r], a.target[4 * p + k], a.g.wi[3 * p + 2], a.loss_mode, a.inv_batch,
+                        &loss_acc);
         } else {
           d = a.dy[4 * p + k];
         }
@@ -649,6 +611,15 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
   decoder_bwd_kernel<<<grid, kBwdThreads, bwd_smem_bytes(), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  reduce_partials_kernel<<<(kDecParams + 255) / 256, 256, 0, s>>>(partial, grid, kDecParams, ddec);
+  if (loss) reduce_loss_kernel<<<1, 32, 0, s>>>(loss_part, grid, loss);
+  if (dlat) latent_segment_kernel<<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid,
+                                      const double *loss_part, const float *rows, float *ddec, double *loss,
+                                      float *dlat, cudaStream_t s) {
   reduce_partials_kernel<<<(kDecParams + 255) / 256, 256, 0, s>>>(partial, grid, kDecParams, ddec);
   if (loss) reduce_loss_kernel<<<1, 32, 0, s>>>(loss_part, grid, loss);
   if (dlat) latent_segment_kernel<<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);

@@ -3,7 +3,7 @@ for profilers (ncu) and quick timing:
 
   python -m paper_2406_17782_gb300.profile_case reference [--spp 16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case decoder [--precision fp16] [--reps 3]
-  python -m paper_2406_17782_gb300.profile_case train [--batch 65536] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case train [--batch 65536] [--train-precision fp32|bf16] [--reps 3]
 
 The workload is the 1920 x 1080 G-buffer of eight weave materials (random-init
 networks); the training case uses a batch of queries over 256 training
@@ -34,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--spp", type=int, default=16, help="samples per axis (reference)")
     ap.add_argument("--precision", default="fp16")
     ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--train-precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
     fab = Fabric(0)
@@ -48,6 +49,7 @@ def main(argv=None):
         fab.set_materials(tm)
         fab.shade_reference(g, 4, 4, 3, out_comps=target)
         fab.set_train_materials(tm)
+        fab.set_train_precision(args.train_precision)
         fn = lambda: fab.train_step(g, target, 1e-3)
     else:
         g = GBuffer.from_numpy(W.frame_gbuffer())
