@@ -294,11 +294,17 @@ __global__ void reduce_partials_kernel(const float *__restrict__ partial, int n_
   out[j] = s;
 }
 
+// 32 threads sum fixed strided subsets, then thread 0 sums the 32 in order.
 __global__ void reduce_loss_kernel(const double *__restrict__ part, int n, double *__restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int c = 0; c < n; ++c) s += part[c];
-    *out = s;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int c = threadIdx.x; c < n; c += 32) s += part[c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += red[k];
+    *out = t;
   }
 }
 
@@ -311,16 +317,25 @@ __global__ void __launch_bounds__(256) latent_segment_kernel(const uint16_t *__r
   float acc[kLatent];
 #pragma unroll
   for (int i = 0; i < kLatent; ++i) acc[i] = 0.0f;
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
-    if (mat[r] != m) continue;
-    const float4 *src = reinterpret_cast<const float4 *>(rows + r * kLatent);
+  // thread t takes rows t, t + 256, ... in order (coalesced across the
+  // block), reading eight material ids ahead so that their loads overlap
+  const int64_t step = blockDim.x;
+  for (int64_t r = threadIdx.x; r < n; r += 8 * step) {
+    int ids[8];
 #pragma unroll
-    for (int q = 0; q < kLatent / 4; ++q) {
-      const float4 v = src[q];
-      acc[4 * q] += v.x;
-      acc[4 * q + 1] += v.y;
-      acc[4 * q + 2] += v.z;
-      acc[4 * q + 3] += v.w;
+    for (int q = 0; q < 8; ++q) ids[q] = r + q * step < n ? (int)mat[r + q * step] : -1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (ids[q] != m) continue;
+      const float4 *src = reinterpret_cast<const float4 *>(rows + (r + q * step) * kLatent);
+#pragma unroll
+      for (int k = 0; k < kLatent / 4; ++k) {
+        const float4 v = src[k];
+        acc[4 * k] += v.x;
+        acc[4 * k + 1] += v.y;
+        acc[4 * k + 2] += v.z;
+        acc[4 * k + 3] += v.w;
+      }
     }
   }
 #pragma unroll
