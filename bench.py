@@ -9,13 +9,20 @@ frame; the latent fold and weight packing run once per material edit and are
 timed separately).  Four G-buffer copies rotate so that every step reads
 inputs that are not in L2 (4 x 79 MB > 129 MB).
 
-Also measured in the same run and reported on the JSON line: the reference
-integral of the same frame at 256 spp, the full neural call including the
-fold, a training step (batch 65536), the end-to-end path from pinned host
-memory, SM clocks during the timed region, and the FP64 oracle timed on the
-host cores.
+Also measured in the same run and reported on the JSON line:
+  * the reference integral of the same frame at 256 spp;
+  * the full neural call including the fold;
+  * the end-to-end path from page-locked host memory (fabric_shade_neural_host);
+  * the batched 4K plan (one launch over a 3840x2160 view and 256 ragged
+    tiles, CUDA graph) per operand precision, and the FP8 frame;
+  * a training step (batch 65536) on the FP32 and the BF16 tensor-core paths;
+  * the quality ladder (--no-quality skips it): the network trained with the
+    library's kernels, then the frame RMSE of the neural path and of the
+    reference at 1-64 spp with their times, latent interpolation and the
+    editing latency;
+  * SM clocks during the timed region, and the FP64 oracle on the host cores.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-extras | --no-quality]
 
 Under torchrun every rank shades its own frame (independent frames, no
 collective on the data path: weak scaling); the elapsed time is the maximum
