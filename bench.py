@@ -211,8 +211,10 @@ def main():
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed neural frames")
     ap.add_argument("--no-quality", action="store_true", help="skip training and the frame-RMSE comparison")
-    ap.add_argument("--quality-queries", type=int, default=1 << 23)
-    ap.add_argument("--quality-steps", type=int, default=30000)
+    ap.add_argument("--quality-queries", type=int, default=1 << 24)
+    ap.add_argument("--quality-steps", type=int, default=150000)
+    ap.add_argument("--quality-precision", default="bf16", choices=["fp32", "bf16"],
+                    help="training forward/backward: FP32 SIMT or BF16 tensor-core kernels")
     ap.add_argument("--quality-lr", type=float, default=3e-3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
@@ -415,14 +417,19 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     copies = len(gbufs)
     runs = {}
     ladder = None
+    ms_host = W.multiscale_gbuffer()
+    ms_dev = GBuffer.from_numpy(ms_host)
+    ms_ladder = None
     for loss in ("eq11", "rendered"):
         fab.set_params(W.decoder_init(weight_bound="small"), W.encoder_init(weight_bound="small"))
         fab.set_train_loss(loss)
+        fab.set_train_precision(args.quality_precision)
         t0 = time.time()
         T.train(fab, tm, g_tr, target, args.quality_steps, 65536, args.quality_lr, log_every=1000, verbose=False)
         torch.cuda.synchronize()
         t_train = time.time() - t0
         fab.set_train_loss("eq11")
+        fab.set_train_precision("fp32")
         rm = T.frame_rmse(fab, "fp16", gt_spp=(32, 32), ref_spps=spps if ladder is None else ())
         rm8 = T.frame_rmse(fab, "fp8", gt_spp=(32, 32), ref_spps=())
         lat = fab.encode_params(W.frame_materials())
@@ -439,15 +446,33 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
                                                                           out_rgb=rgbs[k % copies]), 20)
                 ladder.append({"spp": sp * sp, "rmse": rm[f"reference_{sp * sp}spp"]["rmse"], "ms": ms_r})
             gt_rms = rm["gt_rms"]
+        # the multi-scale frame: footprints of Table 2's sizes, ground truth at 4096 spp
+        rm_ms = T.frame_rmse(fab, "fp16", gt_spp=(64, 64), ref_spps=(1, 2, 4, 8, 16) if ms_ladder is None else (),
+                             gbuf=ms_host)
+        if ms_ladder is None:
+            ms_ladder = []
+            for sp in (1, 2, 4, 8, 16):
+                fab.shade_reference(ms_dev, sp, sp, 5, out_rgb=rgbs[0])
+                ms_r = timed(torch, stream, lambda k: fab.shade_reference(ms_dev, sp, sp, 5, out_rgb=rgbs[0]), 10)
+                ms_ladder.append({"spp": sp * sp, "rmse": rm_ms[f"reference_{sp * sp}spp"]["rmse"], "ms": ms_r})
+            ms_gt_rms = rm_ms["gt_rms"]
         fab.sync_status()
         neural = {"rmse": rm["neural"]["rmse"], "rel_l2": rm["neural"]["rel_l2"], "ms": ms["fp16"]}
         eq = next((r for r in ladder if r["rmse"] <= neural["rmse"]), None)
+        neural_ms = {"rmse": rm_ms["neural"]["rmse"], "rel_l2": rm_ms["neural"]["rel_l2"], "ms": ms["fp16"]}
+        eq_ms = next((r for r in ms_ladder if r["rmse"] <= neural_ms["rmse"]), None)
         runs[loss] = {
             "neural_fp16": neural,
             "neural_fp8": {"rmse": rm8["neural"]["rmse"], "rel_l2": rm8["neural"]["rel_l2"], "ms": ms["fp8"]},
             "neural_meets_0.01": neural["rmse"] <= 0.01,
             "reference_at_neural_rmse": eq,
             "speedup_at_equal_rmse": (eq["ms"] / neural["ms"]) if eq else None,
+            "multiscale": {
+                "neural_fp16": neural_ms,
+                "neural_meets_0.01": neural_ms["rmse"] <= 0.01,
+                "reference_at_neural_rmse": eq_ms,
+                "speedup_at_equal_rmse": (eq_ms["ms"] / neural_ms["ms"]) if eq_ms else None,
+            },
             "train_seconds": t_train,
         }
     del g_tr, target
@@ -459,10 +484,19 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
         "gt_rms": gt_rms,
         "reference": ladder,
         "reference_at_0.01": next((r for r in ladder if r["rmse"] <= 0.01), None),
+        "multiscale": {
+            "frame": "the 1080p frame with footprint sides drawn as in Table 2 (half U(0,1), half U(1,5) "
+                     "periods); ground truth: the reference at 4096 spp; neural ms from the 1080p frame "
+                     "(the decoder's cost does not depend on the footprint)",
+            "gt_rms": ms_gt_rms,
+            "reference": ms_ladder,
+            "reference_at_0.01": next((r for r in ms_ladder if r["rmse"] <= 0.01), None),
+        },
         "loss_eq11": runs["eq11"],
         "loss_rendered": runs["rendered"],
         "training": {"queries": args.quality_queries, "data_spp": 2048, "steps": args.quality_steps,
-                     "batch": 65536, "lr": args.quality_lr, "data_seconds": t_data},
+                     "batch": 65536, "lr": args.quality_lr, "precision": args.quality_precision,
+                     "data_seconds": t_data},
     }
 
 

@@ -434,6 +434,13 @@ fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const flo
 fabric_status fabric_selftest_mma_e4m3(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
                                        float *d_dev, void *stream);
 
+/* The same BF16 product with both operands in shared memory in the MN-major
+ * (transposed) layout the tensor-core training kernel uses for its weight
+ * gradients: element (i, q) of a (and of b) stored with the 8 consecutive i
+ * of one q in 16 contiguous bytes.  k in {16, 32, 48, 64}, n in {16, 32, 64}. */
+fabric_status fabric_selftest_mma_mn(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
+                                     float *d_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -276,6 +276,14 @@ class Fabric:
                                                       _ptr(d), _stream_handle(None)))
         return d
 
+    def selftest_mma_mn(self, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+        """128 x n x k BF16 product with both operands MN-major in shared memory."""
+        n, k = b.shape
+        d = torch.empty((128, n), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_selftest_mma_mn(self.h, _ptr(a.contiguous()), _ptr(b.contiguous()), n, k,
+                                                    _ptr(d), _stream_handle(None)))
+        return d
+
     # ---------------------------------------------- autograd building blocks
     def decoder_forward(self, g: GBuffer, latents, dec, stream=None):
         y = torch.empty((g.n, 4), dtype=torch.float32, device=self.device)

@@ -618,6 +618,17 @@ fabric_status fabric_selftest_mma_e4m3(fabric_ctx *ctx, const float *a_dev, cons
   return FABRIC_OK;
 }
 
+fabric_status fabric_selftest_mma_mn(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
+                                     float *d_dev, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!a_dev || !b_dev || !d_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "NULL pointer");
+  if (!(k == 16 || k == 32 || k == 48 || k == 64) || !(n == 16 || n == 32 || n == 64))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "k must be 16/32/48/64 and n 16/32/64");
+  FAB_CUDA(ctx, launch_selftest_mn(a_dev, b_dev, n, k, d_dev, ctx->d_status, static_cast<cudaStream_t>(stream)),
+           "selftest launch");
+  return FABRIC_OK;
+}
+
 fabric_status fabric_error_stats(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int64_t n,
                                  const float *weights_dev, int group, int weight_stride, double *out_dev,
                                  void *stream) {

@@ -68,10 +68,7 @@ fabric_status fabric_encode_params(fabric_ctx *ctx, const fabric_material *m, in
   }
   FAB_CUDA(ctx, cudaMemcpyAsync(ctx->d_enc_raw, m, n_mat * sizeof(fabric_material), cudaMemcpyHostToDevice, s),
            "encode upload");
-  float *feats = static_cast<float *>(scratch(ctx, align_up((size_t)n_mat * kEncIn * 4)));
-  if (!feats) return fail(ctx, FABRIC_ERR_OOM, "scratch");
-  FAB_CUDA(ctx, launch_material_features(ctx->d_enc_raw, n_mat, feats, s), "features");
-  FAB_CUDA(ctx, launch_encoder_feats(feats, n_mat, ctx->d_enc, latents_dev, nullptr, s), "encoder");
+  FAB_CUDA(ctx, launch_encoder_raw(ctx->d_enc_raw, n_mat, ctx->d_enc, nullptr, latents_dev, nullptr, s), "encoder");
   return FABRIC_OK;
 }
 
@@ -87,11 +84,18 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   if (ctx->n_train_mat < 1) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no training materials set");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int M = ctx->n_train_mat;
+  // the backward's work area: [grid][width] gradient partials, [grid] loss
+  // partials and [n][32] latent-gradient rows
+  const bool tc = ctx->train_prec == FABRIC_PREC_BF16;
+  const int tc_grid = train_tc_grid(q.n, ctx->sm_count), tc_width = train_tc_partial_width(M);
+  const size_t tc_work = align_up((size_t)tc_grid * tc_width * 4) + align_up((size_t)tc_grid * 8) +
+                         align_up((size_t)q.n * kLatent * 4);
+  const size_t dwork_bytes = tc ? tc_work : decoder_backward_work_bytes(q.n, ctx->sm_count);
   const size_t need = align_up((size_t)M * kEncIn * 4) + align_up((size_t)M * kLatent * 4) +
                       align_up((size_t)M * 2 * kEncHidden * 4) +
                       align_up(((size_t)kDecParams + kEncParams) * 4) + align_up((size_t)M * kLatent * 4) +
                       align_up(encoder_backward_work_floats(M) * 4) +
-                      align_up(decoder_backward_work_bytes(q.n, ctx->sm_count)) + align_up(8) +
+                      align_up(dwork_bytes) + align_up(8) +
                       align_up(train_tc_blob_bytes());
   void *base = scratch(ctx, need);
   if (!base) return fail(ctx, FABRIC_ERR_OOM, "training scratch (%zu bytes)", need);
@@ -102,27 +106,22 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   float *grad = c.take<float>((size_t)kDecParams + kEncParams);
   float *dz = c.take<float>((size_t)M * kLatent);
   float *ework = c.take<float>(encoder_backward_work_floats(M));
-  void *dwork = c.take<uint8_t>(decoder_backward_work_bytes(q.n, ctx->sm_count));
+  uint8_t *dwork = c.take<uint8_t>(dwork_bytes);
   double *loss_tmp = c.take<double>(1);
   void *tc_blob = c.take<uint8_t>(train_tc_blob_bytes());
   double *loss = loss_dev ? loss_dev : loss_tmp;
-  FAB_CUDA(ctx, launch_material_features(ctx->d_train_raw, M, feats, s), "features");
-  FAB_CUDA(ctx, launch_encoder_feats(feats, M, ctx->d_enc, z, acts, s), "encoder forward");
-  if (ctx->train_prec == FABRIC_PREC_BF16) {
-    // the work area holds [grid][kDecParams] partials, [grid] loss partials
-    // and [n][32] latent-gradient rows, as for the FP32 path
-    const int grid = train_tc_grid(q.n, ctx->sm_count);
-    uint8_t *w = static_cast<uint8_t *>(dwork);
-    float *partial = reinterpret_cast<float *>(w);
-    size_t off = ((size_t)grid * kDecParams * 4 + 15) & ~size_t(15);
-    double *loss_part = reinterpret_cast<double *>(w + off);
-    off = (off + (size_t)grid * 8 + 15) & ~size_t(15);
-    float *rows = reinterpret_cast<float *>(w + off);
+  FAB_CUDA(ctx, launch_encoder_raw(ctx->d_train_raw, M, ctx->d_enc, feats, z, acts, s), "encoder forward");
+  if (tc) {
+    Carve w{dwork};
+    float *partial = w.take<float>((size_t)tc_grid * tc_width);
+    double *loss_part = w.take<double>((size_t)tc_grid);
+    float *rows = w.take<float>((size_t)q.n * kLatent);
     FAB_CUDA(ctx,
              launch_train_tc(q, z, M, ctx->d_dec, batch->target, ctx->loss_mode, tc_blob, partial, loss_part, rows,
                              ctx->sm_count, ctx->d_status, s),
              "tensor-core decoder forward/backward");
-    FAB_CUDA(ctx, launch_decoder_grad_finish(q, M, partial, grid, loss_part, rows, grad, loss, dz, s), "gradient sums");
+    FAB_CUDA(ctx, launch_decoder_grad_finish(q, M, partial, tc_grid, tc_width, loss_part, rows, grad, loss, dz, s),
+             "gradient sums");
   } else {
     FAB_CUDA(ctx,
              launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, ctx->loss_mode, grad, dz, loss,
@@ -135,10 +134,7 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   ctx->version += 1;
   const size_t np = (size_t)kDecParams + kEncParams;
   float *m = ctx->d_adam, *v = ctx->d_adam + np;
-  FAB_CUDA(ctx, launch_adam(ctx->d_dec, grad, m, v, kDecParams, lr, ctx->adam_step, s), "adam");
-  FAB_CUDA(ctx,
-           launch_adam(ctx->d_enc, grad + kDecParams, m + kDecParams, v + kDecParams, kEncParams, lr,
-                       ctx->adam_step, s),
+  FAB_CUDA(ctx, launch_adam(ctx->d_dec, kDecParams, ctx->d_enc, kEncParams, grad, m, v, lr, ctx->adam_step, s),
            "adam");
   return FABRIC_OK;
 }

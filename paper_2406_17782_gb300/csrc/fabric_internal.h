@@ -178,27 +178,35 @@ cudaError_t launch_encoder_feats(const float *feats, int n, const float *enc, fl
 cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc, const float *acts,
                                     const float *dz, float *denc, float *work, cudaStream_t s);
 size_t encoder_backward_work_floats(int n);
-cudaError_t launch_material_features(const fabric_material *raw, int n, float *feats, cudaStream_t s);
+// Encoder forward with the input features computed from the material
+// records (and written to feats_out, when not null, for the backward pass).
+cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *feats_out, float *z,
+                               float *acts, cudaStream_t s);
 cudaError_t launch_decoder_raw(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                                float *y_raw, int *status, cudaStream_t s);
 cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                                     const float *dy, const float *target, int loss_mode, float *ddec, float *dlat,
                                     double *loss, void *work, int sm_count, int *status, cudaStream_t s);
 size_t decoder_backward_work_bytes(int64_t n, int sm_count);
-// The fixed-order sums after a backward pass that wrote per-CTA partials:
-// parameter gradients, the loss, and the per-material latent gradients.
-cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid,
+// The fixed-order sums after a backward pass that wrote per-CTA partials
+// ([grid][width] floats): parameter gradients, the loss, and the
+// per-material latent gradients (from the partials' columns past
+// kDecParams when width > kDecParams, else from the per-row latent
+// gradients `rows`).
+cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid, int width,
                                       const double *loss_part, const float *rows, float *ddec, double *loss,
                                       float *dlat, cudaStream_t s);
 // Tensor-core (BF16) decoder training forward + backward: per-CTA gradient
 // partials [grid][kDecParams], loss partials [grid], latent-gradient rows [n][32].
 size_t train_tc_blob_bytes();
 int train_tc_grid(int64_t n, int sm_count);
+int train_tc_partial_width(int n_lat);
+cudaError_t launch_selftest_mn(const float *a, const float *b, int n, int k, float *d, int *status, cudaStream_t s);
 cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                             const float *target, int loss_mode, void *blob, float *partial, double *loss_partial,
                             float *dlat_rows, int sm_count, int *status, cudaStream_t s);
-cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, int64_t step,
-                        cudaStream_t s);
+cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const float *grad, float *m, float *v, float lr,
+                        int64_t step, cudaStream_t s);
 cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
                                double *out, void *work, cudaStream_t s);
 size_t error_stats_work_bytes(int64_t n);

@@ -284,31 +284,84 @@ __global__ void __launch_bounds__(kBwdThreads) decoder_bwd_kernel(const BwdArgs 
   }
 }
 
-// Sum per-CTA partials in CTA order: out[j] = sum_c partial[c][j].
-__global__ void reduce_partials_kernel(const float *__restrict__ partial, int n_part, int width,
-                                       float *__restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= width) return;
-  float s = 0.0f;
-  for (int c = 0; c < n_part; ++c) s += partial[(int64_t)c * width + j];
-  out[j] = s;
-}
+// Column sums out[j] = sum_c partial[c][j].  A CTA takes 32 consecutive
+// columns; its kSumSegs warps sum consecutive ranges of rows (in row order),
+// then the range sums are added in range order: a fixed order, so the
+// result does not change from run to run.
+constexpr int kSumSegs = 8;
 
-// 32 threads sum fixed strided subsets, then thread 0 sums the 32 in order.
-__global__ void reduce_loss_kernel(const double *__restrict__ part, int n, double *__restrict__ out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int c = threadIdx.x; c < n; c += 32) s += part[c];
-  red[threadIdx.x] = s;
+__device__ void reduce_loss_warp(const double *__restrict__ part, int n, double *__restrict__ out);
+
+// Columns [0, w0) go to out0, columns [w0, width) to out1.  One CTA past the
+// column blocks (when loss_out is set) sums the loss partials instead, so
+// that both reductions take one launch.
+__global__ void __launch_bounds__(32 * kSumSegs) reduce_partials_kernel(const float *__restrict__ partial,
+                                                                        int n_part, int stride, int width, int w0,
+                                                                        float *__restrict__ out0,
+                                                                        float *__restrict__ out1,
+                                                                        const double *__restrict__ loss_part,
+                                                                        double *__restrict__ loss_out) {
+  __shared__ float seg_sum[kSumSegs][32];
+  if (loss_out && blockIdx.x == gridDim.x - 1) {
+    if (threadIdx.x < 32) reduce_loss_warp(loss_part, n_part, loss_out);
+    return;
+  }
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int per = (n_part + kSumSegs - 1) / kSumSegs;
+  const int c0 = min(n_part, seg * per), c1 = min(n_part, c0 + per);
+  float s = 0.0f;
+  if (j < width) {
+    int c = c0;
+    for (; c + 4 <= c1; c += 4) {
+      float t[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] = partial[(int64_t)(c + q) * stride + j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s += t[q];
+    }
+    for (; c < c1; ++c) s += partial[(int64_t)c * stride + j];
+  }
+  seg_sum[seg][lane] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < 32; ++k) t += red[k];
-    *out = t;
+  if (seg == 0 && j < width) {
+    float tot = seg_sum[0][lane];
+#pragma unroll
+    for (int k = 1; k < kSumSegs; ++k) tot += seg_sum[k][lane];
+    if (j < w0) out0[j] = tot;
+    else out1[j - w0] = tot;
   }
 }
 
-// dlat[m][i] = sum over rows with material m (row order) of dlat_rows[row][i].
+// 32 threads (one warp) sum fixed strided subsets, then lane 0 sums the 32
+// in order.
+__device__ void reduce_loss_warp(const double *__restrict__ part, int n, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += part[c];
+  double t = 0.0;
+  for (int k = 0; k < 32; ++k) t += __shfl_sync(0xFFFFFFFFu, s, k);
+  if (lane == 0) *out = t;
+}
+
+// dlat[m][i] = sum over rows with material m of dlat_rows[row][i]; one CTA
+// per material scans every id.  Thread t takes the rows of id groups t,
+// t + 256, ... in row order (V: groups of eight ids read as one 16-byte
+// load, four groups in flight; otherwise single ids), then the 256 thread
+// sums are added in thread order, so the result is the same on every run.
+__device__ __forceinline__ void add_row(float *acc, const float *__restrict__ rows, int64_t r) {
+  const float4 *src = reinterpret_cast<const float4 *>(rows + r * kLatent);
+#pragma unroll
+  for (int k = 0; k < kLatent / 4; ++k) {
+    const float4 v = src[k];
+    acc[4 * k] += v.x;
+    acc[4 * k + 1] += v.y;
+    acc[4 * k + 2] += v.z;
+    acc[4 * k + 3] += v.w;
+  }
+}
+
+template <bool V>
 __global__ void __launch_bounds__(256) latent_segment_kernel(const uint16_t *__restrict__ mat, int64_t n,
                                                              const float *__restrict__ rows,
                                                              float *__restrict__ dlat) {
@@ -317,26 +370,35 @@ __global__ void __launch_bounds__(256) latent_segment_kernel(const uint16_t *__r
   float acc[kLatent];
 #pragma unroll
   for (int i = 0; i < kLatent; ++i) acc[i] = 0.0f;
-  // thread t takes rows t, t + 256, ... in order (coalesced across the
-  // block), reading eight material ids ahead so that their loads overlap
   const int64_t step = blockDim.x;
-  for (int64_t r = threadIdx.x; r < n; r += 8 * step) {
+  int64_t tail = 0;
+  if (V) {
+    const uint4 *ids8 = reinterpret_cast<const uint4 *>(mat);
+    const int64_t groups = n / 8;
+    tail = groups * 8;
+    for (int64_t g = threadIdx.x; g < groups; g += 4 * step) {
+      uint4 w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = g + q * step < groups ? ids8[g + q * step] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (g + q * step >= groups) break;
+        const uint32_t word[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if ((int)((word[k >> 1] >> (16 * (k & 1))) & 0xFFFFu) == m) add_row(acc, rows, 8 * (g + q * step) + k);
+        }
+      }
+    }
+  }
+  // single ids: every row (V = false), or the last n % 8 rows
+  for (int64_t r = tail + threadIdx.x; r < n; r += 8 * step) {
     int ids[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) ids[q] = r + q * step < n ? (int)mat[r + q * step] : -1;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (ids[q] != m) continue;
-      const float4 *src = reinterpret_cast<const float4 *>(rows + (r + q * step) * kLatent);
-#pragma unroll
-      for (int k = 0; k < kLatent / 4; ++k) {
-        const float4 v = src[k];
-        acc[4 * k] += v.x;
-        acc[4 * k + 1] += v.y;
-        acc[4 * k + 2] += v.z;
-        acc[4 * k + 3] += v.w;
-      }
-    }
+    for (int q = 0; q < 8; ++q)
+      if (ids[q] == m) add_row(acc, rows, r + q * step);
   }
 #pragma unroll
   for (int i = 0; i < kLatent; ++i) red[threadIdx.x][i] = acc[i];
@@ -349,12 +411,13 @@ __global__ void __launch_bounds__(256) latent_segment_kernel(const uint16_t *__r
 }
 
 // ---------------------------------------------------------------------------
-// Encoder (parameters -> latent), one material per CTA of 128 threads.
+// Encoder (parameters -> latent), kEncGroup materials per CTA of 128 threads.
 // acts (optional) [n][2][128] = pre-activations a1, a2 for the backward pass.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float lrelu(float x) { return x > 0.0f ? x : kLeaky * x; }
 
-__device__ void material_features(const fabric_material &m, float *f) {
+__device__ __forceinline__ void material_features(const fabric_material &m, float *f) {
+#pragma unroll
   for (int k = 0; k < kPatternSlots; ++k) f[k] = (m.pattern_id == k) ? 1.0f : 0.0f;
   f[kPatternSlots + 0] = m.twist_deg / 30.0f;
   f[kPatternSlots + 1] = m.incl_deg / 45.0f;
@@ -364,105 +427,252 @@ __device__ void material_features(const fabric_material &m, float *f) {
   f[kPatternSlots + 5] = m.beta[1];
 }
 
-__global__ void material_features_kernel(const fabric_material *__restrict__ raw, int n, float *__restrict__ f) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < n) material_features(raw[m], f + m * kEncIn);
+// Materials per encoder CTA: thread j reads its weight row once for all of
+// them and keeps one accumulator per material (each sum still runs over the
+// inputs in order, as for a single material).
+constexpr int kEncGroup = 4;
+
+// dot of weight row w (LEN floats, 16-byte aligned when V) with the group's
+// vectors x[g][0..LEN), one accumulator per material, inputs in order.  The
+// whole row is loaded into registers first, so that its loads are in flight
+// together rather than one dependent round trip per few elements.
+template <bool V, int LEN, int LD>
+__device__ __forceinline__ void enc_dot(const float *__restrict__ w, const float (*x)[LD], float *acc) {
+  float c[LEN];
+  if (V) {
+    const float4 *w4 = reinterpret_cast<const float4 *>(w);
+#pragma unroll
+    for (int i4 = 0; i4 < LEN / 4; ++i4) {
+      const float4 t = w4[i4];
+      c[4 * i4] = t.x;
+      c[4 * i4 + 1] = t.y;
+      c[4 * i4 + 2] = t.z;
+      c[4 * i4 + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) c[i] = w[i];
+  }
+#pragma unroll
+  for (int i = 0; i < LEN; ++i) {
+#pragma unroll
+    for (int g = 0; g < kEncGroup; ++g) acc[g] = fmaf(c[i], x[g][i], acc[g]);
+  }
 }
 
+// Same for one vector x[0..kEncHidden).
+template <bool V>
+__device__ __forceinline__ void enc_dot1(const float *__restrict__ w, const float *x, float *acc) {
+  float c[kEncHidden];
+  if (V) {
+    const float4 *w4 = reinterpret_cast<const float4 *>(w);
+#pragma unroll
+    for (int i4 = 0; i4 < kEncHidden / 4; ++i4) {
+      const float4 t = w4[i4];
+      c[4 * i4] = t.x;
+      c[4 * i4 + 1] = t.y;
+      c[4 * i4 + 2] = t.z;
+      c[4 * i4 + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kEncHidden; ++i) c[i] = w[i];
+  }
+#pragma unroll
+  for (int i = 0; i < kEncHidden; ++i) acc[0] = fmaf(c[i], x[i], acc[0]);
+}
+
+template <bool V>
 __global__ void __launch_bounds__(kEncHidden) encoder_fwd_kernel(const float *__restrict__ feats,
+                                                                 const fabric_material *__restrict__ raw,
+                                                                 float *__restrict__ feats_out, int n,
                                                                  const float *__restrict__ enc,
                                                                  float *__restrict__ z, float *__restrict__ acts) {
-  __shared__ float f[kEncIn], h1[kEncHidden], h2[kEncHidden];
-  const int m = blockIdx.x, j = threadIdx.x;
-  if (j < kEncIn) f[j] = feats[m * kEncIn + j];
-  __syncthreads();
-  float a1 = enc[kOffEb1 + j];
-  for (int i = 0; i < kEncIn; ++i) a1 = fmaf(enc[kOffE1 + j * kEncIn + i], f[i], a1);
-  h1[j] = lrelu(a1);
-  __syncthreads();
-  float a2 = enc[kOffEb2 + j] + h1[j];   // skip connection before the last activation
-  for (int i = 0; i < kEncHidden; ++i) a2 = fmaf(enc[kOffE2 + j * kEncHidden + i], h1[i], a2);
-  h2[j] = lrelu(a2);
-  if (acts) {
-    acts[(int64_t)m * 2 * kEncHidden + j] = a1;
-    acts[(int64_t)m * 2 * kEncHidden + kEncHidden + j] = a2;
+  __shared__ float f[kEncGroup][kEncIn];
+  __shared__ __align__(16) float h1[kEncGroup][kEncHidden];
+  __shared__ __align__(16) float h2[kEncGroup][kEncHidden];
+  const int m0 = blockIdx.x * kEncGroup, j = threadIdx.x;
+  const int nm = min(kEncGroup, n - m0);
+  if (raw) {
+    if (j < kEncGroup) {
+      float t[kEncIn];
+      if (j < nm) {
+        material_features(raw[m0 + j], t);
+      } else {
+#pragma unroll
+        for (int i = 0; i < kEncIn; ++i) t[i] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < kEncIn; ++i) {
+        f[j][i] = t[i];
+        if (j < nm && feats_out) feats_out[(int64_t)(m0 + j) * kEncIn + i] = t[i];
+      }
+    }
+  } else {
+    for (int t = j; t < kEncGroup * kEncIn; t += kEncHidden) {
+      const int g = t / kEncIn, i = t % kEncIn;
+      f[g][i] = g < nm ? feats[(int64_t)(m0 + g) * kEncIn + i] : 0.0f;
+    }
   }
   __syncthreads();
-  if (j < kLatent) {
-    float acc = enc[kOffEb3 + j];
-    for (int i = 0; i < kEncHidden; ++i) acc = fmaf(enc[kOffE3 + j * kEncHidden + i], h2[i], acc);
-    z[m * kLatent + j] = acc;
+  float a1[kEncGroup], a2[kEncGroup];
+  const float b1 = enc[kOffEb1 + j];
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) a1[g] = b1;
+  enc_dot<false, kEncIn, kEncIn>(enc + kOffE1 + j * kEncIn, f, a1);   // rows of 22 floats: 8-byte aligned at best
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) h1[g][j] = lrelu(a1[g]);
+  __syncthreads();
+  const float b2 = enc[kOffEb2 + j];
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) a2[g] = b2 + h1[g][j];   // skip connection before the last activation
+  enc_dot<V, kEncHidden, kEncHidden>(enc + kOffE2 + j * kEncHidden, h1, a2);
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) {
+    h2[g][j] = lrelu(a2[g]);
+    if (acts && g < nm) {
+      acts[(int64_t)(m0 + g) * 2 * kEncHidden + j] = a1[g];
+      acts[(int64_t)(m0 + g) * 2 * kEncHidden + kEncHidden + j] = a2[g];
+    }
   }
+  __syncthreads();
+  // layer 3: thread j computes latent output k = j % 32 of material j / 32
+  static_assert(kEncGroup * kLatent == kEncHidden, "one layer-3 output per thread");
+  const int k = j % kLatent, g = j / kLatent;
+  float acc[1] = {enc[kOffEb3 + k]};
+  enc_dot1<V>(enc + kOffE3 + k * kEncHidden, h2[g], acc);
+  if (g < nm) z[(int64_t)(m0 + g) * kLatent + k] = acc[0];
 }
 
 // Per material: back-propagated pre-activation gradients da1, da2 and the
-// activations h1, h2 into work [n][4][128].
-__global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float *__restrict__ enc,
+// activations h1, h2 into work [n][4][128]; kEncGroup materials per CTA.
+__global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float *__restrict__ enc, int n,
                                                                      const float *__restrict__ acts,
                                                                      const float *__restrict__ dz,
                                                                      float *__restrict__ work) {
-  __shared__ float sdz[kLatent], da2s[kEncHidden];
-  const int m = blockIdx.x, j = threadIdx.x;
-  if (j < kLatent) sdz[j] = dz[m * kLatent + j];
-  const float a1 = acts[(int64_t)m * 2 * kEncHidden + j];
-  const float a2 = acts[(int64_t)m * 2 * kEncHidden + kEncHidden + j];
+  __shared__ float sdz[kEncGroup][kLatent], da2s[kEncGroup][kEncHidden];
+  const int m0 = blockIdx.x * kEncGroup, j = threadIdx.x;
+  const int nm = min(kEncGroup, n - m0);
+  {
+    const int k = j % kLatent, g = j / kLatent;
+    sdz[g][k] = g < nm ? dz[(int64_t)(m0 + g) * kLatent + k] : 0.0f;
+  }
   __syncthreads();
-  float dh2 = 0.0f;
-  for (int k = 0; k < kLatent; ++k) dh2 = fmaf(enc[kOffE3 + k * kEncHidden + j], sdz[k], dh2);
-  const float da2 = dh2 * (a2 > 0.0f ? 1.0f : kLeaky);
-  da2s[j] = da2;
+  float dh2[kEncGroup], dh1[kEncGroup];
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) dh2[g] = 0.0f;
+  {
+    float w[kLatent];   // column j of E3, all loads in flight together
+#pragma unroll
+    for (int k = 0; k < kLatent; ++k) w[k] = enc[kOffE3 + k * kEncHidden + j];
+#pragma unroll
+    for (int k = 0; k < kLatent; ++k) {
+#pragma unroll
+      for (int g = 0; g < kEncGroup; ++g) dh2[g] = fmaf(w[k], sdz[g][k], dh2[g]);
+    }
+  }
+  float a1[kEncGroup], a2[kEncGroup];
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) {
+    const int64_t m = g < nm ? m0 + g : m0;
+    a1[g] = acts[m * 2 * kEncHidden + j];
+    a2[g] = acts[m * 2 * kEncHidden + kEncHidden + j];
+    const float da2 = dh2[g] * (a2[g] > 0.0f ? 1.0f : kLeaky);
+    da2s[g][j] = da2;
+    dh1[g] = da2;   // through the skip
+  }
   __syncthreads();
-  float dh1 = da2;   // through the skip
-  for (int o = 0; o < kEncHidden; ++o) dh1 = fmaf(enc[kOffE2 + o * kEncHidden + j], da2s[o], dh1);
-  const float da1 = dh1 * (a1 > 0.0f ? 1.0f : kLeaky);
-  float *w = work + (int64_t)m * 4 * kEncHidden;
-  w[j] = da1;
-  w[kEncHidden + j] = da2;
-  w[2 * kEncHidden + j] = lrelu(a1);
-  w[3 * kEncHidden + j] = lrelu(a2);
+  {
+    float w[kEncHidden];   // column j of E2
+#pragma unroll
+    for (int o = 0; o < kEncHidden; ++o) w[o] = enc[kOffE2 + o * kEncHidden + j];
+#pragma unroll
+    for (int o = 0; o < kEncHidden; ++o) {
+#pragma unroll
+      for (int g = 0; g < kEncGroup; ++g) dh1[g] = fmaf(w[o], da2s[g][o], dh1[g]);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) {
+    if (g >= nm) break;
+    float *w = work + (int64_t)(m0 + g) * 4 * kEncHidden;
+    w[j] = dh1[g] * (a1[g] > 0.0f ? 1.0f : kLeaky);
+    w[kEncHidden + j] = da2s[g][j];
+    w[2 * kEncHidden + j] = lrelu(a1[g]);
+    w[3 * kEncHidden + j] = lrelu(a2[g]);
+  }
 }
 
-// One thread per encoder parameter, materials summed in order.
-__global__ void encoder_grad_kernel(const float *__restrict__ feats, int n, const float *__restrict__ dz,
-                                    const float *__restrict__ work, float *__restrict__ denc) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= kEncParams) return;
-  float s = 0.0f;
-  if (e < kOffEb1) {                       // E1[j][i]
-    const int j = e / kEncIn, i = e % kEncIn;
-    for (int m = 0; m < n; ++m) s += work[(int64_t)m * 512 + j] * feats[m * kEncIn + i];
-  } else if (e < kOffE2) {                 // e1[j]
-    const int j = e - kOffEb1;
-    for (int m = 0; m < n; ++m) s += work[(int64_t)m * 512 + j];
-  } else if (e < kOffEb2) {                // E2[j][i]
-    const int j = (e - kOffE2) / kEncHidden, i = (e - kOffE2) % kEncHidden;
-    for (int m = 0; m < n; ++m) s += work[(int64_t)m * 512 + 128 + j] * work[(int64_t)m * 512 + 256 + i];
-  } else if (e < kOffE3) {                 // e2[j]
-    const int j = e - kOffEb2;
-    for (int m = 0; m < n; ++m) s += work[(int64_t)m * 512 + 128 + j];
-  } else if (e < kOffEb3) {                // E3[k][i]
-    const int k = (e - kOffE3) / kEncHidden, i = (e - kOffE3) % kEncHidden;
-    for (int m = 0; m < n; ++m) s += dz[m * kLatent + k] * work[(int64_t)m * 512 + 384 + i];
-  } else {                                 // e3[k]
-    const int k = e - kOffEb3;
-    for (int m = 0; m < n; ++m) s += dz[m * kLatent + k];
+// Encoder parameter gradients: sums over materials of outer products.  A CTA
+// takes 32 consecutive parameters; its 8 warps sum 8 consecutive material
+// ranges, then lane e of warp 0 adds the 8 range sums in order.
+constexpr int kGradSegs = 8;
+
+__device__ __forceinline__ float enc_grad_term(int e, int m, const float *__restrict__ feats,
+                                               const float *__restrict__ dz, const float *__restrict__ work) {
+  const float *w = work + (int64_t)m * 4 * kEncHidden;
+  if (e < kOffEb1) return w[e / kEncIn] * feats[(int64_t)m * kEncIn + e % kEncIn];   // E1[j][i]
+  if (e < kOffE2) return w[e - kOffEb1];                                               // e1[j]
+  if (e < kOffEb2) {                                                                   // E2[j][i]
+    const int r = e - kOffE2;
+    return w[kEncHidden + r / kEncHidden] * w[2 * kEncHidden + r % kEncHidden];
   }
-  denc[e] = s;
+  if (e < kOffE3) return w[kEncHidden + e - kOffEb2];                                  // e2[j]
+  if (e < kOffEb3) {                                                                   // E3[k][i]
+    const int r = e - kOffE3;
+    return dz[(int64_t)m * kLatent + r / kEncHidden] * w[3 * kEncHidden + r % kEncHidden];
+  }
+  return dz[(int64_t)m * kLatent + e - kOffEb3];                                       // e3[k]
+}
+
+__global__ void __launch_bounds__(32 * kGradSegs) encoder_grad_kernel(const float *__restrict__ feats, int n,
+                                                                      const float *__restrict__ dz,
+                                                                      const float *__restrict__ work,
+                                                                      float *__restrict__ denc) {
+  __shared__ float part[kGradSegs][32];
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const int per = (n + kGradSegs - 1) / kGradSegs;
+  const int m0 = min(n, seg * per), m1 = min(n, m0 + per);
+  float s = 0.0f;
+  if (e < kEncParams) {
+    int m = m0;
+    for (; m + 4 <= m1; m += 4) {
+      float t[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] = enc_grad_term(e, m + q, feats, dz, work);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s += t[q];
+    }
+    for (; m < m1; ++m) s += enc_grad_term(e, m, feats, dz, work);
+  }
+  part[seg][lane] = s;
+  __syncthreads();
+  if (seg == 0 && e < kEncParams) {
+    float tot = part[0][lane];
+#pragma unroll
+    for (int k = 1; k < kGradSegs; ++k) tot += part[k][lane];
+    denc[e] = tot;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Adam (Kingma and Ba 2015) with bias correction.
 // ---------------------------------------------------------------------------
-__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                            float *__restrict__ v, int64_t n, float lr, float bc1, float bc2) {
+// Parameters [0, n0) live in p0 and [n0, n0 + n1) in p1; g, m and v hold
+// both sets back to back.
+__global__ void adam_kernel(float *__restrict__ p0, int64_t n0, float *__restrict__ p1, int64_t n1,
+                            const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v, float lr,
+                            float bc1, float bc2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n0 + n1) return;
+  float *p = i < n0 ? p0 + i : p1 + (i - n0);
   const float gi = g[i];
   const float mi = 0.9f * m[i] + 0.1f * gi;
   const float vi = 0.999f * v[i] + 0.001f * gi * gi;
   m[i] = mi;
   v[i] = vi;
-  p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+  *p -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
 }
 
 // ---------------------------------------------------------------------------
@@ -593,6 +803,15 @@ size_t decoder_backward_work_bytes(int64_t n, int sm_count) {
   return bytes + 64;
 }
 
+namespace {
+void latent_sums(const fabric_gbuffer &g, int n_lat, const float *rows, float *dlat, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(g.material) & 15) == 0)
+    latent_segment_kernel<true><<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+  else
+    latent_segment_kernel<false><<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+}
+}  // namespace
+
 cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                                     const float *dy, const float *target, int loss_mode, float *ddec, float *dlat,
                                     double *loss, void *work, int sm_count, int *status, cudaStream_t s) {
@@ -626,29 +845,45 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
   decoder_bwd_kernel<<<grid, kBwdThreads, bwd_smem_bytes(), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  reduce_partials_kernel<<<(kDecParams + 255) / 256, 256, 0, s>>>(partial, grid, kDecParams, ddec);
-  if (loss) reduce_loss_kernel<<<1, 32, 0, s>>>(loss_part, grid, loss);
-  if (dlat) latent_segment_kernel<<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+  reduce_partials_kernel<<<(kDecParams + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s>>>(
+      partial, grid, kDecParams, kDecParams, kDecParams, ddec, nullptr, loss_part, loss);
+  if (dlat) latent_sums(g, n_lat, rows, dlat, s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid,
+cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid, int width,
                                       const double *loss_part, const float *rows, float *ddec, double *loss,
                                       float *dlat, cudaStream_t s) {
-  reduce_partials_kernel<<<(kDecParams + 255) / 256, 256, 0, s>>>(partial, grid, kDecParams, ddec);
-  if (loss) reduce_loss_kernel<<<1, 32, 0, s>>>(loss_part, grid, loss);
-  if (dlat) latent_segment_kernel<<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+  // width > kDecParams: the per-CTA partials already hold the per-material
+  // latent-gradient sums after the decoder's columns
+  const bool folded = width > kDecParams;
+  const int cols = dlat ? width : kDecParams;
+  reduce_partials_kernel<<<(cols + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s>>>(
+      partial, grid, width, cols, kDecParams, ddec, dlat, loss_part, loss);
+  if (dlat && !folded) latent_sums(g, n_lat, rows, dlat, s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_material_features(const fabric_material *raw, int n, float *feats, cudaStream_t s) {
-  material_features_kernel<<<(n + 127) / 128, 128, 0, s>>>(raw, n, feats);
-  return cudaGetLastError();
+namespace {
+void encoder_fwd(const float *feats, const fabric_material *raw, float *feats_out, int n, const float *enc, float *z,
+                 float *acts, cudaStream_t s) {
+  const int grid = (n + kEncGroup - 1) / kEncGroup;
+  if ((reinterpret_cast<uintptr_t>(enc) & 15) == 0)
+    encoder_fwd_kernel<true><<<grid, kEncHidden, 0, s>>>(feats, raw, feats_out, n, enc, z, acts);
+  else
+    encoder_fwd_kernel<false><<<grid, kEncHidden, 0, s>>>(feats, raw, feats_out, n, enc, z, acts);
 }
+}  // namespace
 
 cudaError_t launch_encoder_feats(const float *feats, int n, const float *enc, float *z, float *acts,
                                  cudaStream_t s) {
-  encoder_fwd_kernel<<<n, kEncHidden, 0, s>>>(feats, enc, z, acts);
+  encoder_fwd(feats, nullptr, nullptr, n, enc, z, acts, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *feats_out, float *z,
+                               float *acts, cudaStream_t s) {
+  encoder_fwd(nullptr, raw, feats_out, n, enc, z, acts, s);
   return cudaGetLastError();
 }
 
@@ -661,19 +896,19 @@ cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc,
   float *vec = work + (size_t)n * 2 * kEncHidden;
   if (!acts_in) {
     // recompute the forward pass to obtain the pre-activations (z discarded into vec)
-    encoder_fwd_kernel<<<n, kEncHidden, 0, s>>>(feats, enc, vec, acts);
+    encoder_fwd(feats, nullptr, nullptr, n, enc, vec, acts, s);
     acts_in = acts;
   }
-  encoder_bwd_vec_kernel<<<n, kEncHidden, 0, s>>>(enc, acts_in, dz, vec);
-  encoder_grad_kernel<<<(kEncParams + 255) / 256, 256, 0, s>>>(feats, n, dz, vec, denc);
+  encoder_bwd_vec_kernel<<<(n + kEncGroup - 1) / kEncGroup, kEncHidden, 0, s>>>(enc, n, acts_in, dz, vec);
+  encoder_grad_kernel<<<(kEncParams + 31) / 32, 32 * kGradSegs, 0, s>>>(feats, n, dz, vec, denc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, int64_t step,
-                        cudaStream_t s) {
+cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const float *grad, float *m, float *v, float lr,
+                        int64_t step, cudaStream_t s) {
   const float bc1 = (float)(1.0 - std::pow(0.9, (double)step));
   const float bc2 = (float)(1.0 - std::pow(0.999, (double)step));
-  adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, grad, m, v, n, lr, bc1, bc2);
+  adam_kernel<<<(unsigned)((n0 + n1 + 255) / 256), 256, 0, s>>>(p0, n0, p1, n1, grad, m, v, lr, bc1, bc2);
   return cudaGetLastError();
 }
 

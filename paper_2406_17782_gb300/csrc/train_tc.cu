@@ -5,9 +5,9 @@
 // Per tile, with one query per thread and tile row:
 //   forward   x = [z | q | 1] (K = 80) -> h1 -> h2 -> h3 -> y (N = 16, 4 used):
 //             A operands in tensor memory, B = the weights in shared memory;
-//             every activation also goes, transposed, to shared memory
-//             (j-major rows of 128 queries) for the weight gradients, and its
-//             ReLU mask stays in registers;
+//             every activation also goes to shared memory, as the query's own
+//             row in the MN-major operand layout (16-byte vector stores), for
+//             the weight gradients, and its ReLU mask stays in registers;
 //   loss      dy from Eq. 11 (or the rendered-space option), scaled by 1/B;
 //   backward  da_l = dh_l * mask_l; dh_{l-1} = da_l W_l (B = W_l transposed)
 //             and dW_l^T += h_{l-1}^T da_l (M = 128 input rows of which 65-72
@@ -29,6 +29,7 @@ namespace fab {
 namespace {
 
 constexpr int kRows = 128;
+constexpr int kThreads = 256;   // two threads per query row: warps w and w + 4 share lane quadrant w
 constexpr int kK1 = 80;    // x = z (32) | q (39) | 1 | pad
 constexpr int kKH = 80;    // h (64) | 1 | pad
 constexpr long long kWaitCycles = 4000000000ll;
@@ -44,17 +45,43 @@ constexpr uint32_t kW2t = kW3t + 64 * 64 * 2;         // [64][64]  W2^T
 constexpr uint32_t kW1t = kW2t + 64 * 64 * 2;         // [32][64]  W1[:, :32]^T
 constexpr uint32_t kBlob = kW1t + 32 * 64 * 2;
 
-// Shared memory after the 1 KB header.
+// Shared memory after the 1 KB header.  The weight-gradient operands act^T
+// (M = 128 inputs, 0..79 used) and da (N = 64 or 16 outputs), both with
+// K = the tile's 128 queries, are MN-major: element (j, r) -- input or output
+// j of query r -- lives at mn_offset(j, r, width), core matrices of 8 j by 8 r
+// (16-byte rows along j), 128 bytes apart along j, width * 16 bytes apart
+// along r.
 constexpr uint32_t kSmWts = 0;
-constexpr uint32_t kSmXT = (kBlob + 1023) / 1024 * 1024;   // [128][128] x^T (rows 0..79 used)
+constexpr uint32_t kSmXT = (kBlob + 1023) / 1024 * 1024;   // x^T: 128 inputs x 128 queries (0..79 used)
 constexpr uint32_t kSmH1T = kSmXT + 128 * 128 * 2;
 constexpr uint32_t kSmH2T = kSmH1T + 128 * 128 * 2;
 constexpr uint32_t kSmH3T = kSmH2T + 128 * 128 * 2;
-constexpr uint32_t kSmDaT = kSmH3T + 128 * 128 * 2;        // [64][128] da^T
+constexpr uint32_t kSmDaT = kSmH3T + 128 * 128 * 2;        // da: 64 outputs x 128 queries
 constexpr uint32_t kSmTotal = kSmDaT + 64 * 128 * 2;
 constexpr size_t kDynSmem = 1024 /* align */ + 1024 /* header */ + kSmTotal;
 
 constexpr uint32_t kColD = 0, kColA = 64, kColW1 = 128, kColW2 = 192, kColW3 = 256, kColW4 = 320;
+
+// Instruction-descriptor bits: A and B read MN-major (transposed).
+constexpr uint32_t kTransA = 1u << 15, kTransB = 1u << 16;
+
+// Shared-memory descriptor of an MN-major operand without swizzle: here the
+// leading-dimension field is the stride between 8-deep groups along K and the
+// stride-dimension field the stride between 8-wide core matrices along M or N
+// (the reverse of the K-major roles; checked by fabric_selftest_mma_mn).
+__device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t k_group_stride) {
+  return tc::smem_desc(saddr, k_group_stride, 128u);
+}
+
+__host__ __device__ constexpr uint32_t mn_offset(int j, int r, int width) {
+  return (uint32_t)((j & 7) * 2 + (r & 7) * 16 + (j >> 3) * 128 + (r >> 3) * width * 16);
+}
+
+// Eight consecutive values j0..j0+7 (j0 % 8 == 0) of query r, packed as four
+// BF16 pairs, into an MN-major operand of the given width.
+__device__ __forceinline__ void st_row8(uint8_t *base, int j0, int r, int width, const uint32_t *w4) {
+  *reinterpret_cast<uint4 *>(base + mn_offset(j0, r, width)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+}
 
 __device__ __forceinline__ void put(uint8_t *base, uint32_t off, float v) {
   *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(v);
@@ -92,16 +119,12 @@ struct TrainTcArgs {
   const float *target;    // [n][4]
   int loss_mode;
   float inv_batch;
-  float *partial;         // [grid][kDecParams]
+  float *partial;         // [grid][partial_width]
+  int partial_width;      // kDecParams, or kDecParams + 32 n_lat with the latent sums folded in
   double *loss_partial;   // [grid]
   float *dlat_rows;       // [n][32]
   int *status;
 };
-
-// Element (row, k) of a K-major [rows][K] BF16 tile in shared memory.
-__device__ __forceinline__ void st_bf16(uint8_t *base, int row, int k, int K, float v) {
-  *reinterpret_cast<__nv_bfloat16 *>(base + tc::core_offset(row, k, K)) = __float2bfloat16_rn(v);
-}
 
 // 128-thread barrier of the CTA with tensor-memory ordering on both sides.
 __device__ __forceinline__ void sync_all() {
@@ -110,7 +133,7 @@ __device__ __forceinline__ void sync_all() {
   tc::tc_fence_after();
 }
 
-__global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bar_w = reinterpret_cast<uint64_t *>(smem);
@@ -120,9 +143,11 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
   uint8_t *sm = smem + 1024;
   uint8_t *wts = sm + kSmWts, *xT = sm + kSmXT, *h1T = sm + kSmH1T, *h2T = sm + kSmH2T, *h3T = sm + kSmH3T;
   uint8_t *daT = sm + kSmDaT;
-  const int r = threadIdx.x;                 // tile row (query) and tensor-memory lane
-  const int warp = r >> 5;
-  const bool lead = r == 0;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int hf = warp >> 2;                      // which half of every epilogue's columns
+  const int r = ((warp & 3) << 5) | (tid & 31);  // tile row (query) = tensor-memory lane
+  const bool lead = tid == 0;
 
   if (lead) {
     tc::mbar_init(bar_w, 1);
@@ -130,13 +155,13 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
-  // unused rows of the transposed buffers stay zero
-  for (uint32_t e = r; e < (kSmDaT + 64 * 128 * 2 - kSmXT) / 16; e += kRows)
+  // unused rows of the gradient operands stay zero
+  for (uint32_t e = tid; e < (kSmDaT + 64 * 128 * 2 - kSmXT) / 16; e += kThreads)
     reinterpret_cast<uint4 *>(xT)[e] = make_uint4(0u, 0u, 0u, 0u);
   tc::fence_proxy_async_smem();
   sync_all();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;   // this warp's lane quadrant
   const uint32_t t_d = tmem + lane + kColD, t_a = tmem + lane + kColA;
   if (lead) {
     tc::mbar_arrive_expect_tx(bar_w, kBlob);
@@ -157,12 +182,14 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
       tc::mma_f16_ts(tmem + d_col, tmem + kColA + 8u * kk, bd, tc::idesc_bf16(128, N), kk > 0 ? 1u : 0u);
     }
   };
-  // dW^T (M = 128 input rows, N outputs) += act^T (shared) by da^T (shared), K = 128 queries
+  // dW^T (M = 128 input rows, N outputs) += act^T (shared) by da (shared),
+  // K = 128 queries, both operands MN-major: K = 16 spans two 8-query groups
   auto mma_dw = [&](uint32_t d_col, uint32_t actT, int N, bool acc) {
+    const uint32_t kg_a = 128u * 16u, kg_b = (uint32_t)N * 16u;   // bytes per 8-query group
     for (int kk = 0; kk < kRows / 16; ++kk) {
-      const uint64_t ad = tc::smem_desc(actT + kk * 256u, 128u, kRows * 16u);
-      const uint64_t bd = tc::smem_desc(s_daT + kk * 256u, 128u, kRows * 16u);
-      tc::mma_bf16(tmem + d_col, ad, bd, tc::idesc_bf16(128, N), (acc || kk > 0) ? 1u : 0u);
+      const uint64_t ad = mn_desc(actT + kk * 2u * kg_a, kg_a);
+      const uint64_t bd = mn_desc(s_daT + kk * 2u * kg_b, kg_b);
+      tc::mma_bf16(tmem + d_col, ad, bd, tc::idesc_bf16(128, N) | kTransA | kTransB, (acc || kk > 0) ? 1u : 0u);
     }
   };
   // all threads: make the stores visible, then the lead issues `issue` and
@@ -182,70 +209,79 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
     tc::tc_fence_after();
     return __syncthreads_and(w);
   };
+  // 32 activations of this half (columns c0 .. c0 + 31 of a 64-wide layer)
+  // into the next A operand (16 columns) and the MN-major copy
+  auto put_half = [&](const float *v, uint8_t *mn, int width, int c0) {
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = tc::pack_bf16(v[2 * k], v[2 * k + 1]);
+    tc::tmem_st16(t_a + c0 / 2, w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st_row8(mn, c0 + 8 * q, r, width, w + 4 * q);
+  };
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int64_t p = tile * kRows + r;
     int mat = p < a.g.n ? (int)a.g.material[p] : -1;
     if (mat >= a.n_lat) {
-      atomicOr(a.status, kStatusBadMaterial);
+      if (hf == 0) atomicOr(a.status, kStatusBadMaterial);
       mat = -1;
     }
     const bool valid = mat >= 0;
-    // ---- x = [z | q | 1 | 0] into the A operand and x^T
-    {
-      float x[kK1];
+    // ---- x = [z | q | 1 | 0] into the A operand and the MN-major x^T:
+    // half 0 writes the latent (inputs 0..31), half 1 the query features,
+    // the constant one and the padding (inputs 32..79)
+    if (hf == 0) {
+      float x[32];
 #pragma unroll
-      for (int i = 0; i < kK1; ++i) x[i] = 0.0f;
+      for (int i = 0; i < 32; ++i) x[i] = valid ? a.latents[(int64_t)mat * kLatent + i] : 0.0f;
+      put_half(x, xT, 128, 0);
+    } else {
+      float x[48];
+#pragma unroll
+      for (int i = 0; i < 48; ++i) x[i] = 0.0f;
       if (valid) {
-        for (int i = 0; i < kLatent; ++i) x[i] = a.latents[(int64_t)mat * kLatent + i];
-        query_features(a.g, p, x + kLatent);
-        x[kDecIn] = 1.0f;
+        query_features(a.g, p, x);
+        x[kDecIn - kLatent] = 1.0f;
       }
+      put_half(x, xT, 128, 32);
       uint32_t w[8];
 #pragma unroll
-      for (int c = 0; c < kK1 / 16; ++c) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = tc::pack_bf16(x[16 * c + 2 * k], x[16 * c + 2 * k + 1]);
-        tc::tmem_st8(t_a + 8 * c, w);
-      }
-#pragma unroll
-      for (int j = 0; j < kK1; ++j) st_bf16(xT, j, r, kRows, x[j]);
+      for (int k = 0; k < 8; ++k) w[k] = tc::pack_bf16(x[32 + 2 * k], x[32 + 2 * k + 1]);
+      tc::tmem_st8(t_a + 32, w);
+      st_row8(xT, 64, r, 128, w);
+      st_row8(xT, 72, r, 128, w + 4);
     }
-    // ---- forward: three hidden layers (ReLU masks in registers) and the head
-    uint32_t mask[3][2];
+    // ---- forward: three hidden layers (ReLU masks of this half's columns
+    // in registers) and the head
+    uint32_t mask[3];
     const uint32_t wf[3] = {s_w + kW1f, s_w + kW2f, s_w + kW3f};
     uint8_t *const hT[3] = {h1T, h2T, h3T};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       if (!round([&] { mma_ts(kColD, wf[l], l == 0 ? kK1 : kKH, 64); })) { ok = false; break; }
-      float acc[64];
-      tc::tmem_ld32(t_d, acc);
-      tc::tmem_ld32(t_d + 32, acc + 32);
+      float acc[32];
+      tc::tmem_ld32(t_d + 32 * hf, acc);
       tc::tmem_ld_wait();
-      mask[l][0] = mask[l][1] = 0u;
-      float h[kKH];
+      mask[l] = 0u;
 #pragma unroll
-      for (int j = 0; j < 64; ++j) {
+      for (int j = 0; j < 32; ++j) {
         const bool on = valid && acc[j] > 0.0f;
-        mask[l][j >> 5] |= on ? (1u << (j & 31)) : 0u;
-        h[j] = on ? acc[j] : 0.0f;
+        mask[l] |= on ? (1u << j) : 0u;
+        acc[j] = on ? acc[j] : 0.0f;
       }
-#pragma unroll
-      for (int j = 64; j < kKH; ++j) h[j] = (j == 64 && valid) ? 1.0f : 0.0f;
-      uint32_t w[8];
-#pragma unroll
-      for (int c = 0; c < kKH / 16; ++c) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = tc::pack_bf16(h[16 * c + 2 * k], h[16 * c + 2 * k + 1]);
-        tc::tmem_st8(t_a + 8 * c, w);
+      put_half(acc, hT[l], 128, 32 * hf);
+      if (hf == 1) {   // constant-one input of the next layer and padding, K = 64..79
+        uint32_t w[8] = {valid ? tc::pack_bf16(1.0f, 0.0f) : 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        tc::tmem_st8(t_a + 32, w);
+        st_row8(hT[l], 64, r, 128, w);
+        st_row8(hT[l], 72, r, 128, w + 4);
       }
-#pragma unroll
-      for (int j = 0; j < 65; ++j) st_bf16(hT[l], j, r, kRows, h[j]);
     }
     if (!ok) break;
     if (!round([&] { mma_ts(kColD, s_w + kW4f, kKH, 16); })) { ok = false; break; }
-    // ---- loss and the head's gradient da4 (A operand, K = 16, and da4^T)
-    {
+    // ---- loss and the head's gradient da4 (A operand, K = 16, and da4)
+    if (hf == 0) {
       float y[4];
       tc::tmem_ld4(t_d, y);
       tc::tmem_ld_wait();
@@ -257,8 +293,8 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
       }
       uint32_t w[8] = {tc::pack_bf16(d4[0], d4[1]), tc::pack_bf16(d4[2], d4[3]), 0u, 0u, 0u, 0u, 0u, 0u};
       tc::tmem_st8(t_a, w);
-#pragma unroll
-      for (int o = 0; o < 16; ++o) st_bf16(daT, o, r, kRows, o < 4 ? d4[o] : 0.0f);
+      st_row8(daT, 0, r, 16, w);
+      st_row8(daT, 8, r, 16, w + 4);
     }
     // ---- backward: dh_{l} = da_{l+1} W_{l+1}; dW_{l+1}^T += h_l^T da_{l+1}
     const uint32_t wt[3] = {s_w + kW2t, s_w + kW3t, s_w + kW4t};   // transposed W2, W3, W4
@@ -272,43 +308,35 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
             mma_ts(kColD, wt[l], Kin, 64);
             mma_dw(cdw[l], hTa[l], Nw, !first);
           })) { ok = false; break; }
-      float acc[64];
-      tc::tmem_ld32(t_d, acc);
-      tc::tmem_ld32(t_d + 32, acc + 32);
+      float acc[32];
+      tc::tmem_ld32(t_d + 32 * hf, acc);
       tc::tmem_ld_wait();
-      float da[64];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) da[j] = (mask[l][j >> 5] >> (j & 31)) & 1u ? acc[j] : 0.0f;
-      uint32_t w[8];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = tc::pack_bf16(da[16 * c + 2 * k], da[16 * c + 2 * k + 1]);
-        tc::tmem_st8(t_a + 8 * c, w);
-      }
-#pragma unroll
-      for (int o = 0; o < 64; ++o) st_bf16(daT, o, r, kRows, da[o]);
+      for (int j = 0; j < 32; ++j) acc[j] = (mask[l] >> j) & 1u ? acc[j] : 0.0f;
+      put_half(acc, daT, 64, 32 * hf);
     }
     if (!ok) break;
-    // ---- dz rows = da1 W1[:, :32]; dW1^T += x^T da1
+    // ---- dz rows = da1 W1[:, :32] (16 columns per half); dW1^T += x^T da1
     if (!round([&] {
           mma_ts(kColD, s_w + kW1t, 64, 32);
           mma_dw(kColW1, s_xT, 64, !first);
         })) { ok = false; break; }
     {
-      float dz[32];
-      tc::tmem_ld32(t_d, dz);
+      float dz[16];
+      tc::tmem_ld16(t_d + 16 * hf, dz);
       tc::tmem_ld_wait();
       if (p < a.g.n) {
-        float4 *out = reinterpret_cast<float4 *>(a.dlat_rows + p * kLatent);
+        float4 *out = reinterpret_cast<float4 *>(a.dlat_rows + p * kLatent + 16 * hf);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) out[i] = make_float4(dz[4 * i], dz[4 * i + 1], dz[4 * i + 2], dz[4 * i + 3]);
+        for (int i = 0; i < 4; ++i) out[i] = make_float4(dz[4 * i], dz[4 * i + 1], dz[4 * i + 2], dz[4 * i + 3]);
       }
     }
     first = false;
   }
-  // ---- this CTA's gradient partials: lane j holds row j of every dW^T
-  float *out = a.partial + (int64_t)blockIdx.x * kDecParams;
+  ok = __syncthreads_and(ok);   // one verdict for the CTA before the barriers below
+  // ---- this CTA's gradient partials: lane j holds row j of every dW^T;
+  // the two halves take alternate 16-column chunks
+  float *out = a.partial + (int64_t)blockIdx.x * a.partial_width;
   if (ok) {
     const int j = r;
     const uint32_t t_row = tmem + lane;
@@ -317,7 +345,7 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
       const int offW = l == 0 ? kOffW1 : l == 1 ? kOffW2 : l == 2 ? kOffW3 : kOffW4;
       const int offB = l == 0 ? kOffB1 : l == 1 ? kOffB2 : l == 2 ? kOffB3 : kOffB4;
       const uint32_t col = l == 0 ? kColW1 : l == 1 ? kColW2 : l == 2 ? kColW3 : kColW4;
-      for (int c = 0; c < N; c += 16) {
+      for (int c = 16 * hf; c < N; c += 32) {
         float v[16];
         tc::tmem_ld16(t_row + col + c, v);
         tc::tmem_ld_wait();
@@ -332,9 +360,57 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
       }
     }
   }
-  loss_red[r] = loss_acc;
+  // ---- per-material sums of this CTA's latent-gradient rows, in row order,
+  // into the partials' columns past kDecParams (the operand buffers are free
+  // now).  The CTA's tiles are staged in shared memory as many at a time as
+  // fit; warp w then walks, in row order, the rows of the materials m with
+  // m % 8 == w (found with ballots), so no two warps touch one sum.
+  if (ok && a.partial_width > kDecParams) {
+    float *acc = reinterpret_cast<float *>(sm);                   // [n_lat][32]
+    float *stage = acc + (size_t)a.n_lat * kLatent;                // [group][128][32]
+    const int group = (int)((kSmTotal - (size_t)a.n_lat * kLatent * 4) / (kRows * (kLatent * 4 + 4)));
+    int *ids = reinterpret_cast<int *>(stage + (size_t)group * kRows * kLatent);   // [group][128]
+    const int lane32 = tid & 31;
+    __syncthreads();
+    for (int e = tid; e < a.n_lat * kLatent; e += kThreads) acc[e] = 0.0f;
+    for (int64_t t0 = blockIdx.x; t0 < n_tiles; t0 += (int64_t)group * gridDim.x) {
+      int nt = 0;   // tiles in this group
+      while (nt < group && t0 + (int64_t)nt * gridDim.x < n_tiles) ++nt;
+      __syncthreads();
+      for (int e = tid; e < nt * kRows * (kLatent / 4); e += kThreads) {
+        const int t = e / (kRows * (kLatent / 4)), rest = e % (kRows * (kLatent / 4));
+        const int64_t row = (t0 + (int64_t)t * gridDim.x) * kRows + rest / (kLatent / 4);
+        reinterpret_cast<float4 *>(stage)[e] =
+            row < a.g.n ? reinterpret_cast<const float4 *>(a.dlat_rows)[row * (kLatent / 4) + rest % (kLatent / 4)]
+                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+      for (int e = tid; e < nt * kRows; e += kThreads) {
+        const int64_t row = (t0 + (int64_t)(e / kRows) * gridDim.x) * kRows + e % kRows;
+        const int m = row < a.g.n ? (int)a.g.material[row] : -1;
+        ids[e] = m < a.n_lat ? m : -1;
+      }
+      __syncthreads();
+      for (int t = 0; t < nt; ++t) {
+#pragma unroll
+        for (int k = 0; k < kRows / 32; ++k) {
+          const int q0 = t * kRows + 32 * k;
+          const int m_l = ids[q0 + lane32];
+          uint32_t hit = __ballot_sync(0xFFFFFFFFu, m_l >= 0 && (m_l & 7) == warp);
+          while (hit) {
+            const int b = __ffs(hit) - 1;
+            hit &= hit - 1;
+            const int m = __shfl_sync(0xFFFFFFFFu, m_l, b);
+            acc[m * kLatent + lane32] += stage[(size_t)(q0 + b) * kLatent + lane32];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < a.n_lat * kLatent; e += kThreads) out[kDecParams + e] = first ? 0.0f : acc[e];
+  }
+  if (hf == 0) loss_red[r] = loss_acc;
   __syncthreads();
-  if (r == 0) {
+  if (tid == 0) {
     double s = 0.0;
     for (int k = 0; k < kRows; ++k) s += loss_red[k];
     a.loss_partial[blockIdx.x] = s;
@@ -352,9 +428,66 @@ __global__ void __launch_bounds__(kRows, 1) train_tc_kernel(const TrainTcArgs a)
   }
 }
 
+// ---- self-test of the MN-major operands: d[128][n] = a[128][k] b[n][k]^T
+// with a and b stored by mn_offset (the weight-gradient layout above).
+__global__ void __launch_bounds__(128, 1) selftest_mn_kernel(const float *__restrict__ A,
+                                                              const float *__restrict__ B, int n, int k,
+                                                              float *__restrict__ D, int *status) {
+  __shared__ __align__(1024) uint8_t sa[128 * 64 * 2];
+  __shared__ __align__(1024) uint8_t sb[64 * 64 * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < 128 * k; e += 128) put(sa, mn_offset(e / k, e % k, 128), A[e]);
+  for (int e = tid; e < n * k; e += 128) put(sb, mn_offset(e / k, e % k, n), B[e]);
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&slot, 64);
+  tc::fence_proxy_async_smem();
+  sync_all();
+  const uint32_t tmem = slot;
+  if (tid == 0) {
+    const uint32_t kg_a = 128u * 16u, kg_b = (uint32_t)n * 16u;
+    for (int kk = 0; kk < k / 16; ++kk)
+      tc::mma_bf16(tmem, mn_desc(tc::smem_addr(sa) + kk * 2u * kg_a, kg_a),
+                   mn_desc(tc::smem_addr(sb) + kk * 2u * kg_b, kg_b), tc::idesc_bf16(128, n) | kTransA | kTransB,
+                   kk > 0 ? 1u : 0u);
+    tc::mma_commit(&bar);
+  }
+  const bool ok = tc::mbar_wait(&bar, 0, kWaitCycles);
+  if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
+  tc::tc_fence_after();
+  if (__syncthreads_and(ok)) {
+    for (int c = 0; c < n; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int e = 0; e < 16; ++e) D[tid * n + c + e] = v[e];
+    }
+  }
+  sync_all();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
 }  // namespace
 
+cudaError_t launch_selftest_mn(const float *a, const float *b, int n, int k, float *d, int *status, cudaStream_t s) {
+  selftest_mn_kernel<<<1, 128, 0, s>>>(a, b, n, k, d, status);
+  return cudaGetLastError();
+}
+
 size_t train_tc_blob_bytes() { return kBlob; }
+
+// Materials up to this count have their latent-gradient sums folded into the
+// kernel's per-CTA partials (their sums, one tile of staged rows and its ids
+// fit in the operand buffers); more take the separate per-material kernel.
+int train_tc_partial_width(int n_lat) {
+  const size_t need = (size_t)n_lat * kLatent * 4 + kRows * (kLatent * 4 + 4);   // sums + one staged tile
+  return need <= kSmTotal ? kDecParams + kLatent * n_lat : kDecParams;
+}
 
 int train_tc_grid(int64_t n, int sm_count) {
   const int64_t tiles = (n + kRows - 1) / kRows;
@@ -382,10 +515,11 @@ cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n
   a.loss_mode = loss_mode;
   a.inv_batch = 1.0f / (float)(g.n > 0 ? g.n : 1);
   a.partial = partial;
+  a.partial_width = train_tc_partial_width(n_lat);
   a.loss_partial = loss_partial;
   a.dlat_rows = dlat_rows;
   a.status = status;
-  train_tc_kernel<<<train_tc_grid(g.n, sm_count), kRows, kDynSmem, s>>>(a);
+  train_tc_kernel<<<train_tc_grid(g.n, sm_count), kThreads, kDynSmem, s>>>(a);
   return cudaGetLastError();
 }
 

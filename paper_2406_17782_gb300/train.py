@@ -101,15 +101,16 @@ def _errors(fab, a, gt, g):
             "rmse_fp": math.sqrt(raw[0] / n), "rel_l2_fp": math.sqrt(raw[0] / raw[1]), "max_abs_fp": float(raw[2])}
 
 
-def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(1, 2, 4, 8, 16)):
+def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(1, 2, 4, 8, 16), gbuf=None):
     """Error of the neural 1080p frame, and of the reference at lower sample
     counts, against the reference at gt_spp.  `rmse` / `rel_l2`: the frame
     as rendered under a unit directional light, f_P <wi . n_s> per RGB
     channel (the paper's results are direct-lit renders, Sec. 6); `*_fp`:
-    the raw f_P values."""
+    the raw f_P values.  `gbuf`: a host G-buffer of the frame's materials
+    (default: the 1080p frame)."""
     mats = W.frame_materials()
     fab.set_materials(mats)
-    g = GBuffer.from_numpy(W.frame_gbuffer())
+    g = GBuffer.from_numpy(W.frame_gbuffer() if gbuf is None else gbuf)
     gt, _ = fab.shade_reference(g, gt_spp[0], gt_spp[1], 0x6721)
     lat = fab.encode_params(mats)
     out = {}

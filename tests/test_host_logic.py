@@ -87,6 +87,20 @@ def test_frame_gbuffer_recipe():
     assert np.all(m[:, :240] == 0) and np.all(m[:, -240:] == 7)
 
 
+def test_multiscale_gbuffer_recipe():
+    f = W.frame_gbuffer()
+    g = W.multiscale_gbuffer()
+    # everything but the footprint is the 1080p frame's
+    for k in ("u", "v", "wi", "wo", "material"):
+        assert np.array_equal(f[k], g[k])
+    side = 2.0 * g["radius"].astype(np.float64)
+    assert side.min() > 0 and side.max() <= 5.0 + 1e-5
+    # Table 2: half the sides in (0, 1), half in (1, 5), uniform within each
+    small = side < 1.0
+    assert abs(small.mean() - 0.5) < 0.01
+    assert abs(side[small].mean() - 0.5) < 0.01 and abs(side[~small].mean() - 3.0) < 0.01
+
+
 def test_batched_4k_recipe():
     segs, n = W.batched_4k()
     assert len(segs) == 1 + 4 * 64

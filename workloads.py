@@ -14,6 +14,9 @@ available; all at the paper's 1920x1080 resolution, Sec. 6):
   log-uniform in [1e-4, 1e-1] uv units, wi and wo uniform in solid angle on the
   upper hemisphere, eight materials (one per weave) in eight vertical bands of
   240 px, as in the paper's eight-fabric sofa scene.
+* ``multiscale_gbuffer``: the same frame with footprint sides drawn as in the
+  paper's Table 2 (half U(0,1), half U(1,5) periods), the regime where a pixel
+  covers up to several weave repeats; used only to measure image error.
 * ``training_queries``: half frame-like queries, half drawn from the paper's
   Table 2 (footprint centre U(0,1)^2, side U(0,1) or U(1,5) periods, (x, y) of
   both directions U(-1,1)^2 inside the unit disc).
@@ -146,6 +149,19 @@ def frame_gbuffer(width: int = 1920, height: int = 1080, n_materials: int = N_PA
     material = np.minimum(x // band, n_materials - 1).astype(np.uint16)
     return dict(u=u, v=v, radius=radius, wi=wi, wo=wo, material=material,
                 width=width, height=height)
+
+
+def multiscale_gbuffer(width: int = 1920, height: int = 1080, n_materials: int = N_PATTERNS,
+                       config: int = 2) -> dict:
+    """``frame_gbuffer`` with the footprint radius replaced: side s drawn as
+    in Table 2 (U(0,1) or U(1,5) periods with equal odds), radius = s / 2."""
+    g = frame_gbuffer(width, height, n_materials, config)
+    rng = rng_for(config, "multiscale-footprint")
+    n = width * height
+    big = rng.random(n) < 0.5
+    side = np.where(big, rng.uniform(1.0, 5.0, n), rng.uniform(0.0, 1.0, n))
+    g["radius"] = np.maximum(side / 2.0, 1e-6).astype(np.float32)
+    return g
 
 
 def subset(gbuf: dict, idx: np.ndarray) -> dict:
