@@ -553,6 +553,19 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
   __shared__ float sdz[kEncGroup][kLatent], da2s[kEncGroup][kEncHidden];
   const int m0 = blockIdx.x * kEncGroup, j = threadIdx.x;
   const int nm = min(kEncGroup, n - m0);
+  // every global load of the kernel first, so that they are in flight
+  // together: columns j of E3 and E2, the activations and dz
+  float w3[kLatent], w2[kEncHidden], a1[kEncGroup], a2[kEncGroup];
+#pragma unroll
+  for (int k = 0; k < kLatent; ++k) w3[k] = enc[kOffE3 + k * kEncHidden + j];
+#pragma unroll
+  for (int o = 0; o < kEncHidden; ++o) w2[o] = enc[kOffE2 + o * kEncHidden + j];
+#pragma unroll
+  for (int g = 0; g < kEncGroup; ++g) {
+    const int64_t m = g < nm ? m0 + g : m0;
+    a1[g] = acts[m * 2 * kEncHidden + j];
+    a2[g] = acts[m * 2 * kEncHidden + kEncHidden + j];
+  }
   {
     const int k = j % kLatent, g = j / kLatent;
     sdz[g][k] = g < nm ? dz[(int64_t)(m0 + g) * kLatent + k] : 0.0f;
@@ -561,36 +574,22 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
   float dh2[kEncGroup], dh1[kEncGroup];
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) dh2[g] = 0.0f;
-  {
-    float w[kLatent];   // column j of E3, all loads in flight together
 #pragma unroll
-    for (int k = 0; k < kLatent; ++k) w[k] = enc[kOffE3 + k * kEncHidden + j];
+  for (int k = 0; k < kLatent; ++k) {
 #pragma unroll
-    for (int k = 0; k < kLatent; ++k) {
-#pragma unroll
-      for (int g = 0; g < kEncGroup; ++g) dh2[g] = fmaf(w[k], sdz[g][k], dh2[g]);
-    }
+    for (int g = 0; g < kEncGroup; ++g) dh2[g] = fmaf(w3[k], sdz[g][k], dh2[g]);
   }
-  float a1[kEncGroup], a2[kEncGroup];
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) {
-    const int64_t m = g < nm ? m0 + g : m0;
-    a1[g] = acts[m * 2 * kEncHidden + j];
-    a2[g] = acts[m * 2 * kEncHidden + kEncHidden + j];
     const float da2 = dh2[g] * (a2[g] > 0.0f ? 1.0f : kLeaky);
     da2s[g][j] = da2;
     dh1[g] = da2;   // through the skip
   }
   __syncthreads();
-  {
-    float w[kEncHidden];   // column j of E2
 #pragma unroll
-    for (int o = 0; o < kEncHidden; ++o) w[o] = enc[kOffE2 + o * kEncHidden + j];
+  for (int o = 0; o < kEncHidden; ++o) {
 #pragma unroll
-    for (int o = 0; o < kEncHidden; ++o) {
-#pragma unroll
-      for (int g = 0; g < kEncGroup; ++g) dh1[g] = fmaf(w[o], da2s[g][o], dh1[g]);
-    }
+    for (int g = 0; g < kEncGroup; ++g) dh1[g] = fmaf(w2[o], da2s[g][o], dh1[g]);
   }
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) {
