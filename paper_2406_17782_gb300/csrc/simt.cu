@@ -602,56 +602,90 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
   }
 }
 
-// Encoder parameter gradients: sums over materials of outer products.  A CTA
-// takes 32 consecutive parameters; its 8 warps sum 8 consecutive material
-// ranges, then lane e of warp 0 adds the 8 range sums in order.
-constexpr int kGradSegs = 8;
+// Encoder parameter gradients: every block is a sum over materials of outer
+// products, out[r][c] = sum_m L[m][r] R[m][c] (R = 1 for the biases).  A CTA
+// takes a 32 x 32 block of one of them: it stages 64 materials' rows of L
+// and R at a time in shared memory (all of a chunk's loads in flight
+// together), and thread (w, c) accumulates rows 4w..4w+3 of column c over the
+// materials in order.
+constexpr int kGradChunk = 64;
 
-__device__ __forceinline__ float enc_grad_term(int e, int m, const float *__restrict__ feats,
-                                               const float *__restrict__ dz, const float *__restrict__ work) {
-  const float *w = work + (int64_t)m * 4 * kEncHidden;
-  if (e < kOffEb1) return w[e / kEncIn] * feats[(int64_t)m * kEncIn + e % kEncIn];   // E1[j][i]
-  if (e < kOffE2) return w[e - kOffEb1];                                               // e1[j]
-  if (e < kOffEb2) {                                                                   // E2[j][i]
-    const int r = e - kOffE2;
-    return w[kEncHidden + r / kEncHidden] * w[2 * kEncHidden + r % kEncHidden];
-  }
-  if (e < kOffE3) return w[kEncHidden + e - kOffEb2];                                  // e2[j]
-  if (e < kOffEb3) {                                                                   // E3[k][i]
-    const int r = e - kOffE3;
-    return dz[(int64_t)m * kLatent + r / kEncHidden] * w[3 * kEncHidden + r % kEncHidden];
-  }
-  return dz[(int64_t)m * kLatent + e - kOffEb3];                                       // e3[k]
+struct GradBlock {
+  int l_off, r_off;        // column offsets of L and R in their per-material rows (r_off < 0: R = 1)
+  int l_src, r_src;        // 0: work rows (512 floats), 1: feats rows (kEncIn), 2: dz rows (kLatent)
+  int rows, cols;          // extent of the whole parameter block
+  int out;                 // offset of the block in the encoder parameters
+};
+
+__constant__ GradBlock kGradBlocks[6] = {
+    {0, 0, 0, 1, kEncHidden, kEncIn, kOffE1},                              // E1[j][i] = sum da1_j f_i
+    {0, -1, 0, 0, kEncHidden, 1, kOffEb1},                                 // e1[j]
+    {kEncHidden, 2 * kEncHidden, 0, 0, kEncHidden, kEncHidden, kOffE2},    // E2[j][i] = sum da2_j h1_i
+    {kEncHidden, -1, 0, 0, kEncHidden, 1, kOffEb2},                        // e2[j]
+    {0, 3 * kEncHidden, 2, 0, kLatent, kEncHidden, kOffE3},                // E3[k][i] = sum dz_k h2_i
+    {0, -1, 2, 0, kLatent, 1, kOffEb3},                                    // e3[k]
+};
+
+__device__ __forceinline__ const float *grad_src(int src, const float *work, const float *feats, const float *dz,
+                                                 int &ld) {
+  ld = src == 0 ? 4 * kEncHidden : src == 1 ? kEncIn : kLatent;
+  return src == 0 ? work : src == 1 ? feats : dz;
 }
 
-__global__ void __launch_bounds__(32 * kGradSegs) encoder_grad_kernel(const float *__restrict__ feats, int n,
-                                                                      const float *__restrict__ dz,
-                                                                      const float *__restrict__ work,
-                                                                      float *__restrict__ denc) {
-  __shared__ float part[kGradSegs][32];
-  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
-  const int e = blockIdx.x * 32 + lane;
-  const int per = (n + kGradSegs - 1) / kGradSegs;
-  const int m0 = min(n, seg * per), m1 = min(n, m0 + per);
-  float s = 0.0f;
-  if (e < kEncParams) {
-    int m = m0;
-    for (; m + 4 <= m1; m += 4) {
-      float t[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) t[q] = enc_grad_term(e, m + q, feats, dz, work);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s += t[q];
-    }
-    for (; m < m1; ++m) s += enc_grad_term(e, m, feats, dz, work);
+// Blocks of 32 x 32 outputs, in the order of kGradBlocks.
+__host__ __device__ constexpr int grad_tiles(int rows, int cols) { return ((rows + 31) / 32) * ((cols + 31) / 32); }
+constexpr int kGradTiles = grad_tiles(kEncHidden, kEncIn) + grad_tiles(kEncHidden, 1) +
+                           grad_tiles(kEncHidden, kEncHidden) + grad_tiles(kEncHidden, 1) +
+                           grad_tiles(kLatent, kEncHidden) + grad_tiles(kLatent, 1);
+
+__global__ void __launch_bounds__(256) encoder_grad_kernel(const float *__restrict__ feats, int n,
+                                                           const float *__restrict__ dz,
+                                                           const float *__restrict__ work,
+                                                           float *__restrict__ denc) {
+  __shared__ __align__(16) float sl[kGradChunk][32];
+  __shared__ float sr[kGradChunk][32];
+  // which block, and which 32 x 32 tile of it
+  int t = blockIdx.x, b = 0;
+  while (t >= grad_tiles(kGradBlocks[b].rows, kGradBlocks[b].cols)) {
+    t -= grad_tiles(kGradBlocks[b].rows, kGradBlocks[b].cols);
+    ++b;
   }
-  part[seg][lane] = s;
-  __syncthreads();
-  if (seg == 0 && e < kEncParams) {
-    float tot = part[0][lane];
+  const GradBlock B = kGradBlocks[b];
+  const int ct = (B.cols + 31) / 32;
+  const int r0 = (t / ct) * 32, c0 = (t % ct) * 32;
+  int ldl, ldr;
+  const float *L = grad_src(B.l_src, work, feats, dz, ldl);
+  const float *R = grad_src(B.r_src, work, feats, dz, ldr);
+  const int tid = threadIdx.x, c = tid & 31, w = tid >> 5;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int m0 = 0; m0 < n; m0 += kGradChunk) {
+    const int mc = min(kGradChunk, n - m0);
+    __syncthreads();
 #pragma unroll
-    for (int k = 1; k < kGradSegs; ++k) tot += part[k][lane];
-    denc[e] = tot;
+    for (int q = 0; q < kGradChunk * 32 / 256; ++q) {
+      const int e = tid + 256 * q, mm = e >> 5, k = e & 31;
+      const bool in = mm < mc;
+      sl[mm][k] = in && r0 + k < B.rows ? L[(int64_t)(m0 + mm) * ldl + B.l_off + r0 + k] : 0.0f;
+      sr[mm][k] = !in ? 0.0f
+                      : B.r_off < 0 ? 1.0f
+                                    : (c0 + k < B.cols ? R[(int64_t)(m0 + mm) * ldr + B.r_off + c0 + k] : 0.0f);
+    }
+    __syncthreads();
+    for (int mm = 0; mm < mc; ++mm) {
+      const float4 a = reinterpret_cast<const float4 *>(sl[mm])[w];
+      const float x = sr[mm][c];
+      acc[0] = fmaf(a.x, x, acc[0]);
+      acc[1] = fmaf(a.y, x, acc[1]);
+      acc[2] = fmaf(a.z, x, acc[2]);
+      acc[3] = fmaf(a.w, x, acc[3]);
+    }
+  }
+  if (c0 + c < B.cols) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = r0 + 4 * w + k;
+      if (r < B.rows) denc[B.out + r * B.cols + c0 + c] = acc[k];
+    }
   }
 }
 
@@ -899,7 +933,7 @@ cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc,
     acts_in = acts;
   }
   encoder_bwd_vec_kernel<<<(n + kEncGroup - 1) / kEncGroup, kEncHidden, 0, s>>>(enc, n, acts_in, dz, vec);
-  encoder_grad_kernel<<<(kEncParams + 31) / 32, 32 * kGradSegs, 0, s>>>(feats, n, dz, vec, denc);
+  encoder_grad_kernel<<<kGradTiles, 256, 0, s>>>(feats, n, dz, vec, denc);
   return cudaGetLastError();
 }
 

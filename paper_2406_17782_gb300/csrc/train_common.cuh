@@ -28,15 +28,31 @@ __device__ __forceinline__ void octaves_accurate(float x, float *f16) {
   }
 }
 
-// The 39 query features of point p: enc(u) | enc(v) | log footprint | wi | wo.
-__device__ __forceinline__ void query_features(const fabric_gbuffer &g, int64_t p, float *q) {
-  octaves_accurate(g.u[p], q);
-  octaves_accurate(g.v[p], q + 16);
-  q[32] = (logf(fmaxf(g.radius[p], kRFloor)) - kLogRC0) * kLogRInvC1;
+// The 39 query features enc(u) | enc(v) | log footprint | wi | wo from the
+// point's record r = (u, v, radius, wi[3], wo[3]).
+__device__ __forceinline__ void query_features_of(const float *r, float *q) {
+  octaves_accurate(r[0], q);
+  octaves_accurate(r[1], q + 16);
+  q[32] = (logf(fmaxf(r[2], kRFloor)) - kLogRC0) * kLogRInvC1;
+  for (int i = 0; i < 6; ++i) q[33 + i] = r[3 + i];
+}
+
+// The G-buffer record of point p, as query_features_of reads it.
+__device__ __forceinline__ void load_record(const fabric_gbuffer &g, int64_t p, float *r) {
+  r[0] = g.u[p];
+  r[1] = g.v[p];
+  r[2] = g.radius[p];
   for (int i = 0; i < 3; ++i) {
-    q[33 + i] = g.wi[3 * p + i];
-    q[36 + i] = g.wo[3 * p + i];
+    r[3 + i] = g.wi[3 * p + i];
+    r[6 + i] = g.wo[3 * p + i];
   }
+}
+
+// The 39 query features of point p.
+__device__ __forceinline__ void query_features(const fabric_gbuffer &g, int64_t p, float *q) {
+  float r[9];
+  load_record(g, p, r);
+  query_features_of(r, q);
 }
 
 // d loss / d y_k for output k of one query (scaled by inv_batch); adds the

@@ -193,21 +193,23 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     }
   };
   // all threads: make the stores visible, then the lead issues `issue` and
-  // everyone waits for the products
+  // everyone waits for the products.  The verdict of each wait travels with
+  // the next round's barrier (or the one after the tile loop), so a round
+  // costs one CTA barrier; false: some thread's previous wait expired.
   auto round = [&](auto issue) -> bool {
     tc::tmem_st_wait();
     tc::fence_proxy_async_smem();
     tc::tc_fence_before();
-    __syncthreads();
+    if (!__syncthreads_and(ok)) return false;
     if (lead) {
       tc::tc_fence_after();
       issue();
       tc::mma_commit(bar_mma);
     }
-    const bool w = tc::mbar_wait_sleep(bar_mma, phase, kWaitCycles);
+    ok = tc::mbar_wait_sleep(bar_mma, phase, kWaitCycles);
     phase ^= 1u;
     tc::tc_fence_after();
-    return __syncthreads_and(w);
+    return true;
   };
   // 32 activations of this half (columns c0 .. c0 + 31 of a 64-wide layer)
   // into the next A operand (16 columns) and the MN-major copy
@@ -220,28 +222,50 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     for (int q = 0; q < 4; ++q) st_row8(mn, c0 + 8 * q, r, width, w + 4 * q);
   };
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const int64_t p = tile * kRows + r;
-    int mat = p < a.g.n ? (int)a.g.material[p] : -1;
-    if (mat >= a.n_lat) {
+  // A tile's global inputs, loaded one tile ahead (during the previous
+  // tile's backward pass): half 0 the latent row, the targets and <wi.n_s>,
+  // half 1 the G-buffer record; both the material id.
+  int in_mat = -1;
+  float in_v[kLatent], in_tg[4], in_wz = 0.0f;
+  auto load_inputs = [&](int64_t t) {
+    const int64_t q = t * kRows + r;
+    in_mat = t < n_tiles && q < a.g.n ? (int)a.g.material[q] : -1;
+    if (in_mat >= a.n_lat) {
       if (hf == 0) atomicOr(a.status, kStatusBadMaterial);
-      mat = -1;
+      in_mat = -1;
     }
+    if (hf == 0) {
+#pragma unroll
+      for (int i = 0; i < kLatent; ++i) in_v[i] = in_mat >= 0 ? a.latents[(int64_t)in_mat * kLatent + i] : 0.0f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) in_tg[k] = in_mat >= 0 ? a.target[4 * q + k] : 0.0f;
+      in_wz = in_mat >= 0 ? a.g.wi[3 * q + 2] : 0.0f;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) in_v[i] = 0.0f;
+      if (in_mat >= 0) load_record(a.g, q, in_v);
+    }
+  };
+  load_inputs(blockIdx.x);
+
+  bool fail = false;   // CTA-uniform: a round found an expired wait
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t p = tile * kRows + r;
+    const int mat = in_mat;
     const bool valid = mat >= 0;
+    float tg[4] = {in_tg[0], in_tg[1], in_tg[2], in_tg[3]};
+    const float wz = in_wz;
     // ---- x = [z | q | 1 | 0] into the A operand and the MN-major x^T:
     // half 0 writes the latent (inputs 0..31), half 1 the query features,
     // the constant one and the padding (inputs 32..79)
     if (hf == 0) {
-      float x[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = valid ? a.latents[(int64_t)mat * kLatent + i] : 0.0f;
-      put_half(x, xT, 128, 0);
+      put_half(in_v, xT, 128, 0);
     } else {
       float x[48];
 #pragma unroll
       for (int i = 0; i < 48; ++i) x[i] = 0.0f;
       if (valid) {
-        query_features(a.g, p, x);
+        query_features_of(in_v, x);
         x[kDecIn - kLatent] = 1.0f;
       }
       put_half(x, xT, 128, 32);
@@ -259,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     uint8_t *const hT[3] = {h1T, h2T, h3T};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      if (!round([&] { mma_ts(kColD, wf[l], l == 0 ? kK1 : kKH, 64); })) { ok = false; break; }
+      if (!round([&] { mma_ts(kColD, wf[l], l == 0 ? kK1 : kKH, 64); })) { fail = true; break; }
       float acc[32];
       tc::tmem_ld32(t_d + 32 * hf, acc);
       tc::tmem_ld_wait();
@@ -278,8 +302,8 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
         st_row8(hT[l], 72, r, 128, w + 4);
       }
     }
-    if (!ok) break;
-    if (!round([&] { mma_ts(kColD, s_w + kW4f, kKH, 16); })) { ok = false; break; }
+    if (fail) break;
+    if (!round([&] { mma_ts(kColD, s_w + kW4f, kKH, 16); })) { fail = true; break; }
     // ---- loss and the head's gradient da4 (A operand, K = 16, and da4)
     if (hf == 0) {
       float y[4];
@@ -288,14 +312,14 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       float d4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (valid) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          d4[k] = loss_grad(k, y[k], a.target[4 * p + k], a.g.wi[3 * p + 2], a.loss_mode, a.inv_batch, &loss_acc);
+        for (int k = 0; k < 4; ++k) d4[k] = loss_grad(k, y[k], tg[k], wz, a.loss_mode, a.inv_batch, &loss_acc);
       }
       uint32_t w[8] = {tc::pack_bf16(d4[0], d4[1]), tc::pack_bf16(d4[2], d4[3]), 0u, 0u, 0u, 0u, 0u, 0u};
       tc::tmem_st8(t_a, w);
       st_row8(daT, 0, r, 16, w);
       st_row8(daT, 8, r, 16, w + 4);
     }
+    load_inputs(tile + gridDim.x);   // the next tile's, in flight during the backward pass
     // ---- backward: dh_{l} = da_{l+1} W_{l+1}; dW_{l+1}^T += h_l^T da_{l+1}
     const uint32_t wt[3] = {s_w + kW2t, s_w + kW3t, s_w + kW4t};   // transposed W2, W3, W4
     const uint32_t hTa[3] = {s_h1T, s_h2T, s_h3T};
@@ -307,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       if (!round([&] {
             mma_ts(kColD, wt[l], Kin, 64);
             mma_dw(cdw[l], hTa[l], Nw, !first);
-          })) { ok = false; break; }
+          })) { fail = true; break; }
       float acc[32];
       tc::tmem_ld32(t_d + 32 * hf, acc);
       tc::tmem_ld_wait();
@@ -315,12 +339,12 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       for (int j = 0; j < 32; ++j) acc[j] = (mask[l] >> j) & 1u ? acc[j] : 0.0f;
       put_half(acc, daT, 64, 32 * hf);
     }
-    if (!ok) break;
+    if (fail) break;
     // ---- dz rows = da1 W1[:, :32] (16 columns per half); dW1^T += x^T da1
     if (!round([&] {
           mma_ts(kColD, s_w + kW1t, 64, 32);
           mma_dw(kColW1, s_xT, 64, !first);
-        })) { ok = false; break; }
+        })) { fail = true; break; }
     {
       float dz[16];
       tc::tmem_ld16(t_d + 16 * hf, dz);
@@ -333,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     }
     first = false;
   }
-  ok = __syncthreads_and(ok);   // one verdict for the CTA before the barriers below
+  ok = __syncthreads_and(ok && !fail);   // one verdict for the CTA before the barriers below
   // ---- this CTA's gradient partials: lane j holds row j of every dW^T;
   // the two halves take alternate 16-column chunks
   float *out = a.partial + (int64_t)blockIdx.x * a.partial_width;
