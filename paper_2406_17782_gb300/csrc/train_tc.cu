@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       issue();
       tc::mma_commit(bar_mma);
     }
-    ok = tc::mbar_wait_sleep(bar_mma, phase, kWaitCycles);
+    ok = tc::mbar_wait(bar_mma, phase, kWaitCycles);   // spin: one CTA per SM, nothing else to run
     phase ^= 1u;
     tc::tc_fence_after();
     return true;
