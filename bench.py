@@ -515,6 +515,40 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     ms_neural = None
     out["reference"] = {"ms_per_frame": ms_ref, "pts_per_s": N_POINTS / (ms_ref * 1e-3), "spp": 256,
                         "sample_evals_per_s": N_POINTS * 256 / (ms_ref * 1e-3)}
+    # FP64 image-wide error reduction: the 1080p RGB frame against another,
+    # and two 2^25-element arrays (268 MB, larger than L2) for the HBM view;
+    # ten calls per CUDA graph replay, so that the device time is measured
+    # rather than the host's per-call overhead
+    big_a = torch.rand(1 << 25, device="cuda")
+    big_b = torch.rand(1 << 25, device="cuda")
+    err_out = torch.empty((10, 3), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+
+    def err_graph(pairs):
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                for k, (x, y) in enumerate(pairs):
+                    fab.error_stats(x, y, out=err_out[k])
+        graph.replay()
+        return graph
+
+    g_frame = err_graph([(rgbs[k % copies], rgbs[(k + 1) % copies]) for k in range(10)])
+    ms_err = timed(torch, stream, lambda k: g_frame.replay(), 20) / 10
+    g_big = err_graph([(big_a, big_b)] * 10)
+    ms_err_big = timed(torch, stream, lambda k: g_big.replay(), 5) / 10
+    del g_frame, g_big, big_a, big_b
+    out["error_reduction"] = {
+        "frame_ms": ms_err, "frame_elements": 3 * N_POINTS,
+        "large_ms": ms_err_big, "large_elements": 1 << 25,
+        "large_gbs": 8 * (1 << 25) / (ms_err_big * 1e-3) / 1e9,
+        "large_hbm_frac": 8 * (1 << 25) / (ms_err_big * 1e-3) / 1e9 / peaks()[0]["hbm_gbs"],
+        "note": "sum (a-b)^2, sum b^2 and max |a-b| to FP64 accuracy (terms from error-free FP32 "
+                "transformations, FP64 sums; fixed 608-block grid, fixed-order final sum); 8 bytes read per "
+                "element; fraction of the measured HBM copy rate",
+    }
     out["neural_with_fold_ms_per_frame"] = ms_full
     # end to end: pinned host G-buffer in, RGB back to pinned host memory,
     # through the library's host-buffer call (direct access over the host

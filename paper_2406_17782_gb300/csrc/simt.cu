@@ -711,22 +711,131 @@ __global__ void adam_kernel(float *__restrict__ p0, int64_t n0, float *__restric
 // ---------------------------------------------------------------------------
 // FP64 error statistics: fixed grid of partial sums, then one fixed-order sum.
 // ---------------------------------------------------------------------------
-constexpr int kErrBlocks = 512;
+constexpr int kErrBlocks = 608;   // one wave: 4 CTAs of 256 threads (64 registers) on each of 152 SMs
 constexpr int kErrThreads = 256;
+
+// Per element the kernel needs (w(a-b))^2, (w b)^2 and |w(a-b)| to FP64
+// accuracy.  On this GPU FP64 instructions issue at a small fraction of the
+// FP32 rate, so the main loop holds no FP64 arithmetic at all: the terms are
+// formed with error-free FP32 transformations (Knuth's TwoSum, the FMA
+// TwoProduct) as unevaluated sums hi + lo -- a - b is exact as a pair, its
+// square exact to about 2^-48 relative -- and each thread adds runs of
+// kErrRun terms in renormalised double-float form (error below
+// kErrRun * 2^-47 of a run's sum) before adding the run into its FP64 sums.
+// The maximum is kept as a pair too: |a - b| = |hi| + sign(hi) lo, compared
+// lexicographically, which is exact because FP32 rounding is monotone (with
+// weights, the pair carries the product to about 2^-47 relative).  Elements
+// whose values fall outside [2^-40, 2^60] in magnitude (where a square could
+// overflow or its low part leave the normal range), and non-finite ones,
+// are skipped there and handled in FP64 by a second pass over the thread's
+// share, which runs only in threads that met one.
+constexpr int kErrRun = 32;
+constexpr int kErrBatch = 8;   // loads in flight per thread
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+// s = h + l (|l| <= ulp(h) / 2) += x + y, with x >= 0 and |y| << x
+struct DFloat {
+  float h = 0.0f, l = 0.0f;
+  __device__ __forceinline__ void add(float x, float y) {
+    float t, e;
+    two_sum(h, x, t, e);
+    e = __fadd_rn(e, __fadd_rn(l, y));
+    h = __fadd_rn(t, e);                 // fast two-sum: t >= |e|
+    l = __fsub_rn(e, __fsub_rn(h, t));
+  }
+};
+
+__device__ __forceinline__ bool err_fast(float x) {
+  const float ax = fabsf(x);
+  return ax == 0.0f || (ax >= 0x1p-40f && ax <= 0x1p60f);
+}
+
+// w (a - b) as dh + dl and w b as bh + bl; true when the pairs' range holds
+__device__ __forceinline__ bool err_pairs(float ai, float bi, const float *w, float wv, float &dh, float &dl,
+                                          float &bh, float &bl) {
+  two_sum(ai, -bi, dh, dl);
+  if (w) {
+    float th, te;
+    two_prod(dh, wv, th, te);
+    dl = __fmaf_rn(dl, wv, te);
+    dh = th;
+    two_prod(bi, wv, bh, bl);
+  } else {
+    bh = bi;
+    bl = 0.0f;
+  }
+  return err_fast(dh) && err_fast(bh) && (w == nullptr || err_fast(wv));
+}
 
 __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *__restrict__ a,
                                                                   const float *__restrict__ b, int64_t n,
                                                                   const float *__restrict__ w, int group,
                                                                   int w_stride, double *__restrict__ part) {
   __shared__ double s0[kErrThreads], s1[kErrThreads], s2[kErrThreads];
-  double e2 = 0.0, b2 = 0.0, mx = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kErrThreads + threadIdx.x; i < n; i += (int64_t)kErrBlocks * kErrThreads) {
-    const double wi = w ? (double)w[(i / group) * w_stride] : 1.0;
-    const double d = ((double)a[i] - (double)b[i]) * wi;
-    const double bb = (double)b[i] * wi;
-    e2 += d * d;
-    b2 += bb * bb;
-    mx = fmax(mx, fabs(d));
+  const int64_t stride = (int64_t)kErrBlocks * kErrThreads;
+  const int64_t start = (int64_t)blockIdx.x * kErrThreads + threadIdx.x;
+  double e2 = 0.0, b2 = 0.0;
+  float mh = -1.0f, ml = 0.0f;   // largest |w(a-b)| so far as mh + ml (mh < 0: none)
+  bool slow = false;
+  for (int64_t i0 = start; i0 < n; i0 += kErrRun * stride) {
+    DFloat E, B;
+#pragma unroll 1
+    for (int r0 = 0; r0 < kErrRun; r0 += kErrBatch) {
+      // a batch of loads in flight together; positions past n read as a = b = 0
+      float av[kErrBatch], bv[kErrBatch], wv[kErrBatch];
+#pragma unroll
+      for (int q = 0; q < kErrBatch; ++q) {
+        const int64_t i = i0 + (int64_t)(r0 + q) * stride;
+        const bool in = i < n;
+        av[q] = in ? a[i] : 0.0f;
+        bv[q] = in ? b[i] : 0.0f;
+        wv[q] = w && in ? w[(i / group) * w_stride] : 1.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < kErrBatch; ++q) {
+        float dh, dl, bh, bl;
+        if (!err_pairs(av[q], bv[q], w, wv[q], dh, dl, bh, bl)) {
+          slow = true;
+          continue;
+        }
+        float p, pe, qq, qe;
+        two_prod(dh, dh, p, pe);
+        two_prod(bh, bh, qq, qe);
+        E.add(p, __fmaf_rn(2.0f * dh, dl, pe));   // (dh + dl)^2 without the dl^2 term (below 2^-48)
+        B.add(qq, __fmaf_rn(2.0f * bh, bl, qe));
+        const float sh = fabsf(dh), sl = dh < 0.0f ? -dl : dl;
+        if (sh > mh || (sh == mh && sl > ml)) {
+          mh = sh;
+          ml = sl;
+        }
+      }
+    }
+    e2 += (double)E.h + (double)E.l;
+    b2 += (double)B.h + (double)B.l;
+  }
+  double mx = mh < 0.0f ? 0.0 : (double)mh + (double)ml;
+  if (slow) {
+    for (int64_t i = start; i < n; i += stride) {
+      const float ai = a[i], bi = b[i];
+      const float wv = w ? w[(i / group) * w_stride] : 1.0f;
+      float dh, dl, bh, bl;
+      if (err_pairs(ai, bi, w, wv, dh, dl, bh, bl)) continue;
+      const double wi = (double)wv;
+      const double d = ((double)ai - (double)bi) * wi;
+      const double bb = (double)bi * wi;
+      e2 += d * d;
+      b2 += bb * bb;
+      mx = fmax(mx, fabs(d));
+    }
   }
   s0[threadIdx.x] = e2;
   s1[threadIdx.x] = b2;
@@ -747,17 +856,27 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
   }
 }
 
+// One warp: lane l sums the partials l, l + 32, ... in order, then the 32
+// lane sums are added in lane order.
 __global__ void err_final_kernel(const double *__restrict__ part, double *__restrict__ out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
   double e2 = 0.0, b2 = 0.0, mx = 0.0;
-  for (int k = 0; k < kErrBlocks; ++k) {
+  for (int k = lane; k < kErrBlocks; k += 32) {
     e2 += part[3 * k];
     b2 += part[3 * k + 1];
     mx = fmax(mx, part[3 * k + 2]);
   }
-  out[0] = e2;
-  out[1] = b2;
-  out[2] = mx;
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int k = 0; k < 32; ++k) {
+    t0 += __shfl_sync(0xFFFFFFFFu, e2, k);
+    t1 += __shfl_sync(0xFFFFFFFFu, b2, k);
+    t2 = fmax(t2, __shfl_sync(0xFFFFFFFFu, mx, k));
+  }
+  if (lane == 0) {
+    out[0] = t0;
+    out[1] = t1;
+    out[2] = t2;
+  }
 }
 
 size_t fwd_smem_bytes() { return (((kDecParams + 3) & ~3) + (size_t)(kDecIn + kHidden) * kFwdThreads) * 4; }

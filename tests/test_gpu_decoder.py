@@ -203,6 +203,27 @@ def test_fp16_many_materials_wider_first_layer(fab, setup):
     assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
 
 
+def test_error_stats_mixed_magnitudes(fab):
+    """Elements outside the range where the reduction forms squares from FP32
+    pairs (|x| below 2^-40 or above 2^60) take the FP64 path; sums still
+    within 1e-12 of FP64 and the maximum exact, with both kinds mixed."""
+    rng = np.random.default_rng(13)
+    n = 400_000
+    scale = rng.choice(np.array([1e-16, 1e-13, 1.0, 1e3, 1e19, 1e25]), size=n).astype(np.float64)
+    a = (rng.standard_normal(n) * scale).astype(np.float32)
+    b = (a.astype(np.float64) * (1 + 1e-3 * rng.standard_normal(n))).astype(np.float32)
+    out = fab.error_stats(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    d = a.astype(np.float64) - b.astype(np.float64)
+    np.testing.assert_allclose(out[0], (d * d).sum(), rtol=1e-12)
+    np.testing.assert_allclose(out[1], (b.astype(np.float64) ** 2).sum(), rtol=1e-12)
+    assert out[2] == np.abs(d).max()
+    # the small-magnitude part alone (its sum is not swamped by the large one)
+    small = np.abs(scale) < 1e-12
+    out = fab.error_stats(torch.from_numpy(a[small]).cuda(), torch.from_numpy(b[small]).cuda()).cpu().numpy()
+    np.testing.assert_allclose(out[0], (d[small] ** 2).sum(), rtol=1e-12)
+    assert out[2] == np.abs(d[small]).max()
+
+
 def test_neural_error_stats_fp64_reduction(fab, setup):
     """The FP64 image-wide error reduction against numpy on the same data."""
     rng = np.random.default_rng(9)

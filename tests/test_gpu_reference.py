@@ -53,6 +53,17 @@ def test_frame_subset_16x16(fab, frame_mats):
     assert_close(rgb, wr, "rgb")
 
 
+def test_multiscale_frame_subset_16x16(fab, frame_mats):
+    """Footprints of Table 2's sizes (sides up to five weave repeats), as in
+    the multi-scale frame of the quality measurement."""
+    g = W.subset(W.multiscale_gbuffer(), W.sample_indices(1920 * 1080, 2048, stream="ref-multiscale"))
+    assert g["radius"].max() > 2.0
+    rgb, comps = run_gpu(fab, g, 16, 16, 91)
+    wc, wr = oracle.shade_reference(frame_mats, g, 16, 16, 91)
+    assert_close(comps, wc, "comps")
+    assert_close(rgb, wr, "rgb")
+
+
 @pytest.mark.parametrize("sx,sy", [(1, 1), (2, 1), (2, 2), (4, 4), (3, 5), (8, 8), (64, 32)])
 def test_sample_counts_and_lane_groupings(fab, frame_mats, sx, sy):
     g = W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 257, stream=f"spp{sx}x{sy}"))
