@@ -4,10 +4,13 @@ for profilers (ncu) and quick timing:
   python -m paper_2406_17782_gb300.profile_case reference [--spp 16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case decoder [--precision fp16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case train [--batch 65536] [--train-precision fp32|bf16] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case error [--elements 33554432] [--reps 3]
 
 The workload is the 1920 x 1080 G-buffer of eight weave materials (random-init
 networks); the training case uses a batch of queries over 256 training
-materials with targets from the reference kernel at 4 x 4 samples.  Prints the
+materials with targets from the reference kernel at 4 x 4 samples; the error
+case reduces two arrays of uniform random floats (2^25 elements each by
+default, 268 MB together: more than L2).  Prints the
 mean time per launch (CUDA events) as one JSON line.
 """
 from __future__ import annotations
@@ -30,18 +33,25 @@ from .api import Fabric, GBuffer  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["reference", "decoder", "train"])
+    ap.add_argument("case", choices=["reference", "decoder", "train", "error"])
     ap.add_argument("--spp", type=int, default=16, help="samples per axis (reference)")
     ap.add_argument("--precision", default="fp16")
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--train-precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--elements", type=int, default=1 << 25, help="array length (error)")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
     fab = Fabric(0)
     mats = W.frame_materials()
     fab.set_materials(mats)
     fab.set_params(W.decoder_init(), W.encoder_init())
-    if args.case == "train":
+    if args.case == "error":
+        ea = torch.rand(args.elements, device=fab.device)
+        eb = torch.rand(args.elements, device=fab.device)
+        out = torch.empty(3, dtype=torch.float64, device=fab.device)
+        fn = lambda: fab.error_stats(ea, eb, out=out)
+        points = args.elements
+    elif args.case == "train":
         tm = W.training_materials(32)
         q = W.training_queries(args.batch, len(tm), stream="profile-train")
         g = GBuffer.from_numpy(q)
@@ -51,6 +61,7 @@ def main(argv=None):
         fab.set_train_materials(tm)
         fab.set_train_precision(args.train_precision)
         fn = lambda: fab.train_step(g, target, 1e-3)
+        points = g.n
     else:
         g = GBuffer.from_numpy(W.frame_gbuffer())
         rgb = torch.empty((g.n, 3), dtype=torch.float32, device=fab.device)
@@ -59,6 +70,7 @@ def main(argv=None):
         else:
             fab.prepare_neural(fab.encode_params(mats), args.precision)
             fn = lambda: fab.shade_neural_prepared(g, args.precision, out_rgb=rgb)
+        points = g.n
     fn()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -69,7 +81,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     fab.sync_status()
     print(json.dumps({"case": args.case, "ms_per_launch": e0.elapsed_time(e1) / args.reps, "reps": args.reps,
-                      "points": g.n}))
+                      "points": points}))
 
 
 if __name__ == "__main__":

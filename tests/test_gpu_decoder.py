@@ -137,6 +137,18 @@ def test_tensor_core_decoder_rel_l2(fab, setup, prec):
     assert e_emu <= TOL_EMU
 
 
+def test_fp16_decoder_multiscale_footprints(fab, setup):
+    """Footprints of Table 2's sizes (log-footprint feature beyond the
+    1080p frame's range) through the FP16 tensor-core decoder."""
+    mats, dec, z = setup
+    g = W.subset(W.multiscale_gbuffer(), W.sample_indices(1920 * 1080, 8192, stream="dec-multiscale"))
+    rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp16", comps=True)
+    fab.sync_status()
+    want_c, want_rgb = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, g)
+    assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
+    assert rel_l2(rgb.cpu().numpy(), want_rgb) <= TOL_FP64["fp16"]
+
+
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
 def test_fp16_ragged_tiles(fab, setup, n):
     mats, dec, z = setup
