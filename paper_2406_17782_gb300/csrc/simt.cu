@@ -760,10 +760,10 @@ __device__ __forceinline__ bool err_fast(float x) {
 }
 
 // w (a - b) as dh + dl and w b as bh + bl; true when the pairs' range holds
-__device__ __forceinline__ bool err_pairs(float ai, float bi, const float *w, float wv, float &dh, float &dl,
-                                          float &bh, float &bl) {
+template <bool W>
+__device__ __forceinline__ bool err_pairs(float ai, float bi, float wv, float &dh, float &dl, float &bh, float &bl) {
   two_sum(ai, -bi, dh, dl);
-  if (w) {
+  if (W) {
     float th, te;
     two_prod(dh, wv, th, te);
     dl = __fmaf_rn(dl, wv, te);
@@ -773,20 +773,23 @@ __device__ __forceinline__ bool err_pairs(float ai, float bi, const float *w, fl
     bh = bi;
     bl = 0.0f;
   }
-  return err_fast(dh) && err_fast(bh) && (w == nullptr || err_fast(wv));
+  return err_fast(dh) && err_fast(bh) && (!W || err_fast(wv));
 }
 
+// W: weights present; Idx: index type (32-bit when n and the strides fit).
+template <bool W, typename Idx>
 __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *__restrict__ a,
-                                                                  const float *__restrict__ b, int64_t n,
+                                                                  const float *__restrict__ b, int64_t n_,
                                                                   const float *__restrict__ w, int group,
                                                                   int w_stride, double *__restrict__ part) {
   __shared__ double s0[kErrThreads], s1[kErrThreads], s2[kErrThreads];
-  const int64_t stride = (int64_t)kErrBlocks * kErrThreads;
-  const int64_t start = (int64_t)blockIdx.x * kErrThreads + threadIdx.x;
+  const Idx n = (Idx)n_;
+  const Idx stride = (Idx)kErrBlocks * kErrThreads;
+  const Idx start = (Idx)blockIdx.x * kErrThreads + threadIdx.x;
   double e2 = 0.0, b2 = 0.0;
   float mh = -1.0f, ml = 0.0f;   // largest |w(a-b)| so far as mh + ml (mh < 0: none)
   bool slow = false;
-  for (int64_t i0 = start; i0 < n; i0 += kErrRun * stride) {
+  for (Idx i0 = start; i0 < n; i0 += kErrRun * stride) {
     DFloat E, B;
 #pragma unroll 1
     for (int r0 = 0; r0 < kErrRun; r0 += kErrBatch) {
@@ -794,16 +797,16 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
       float av[kErrBatch], bv[kErrBatch], wv[kErrBatch];
 #pragma unroll
       for (int q = 0; q < kErrBatch; ++q) {
-        const int64_t i = i0 + (int64_t)(r0 + q) * stride;
+        const Idx i = i0 + (Idx)(r0 + q) * stride;
         const bool in = i < n;
         av[q] = in ? a[i] : 0.0f;
         bv[q] = in ? b[i] : 0.0f;
-        wv[q] = w && in ? w[(i / group) * w_stride] : 1.0f;
+        wv[q] = W && in ? w[(int64_t)(i / group) * w_stride] : 1.0f;
       }
 #pragma unroll
       for (int q = 0; q < kErrBatch; ++q) {
         float dh, dl, bh, bl;
-        if (!err_pairs(av[q], bv[q], w, wv[q], dh, dl, bh, bl)) {
+        if (!err_pairs<W>(av[q], bv[q], wv[q], dh, dl, bh, bl)) {
           slow = true;
           continue;
         }
@@ -824,11 +827,11 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
   }
   double mx = mh < 0.0f ? 0.0 : (double)mh + (double)ml;
   if (slow) {
-    for (int64_t i = start; i < n; i += stride) {
+    for (Idx i = start; i < n; i += stride) {
       const float ai = a[i], bi = b[i];
-      const float wv = w ? w[(i / group) * w_stride] : 1.0f;
+      const float wv = W ? w[(int64_t)(i / group) * w_stride] : 1.0f;
       float dh, dl, bh, bl;
-      if (err_pairs(ai, bi, w, wv, dh, dl, bh, bl)) continue;
+      if (err_pairs<W>(ai, bi, wv, dh, dl, bh, bl)) continue;
       const double wi = (double)wv;
       const double d = ((double)ai - (double)bi) * wi;
       const double bb = (double)bi * wi;
@@ -1069,7 +1072,11 @@ size_t error_stats_work_bytes(int64_t) { return (size_t)kErrBlocks * 3 * sizeof(
 cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
                                double *out, void *work, cudaStream_t s) {
   double *part = static_cast<double *>(work);
-  err_partial_kernel<<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  const bool small = n + (int64_t)kErrRun * kErrBlocks * kErrThreads < ((int64_t)1 << 31);
+  if (w && small) err_partial_kernel<true, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  else if (w) err_partial_kernel<true, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  else if (small) err_partial_kernel<false, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  else err_partial_kernel<false, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
   err_final_kernel<<<1, 32, 0, s>>>(part, out);
   return cudaGetLastError();
 }
