@@ -210,13 +210,35 @@ struct TcArgs {
   int n_segs;
 };
 
-// Segment holding global tile `tile` (binary search over the prefix sums).
-__device__ __forceinline__ int find_segment(const TcArgs &a, int64_t tile) {
-  int lo = 0, hi = a.n_segs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(a.seg_tile0 + mid) <= tile) lo = mid; else hi = mid - 1;
+// Segment holding global tile `tile`: the largest s < n_segs with
+// seg_tile0[s] <= tile (seg_tile0[n_segs] = n_tiles > tile).  A pipeline
+// visits its tiles in increasing order, so the search starts from the
+// segment of its previous tile (`cursor`): one load while the tile stays in
+// that segment, otherwise a galloping search then bisection, instead of a
+// full bisection of dependent loads for every tile.
+__device__ __forceinline__ int find_segment(const TcArgs &a, int64_t tile, int cursor, int64_t &first_tile) {
+  int lo = cursor;   // seg_tile0[lo] <= tile
+  int64_t lo_t0 = __ldg(a.seg_tile0 + lo);
+  if (__ldg(a.seg_tile0 + lo + 1) > tile) {
+    first_tile = lo_t0;
+    return lo;
   }
+  int hi = lo + 1, step = 1;   // seg_tile0[hi] <= tile
+  while (true) {
+    lo = hi;
+    step <<= 1;
+    hi = lo + step;
+    if (hi >= a.n_segs) {
+      hi = a.n_segs;
+      break;
+    }
+    if (__ldg(a.seg_tile0 + hi) > tile) break;
+  }
+  while (hi - lo > 1) {   // seg_tile0[lo] <= tile < seg_tile0[hi]
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a.seg_tile0 + mid) <= tile) lo = mid; else hi = mid;
+  }
+  first_tile = __ldg(a.seg_tile0 + lo);
   return lo;
 }
 
@@ -229,16 +251,18 @@ struct TileView {
 };
 
 template <bool MULTI>
-__device__ __forceinline__ TileView tile_view(const TcArgs &a, int64_t tile) {
+__device__ __forceinline__ TileView tile_view(const TcArgs &a, int64_t tile, int &cursor) {
   TileView t;
   if (!MULTI || tile >= a.n_tiles) {
     t.u = a.u; t.v = a.v; t.radius = a.radius; t.wi = a.wi; t.wo = a.wo; t.material = a.material;
     t.rgb = a.rgb; t.comps = a.comps; t.n = MULTI ? 0 : a.n; t.first = tile * 128;
   } else {
-    const int s = find_segment(a, tile);
+    int64_t t0;
+    const int s = find_segment(a, tile, cursor, t0);
+    cursor = s;
     const SegDesc &d = a.segs[s];
     t.u = d.u; t.v = d.v; t.radius = d.radius; t.wi = d.wi; t.wo = d.wo; t.material = d.material;
-    t.rgb = d.rgb; t.comps = d.comps; t.n = d.n; t.first = (tile - __ldg(a.seg_tile0 + s)) * 128;
+    t.rgb = d.rgb; t.comps = d.comps; t.n = d.n; t.first = (tile - t0) * 128;
   }
   return t;
 }
@@ -363,7 +387,8 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
   // first tile's inputs travel while the weights land
   const int64_t stride = (int64_t)gridDim.x * WG;
   int64_t tile = (int64_t)blockIdx.x * WG + wg;
-  TileView view = tile_view<MULTI>(a, tile);
+  int seg_cursor = 0;   // segment of the pipeline's latest tile (batched launches)
+  TileView view = tile_view<MULTI>(a, tile, seg_cursor);
   Point pt = load_point<H>(view, view.first + row, h);
   bool ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
   const float *alb = reinterpret_cast<const float *>(wts + L.alb);
@@ -462,7 +487,7 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
         tc::mma_commit(my_bar);
       }
       if (layer == 0) {   // next tile's inputs, in flight during this tile's layers
-        view = tile_view<MULTI>(a, tile + stride);
+        view = tile_view<MULTI>(a, tile + stride, seg_cursor);
         pt = load_point<H>(view, view.first + row, h);
       }
       // every warp sleeps on the mbarrier until the products land (no
