@@ -206,8 +206,9 @@ struct TcArgs {
   float *rgb, *comps;
   int *status;
   const SegDesc *segs;
-  const int64_t *seg_tile0;
+  const int64_t *seg_tile0;   // read through `seg_t0` below: global, or the CTA's shared copy
   int n_segs;
+  int seg_in_smem;            // 1: each CTA copies seg_tile0 into its spare shared memory
 };
 
 // Segment holding global tile `tile`: the largest s < n_segs with
@@ -216,10 +217,11 @@ struct TcArgs {
 // segment of its previous tile (`cursor`): one load while the tile stays in
 // that segment, otherwise a galloping search then bisection, instead of a
 // full bisection of dependent loads for every tile.
-__device__ __forceinline__ int find_segment(const TcArgs &a, int64_t tile, int cursor, int64_t &first_tile) {
-  int lo = cursor;   // seg_tile0[lo] <= tile
-  int64_t lo_t0 = __ldg(a.seg_tile0 + lo);
-  if (__ldg(a.seg_tile0 + lo + 1) > tile) {
+__device__ __forceinline__ int find_segment(const TcArgs &a, const int64_t *seg_t0, int64_t tile, int cursor,
+                                            int64_t &first_tile) {
+  int lo = cursor;   // seg_t0[lo] <= tile
+  int64_t lo_t0 = seg_t0[lo];
+  if (seg_t0[lo + 1] > tile) {
     first_tile = lo_t0;
     return lo;
   }
@@ -232,13 +234,13 @@ __device__ __forceinline__ int find_segment(const TcArgs &a, int64_t tile, int c
       hi = a.n_segs;
       break;
     }
-    if (__ldg(a.seg_tile0 + hi) > tile) break;
+    if (seg_t0[hi] > tile) break;
   }
-  while (hi - lo > 1) {   // seg_tile0[lo] <= tile < seg_tile0[hi]
+  while (hi - lo > 1) {   // seg_t0[lo] <= tile < seg_t0[hi]
     const int mid = (lo + hi) >> 1;
-    if (__ldg(a.seg_tile0 + mid) <= tile) lo = mid; else hi = mid;
+    if (seg_t0[mid] <= tile) lo = mid; else hi = mid;
   }
-  first_tile = __ldg(a.seg_tile0 + lo);
+  first_tile = seg_t0[lo];
   return lo;
 }
 
@@ -251,14 +253,14 @@ struct TileView {
 };
 
 template <bool MULTI>
-__device__ __forceinline__ TileView tile_view(const TcArgs &a, int64_t tile, int &cursor) {
+__device__ __forceinline__ TileView tile_view(const TcArgs &a, const int64_t *seg_t0, int64_t tile, int &cursor) {
   TileView t;
   if (!MULTI || tile >= a.n_tiles) {
     t.u = a.u; t.v = a.v; t.radius = a.radius; t.wi = a.wi; t.wo = a.wo; t.material = a.material;
     t.rgb = a.rgb; t.comps = a.comps; t.n = MULTI ? 0 : a.n; t.first = tile * 128;
   } else {
     int64_t t0;
-    const int s = find_segment(a, tile, cursor, t0);
+    const int s = find_segment(a, seg_t0, tile, cursor, t0);
     cursor = s;
     const SegDesc &d = a.segs[s];
     t.u = d.u; t.v = d.v; t.radius = d.radius; t.wi = d.wi; t.wo = d.wo; t.material = d.material;
@@ -373,6 +375,14 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, kColsPerTile * WG);
+  // batched launches: the segment table (prefix sums of tile counts) in the
+  // shared memory past the weights, when the launch gave room for it
+  const int64_t *seg_t0 = a.seg_tile0;
+  if (MULTI && a.seg_in_smem) {
+    int64_t *s_t0 = reinterpret_cast<int64_t *>(smem + 1024 + align1k(L.total));
+    for (int i = tid; i <= a.n_segs; i += blockDim.x) s_t0[i] = a.seg_tile0[i];
+    seg_t0 = s_t0;
+  }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -388,7 +398,7 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
   const int64_t stride = (int64_t)gridDim.x * WG;
   int64_t tile = (int64_t)blockIdx.x * WG + wg;
   int seg_cursor = 0;   // segment of the pipeline's latest tile (batched launches)
-  TileView view = tile_view<MULTI>(a, tile, seg_cursor);
+  TileView view = tile_view<MULTI>(a, seg_t0, tile, seg_cursor);
   Point pt = load_point<H>(view, view.first + row, h);
   bool ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
   const float *alb = reinterpret_cast<const float *>(wts + L.alb);
@@ -487,7 +497,7 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
         tc::mma_commit(my_bar);
       }
       if (layer == 0) {   // next tile's inputs, in flight during this tile's layers
-        view = tile_view<MULTI>(a, tile + stride, seg_cursor);
+        view = tile_view<MULTI>(a, seg_t0, tile + stride, seg_cursor);
         pt = load_point<H>(view, view.first + row, h);
       }
       // every warp sleeps on the mbarrier until the products land (no
@@ -888,6 +898,18 @@ static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count,
     const size_t floor_smem = (size_t)smem_sm / (size_t)(per_sm + 1) - 1024 + 1;   // (per_sm + 1) CTAs overflow
     const size_t roomy = (size_t)smem_sm / (size_t)per_sm - 1024;                     // per_sm CTAs still fit
     if (floor_smem > launch_smem && floor_smem <= roomy && floor_smem <= 200 * 1024) launch_smem = floor_smem;
+    // batched: the segment table in the spare shared memory, when it fits
+    // without lowering the CTAs per SM
+    a.seg_in_smem = 0;
+    if (multi) {
+      const size_t table = ((size_t)a.n_segs + 1) * sizeof(int64_t);
+      if (smem + table <= launch_smem) {
+        a.seg_in_smem = 1;
+      } else if (smem + table <= roomy && smem + table <= 200 * 1024) {
+        launch_smem = smem + table;
+        a.seg_in_smem = 1;
+      }
+    }
   }
   void *args[] = {&a};
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kTile * wg * h), args, launch_smem, s);
