@@ -40,6 +40,30 @@ def make_segments(sizes, seed=0):
 SIZES = [50_000, 1, 127, 128, 129, 0, 300, 4097, 65_536, 256, 999]
 
 
+def test_plan_with_many_segments(fab, prepared):
+    """3000 small segments (empty ones among them): the segment table no
+    longer fits the spare shared memory, so the lookup reads it from global
+    memory; the draw still equals per-segment draws bit for bit."""
+    mats, dec, z, lat = prepared
+    rng = np.random.default_rng(5)
+    sizes = [int(x) for x in rng.choice(np.array([0, 1, 37, 128, 129, 300]), size=3000)]
+    frame = W.frame_gbuffer()
+    g_all = GBuffer.from_numpy(W.subset(frame, np.arange(0, sum(sizes))))
+    segs, off = [], 0
+    for n in sizes:
+        g = GBuffer(*(getattr(g_all, k)[off:off + n] for k in ("u", "v", "radius", "wi", "wo", "material")))
+        segs.append((g, torch.full((n, 3), float("nan"), device="cuda")))
+        off += n
+    fab.prepare_neural(lat, "fp16")
+    plan = fab.plan([(g, rgb, None) for g, rgb in segs])
+    plan.shade("fp16")
+    fab.sync_status()
+    want, _ = fab.shade_neural_prepared(g_all, "fp16")
+    fab.sync_status()
+    got = torch.cat([rgb for _, rgb in segs])
+    assert torch.equal(got, want)
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
 def test_plan_equals_per_segment_draws(fab, prepared, prec):
     mats, dec, z, lat = prepared
