@@ -12,6 +12,35 @@
 
 namespace fab {
 
+// Programmatic dependent launch: a kernel launched with launch_dependent()
+// may be scheduled while the kernel before it in the stream is still
+// finishing, which hides the gap between dependent launches.  Every such
+// kernel calls grid_dependency_wait() before it reads anything an earlier
+// kernel wrote (the wait returns once those kernels have completed and
+// their memory is visible; without a pending dependency it returns at
+// once), and grid_dependents_launch() once the next kernel may be
+// scheduled.
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                   Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr int kLatent = 32;
 constexpr int kHidden = 64;
 constexpr int kQueryFeat = 39;          // enc(u) 16 | enc(v) 16 | l | wi 3 | wo 3

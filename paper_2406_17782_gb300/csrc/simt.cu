@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(32 * kSumSegs) reduce_partials_kernel(const fl
                                                                         float *__restrict__ out1,
                                                                         const double *__restrict__ loss_part,
                                                                         double *__restrict__ loss_out) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   __shared__ float seg_sum[kSumSegs][32];
   if (loss_out && blockIdx.x == gridDim.x - 1) {
     if (threadIdx.x < 32) reduce_loss_warp(loss_part, n_part, loss_out);
@@ -365,6 +367,8 @@ template <bool V>
 __global__ void __launch_bounds__(256) latent_segment_kernel(const uint16_t *__restrict__ mat, int64_t n,
                                                              const float *__restrict__ rows,
                                                              float *__restrict__ dlat) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   const int m = blockIdx.x;
   __shared__ float red[256][kLatent + 1];
   float acc[kLatent];
@@ -488,6 +492,8 @@ __global__ void __launch_bounds__(kEncHidden) encoder_fwd_kernel(const float *__
                                                                  float *__restrict__ feats_out, int n,
                                                                  const float *__restrict__ enc,
                                                                  float *__restrict__ z, float *__restrict__ acts) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   __shared__ float f[kEncGroup][kEncIn];
   __shared__ __align__(16) float h1[kEncGroup][kEncHidden];
   __shared__ __align__(16) float h2[kEncGroup][kEncHidden];
@@ -550,6 +556,8 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
                                                                      const float *__restrict__ acts,
                                                                      const float *__restrict__ dz,
                                                                      float *__restrict__ work) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   __shared__ float sdz[kEncGroup][kLatent], da2s[kEncGroup][kEncHidden];
   const int m0 = blockIdx.x * kEncGroup, j = threadIdx.x;
   const int nm = min(kEncGroup, n - m0);
@@ -642,6 +650,8 @@ __global__ void __launch_bounds__(256) encoder_grad_kernel(const float *__restri
                                                            const float *__restrict__ dz,
                                                            const float *__restrict__ work,
                                                            float *__restrict__ denc) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   __shared__ __align__(16) float sl[kGradChunk][32];
   __shared__ float sr[kGradChunk][32];
   // which block, and which 32 x 32 tile of it
@@ -697,6 +707,8 @@ __global__ void __launch_bounds__(256) encoder_grad_kernel(const float *__restri
 __global__ void adam_kernel(float *__restrict__ p0, int64_t n0, float *__restrict__ p1, int64_t n1,
                             const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v, float lr,
                             float bc1, float bc2) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n0 + n1) return;
   float *p = i < n0 ? p0 + i : p1 + (i - n0);
@@ -961,9 +973,9 @@ size_t decoder_backward_work_bytes(int64_t n, int sm_count) {
 namespace {
 void latent_sums(const fabric_gbuffer &g, int n_lat, const float *rows, float *dlat, cudaStream_t s) {
   if ((reinterpret_cast<uintptr_t>(g.material) & 15) == 0)
-    latent_segment_kernel<true><<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+    launch_dependent(latent_segment_kernel<true>, n_lat, 256, 0, s, g.material, g.n, rows, dlat);
   else
-    latent_segment_kernel<false><<<n_lat, 256, 0, s>>>(g.material, g.n, rows, dlat);
+    launch_dependent(latent_segment_kernel<false>, n_lat, 256, 0, s, g.material, g.n, rows, dlat);
 }
 }  // namespace
 
@@ -1000,8 +1012,8 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
   decoder_bwd_kernel<<<grid, kBwdThreads, bwd_smem_bytes(), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  reduce_partials_kernel<<<(kDecParams + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s>>>(
-      partial, grid, kDecParams, kDecParams, kDecParams, ddec, nullptr, loss_part, loss);
+  launch_dependent(reduce_partials_kernel, (kDecParams + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s, partial, grid,
+                   kDecParams, kDecParams, kDecParams, ddec, nullptr, loss_part, loss);
   if (dlat) latent_sums(g, n_lat, rows, dlat, s);
   return cudaGetLastError();
 }
@@ -1013,8 +1025,8 @@ cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const
   // latent-gradient sums after the decoder's columns
   const bool folded = width > kDecParams;
   const int cols = dlat ? width : kDecParams;
-  reduce_partials_kernel<<<(cols + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s>>>(
-      partial, grid, width, cols, kDecParams, ddec, dlat, loss_part, loss);
+  launch_dependent(reduce_partials_kernel, (cols + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s, partial, grid,
+                   width, cols, kDecParams, ddec, dlat, loss_part, loss);
   if (dlat && !folded) latent_sums(g, n_lat, rows, dlat, s);
   return cudaGetLastError();
 }
@@ -1024,9 +1036,9 @@ void encoder_fwd(const float *feats, const fabric_material *raw, float *feats_ou
                  float *acts, cudaStream_t s) {
   const int grid = (n + kEncGroup - 1) / kEncGroup;
   if ((reinterpret_cast<uintptr_t>(enc) & 15) == 0)
-    encoder_fwd_kernel<true><<<grid, kEncHidden, 0, s>>>(feats, raw, feats_out, n, enc, z, acts);
+    launch_dependent(encoder_fwd_kernel<true>, grid, kEncHidden, 0, s, feats, raw, feats_out, n, enc, z, acts);
   else
-    encoder_fwd_kernel<false><<<grid, kEncHidden, 0, s>>>(feats, raw, feats_out, n, enc, z, acts);
+    launch_dependent(encoder_fwd_kernel<false>, grid, kEncHidden, 0, s, feats, raw, feats_out, n, enc, z, acts);
 }
 }  // namespace
 
@@ -1054,8 +1066,8 @@ cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc,
     encoder_fwd(feats, nullptr, nullptr, n, enc, vec, acts, s);
     acts_in = acts;
   }
-  encoder_bwd_vec_kernel<<<(n + kEncGroup - 1) / kEncGroup, kEncHidden, 0, s>>>(enc, n, acts_in, dz, vec);
-  encoder_grad_kernel<<<kGradTiles, 256, 0, s>>>(feats, n, dz, vec, denc);
+  launch_dependent(encoder_bwd_vec_kernel, (n + kEncGroup - 1) / kEncGroup, kEncHidden, 0, s, enc, n, acts_in, dz, vec);
+  launch_dependent(encoder_grad_kernel, kGradTiles, 256, 0, s, feats, n, dz, vec, denc);
   return cudaGetLastError();
 }
 
@@ -1063,7 +1075,7 @@ cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const floa
                         int64_t step, cudaStream_t s) {
   const float bc1 = (float)(1.0 - std::pow(0.9, (double)step));
   const float bc2 = (float)(1.0 - std::pow(0.999, (double)step));
-  adam_kernel<<<(unsigned)((n0 + n1 + 255) / 256), 256, 0, s>>>(p0, n0, p1, n1, grad, m, v, lr, bc1, bc2);
+  launch_dependent(adam_kernel, (unsigned)((n0 + n1 + 255) / 256), 256, 0, s, p0, n0, p1, n1, grad, m, v, lr, bc1, bc2);
   return cudaGetLastError();
 }
 

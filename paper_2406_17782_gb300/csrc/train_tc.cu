@@ -88,6 +88,8 @@ __device__ __forceinline__ void put(uint8_t *base, uint32_t off, float v) {
 }
 
 __global__ void __launch_bounds__(256) train_pack_kernel(const float *__restrict__ dec, uint8_t *__restrict__ blob) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < 64 * 80; e += blockDim.x * gridDim.x) {
     const int o = e / 80, j = e % 80;
     const float w1 = j < kDecIn ? dec[kOffW1 + o * kDecIn + j] : (j == kDecIn ? dec[kOffB1 + o] : 0.0f);
@@ -134,6 +136,8 @@ __device__ __forceinline__ void sync_all() {
 }
 
 __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs a) {
+  grid_dependency_wait();
+  grid_dependents_launch();
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bar_w = reinterpret_cast<uint64_t *>(smem);
@@ -529,7 +533,7 @@ cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  train_pack_kernel<<<8, 256, 0, s>>>(dec, static_cast<uint8_t *>(blob));
+  launch_dependent(train_pack_kernel, 8, 256, 0, s, dec, static_cast<uint8_t *>(blob));
   TrainTcArgs a;
   a.g = g;
   a.latents = latents;
@@ -543,8 +547,7 @@ cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n
   a.loss_partial = loss_partial;
   a.dlat_rows = dlat_rows;
   a.status = status;
-  train_tc_kernel<<<train_tc_grid(g.n, sm_count), kThreads, kDynSmem, s>>>(a);
-  return cudaGetLastError();
+  return launch_dependent(train_tc_kernel, train_tc_grid(g.n, sm_count), kThreads, kDynSmem, s, a);
 }
 
 }  // namespace fab
