@@ -50,8 +50,8 @@ WIDTH, HEIGHT = 1920, 1080
 N_POINTS = WIDTH * HEIGHT
 FLOP_PER_POINT = 2 * (39 * 64 + 64 * 64 + 64 * 64 + 64 * 4)      # 21,888 (layer 1 with the latent folded)
 BYTES_PER_POINT = 38 + 12                                          # G-buffer record in, RGB out
-# DRAM bytes (read + write) of one FP16 decoder launch on this frame, from the
-# ncu capture summarised in profiles/decoder_tc_1080p_fp16.md (same kernel)
+# DRAM bytes (read + write) of one FP16 decoder launch on this frame, from an
+# ncu capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_FP16 = 78_858_752 + 5_348_864
 WORKLOAD = "1920x1080 G-buffer, 8 weave materials (one per 240-px band), random-init decoder"
 
