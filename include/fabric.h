@@ -434,6 +434,14 @@ fabric_status fabric_selftest_mma(fabric_ctx *ctx, const float *a_dev, const flo
 fabric_status fabric_selftest_mma_e4m3(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
                                        float *d_dev, void *stream);
 
+/* The bounded-wait path of the kernels, exercised on purpose: one CTA waits
+ * on an mbarrier that nothing ever completes (spinning when sleep = 0, with
+ * try_wait and a suspend hint otherwise), gives up after about a
+ * millisecond, records a timeout in the status word and returns; the next
+ * fabric_sync_status returns FABRIC_ERR_TIMEOUT and clears it, and the
+ * context stays usable.  Nothing faults or hangs.  Used by the tests. */
+fabric_status fabric_selftest_wait_timeout(fabric_ctx *ctx, int sleep, void *stream);
+
 /* The same BF16 product with both operands in shared memory in the MN-major
  * (transposed) layout the tensor-core training kernel uses for its weight
  * gradients: element (i, q) of a (and of b) stored with the 8 consecutive i

@@ -105,6 +105,7 @@ def load(path: str | None = None):
         "fabric_selftest_mma": (st, [vp, vp, vp, i32, i32, i32, vp, vp]),
         "fabric_selftest_mma_e4m3": (st, [vp, vp, vp, i32, i32, vp, vp]),
         "fabric_selftest_mma_mn": (st, [vp, vp, vp, i32, i32, vp, vp]),
+        "fabric_selftest_wait_timeout": (st, [vp, i32, vp]),
         "fabric_shade_neural_noalloc": (st, [vp, P(FabricGBuffer), vp, st, vp, vp, vp]),
         "fabric_plan_create": (st, [vp, vp, i32, P(vp)]),
         "fabric_plan_shade": (st, [vp, vp, st, vp]),

@@ -276,6 +276,11 @@ class Fabric:
                                                       _ptr(d), _stream_handle(None)))
         return d
 
+    def selftest_wait_timeout(self, sleep: bool = False):
+        """Launch the bounded-wait self-test (a wait that can never complete
+        gives up after about 1 ms); the next sync_status raises TIMEOUT."""
+        self._check(self.lib.fabric_selftest_wait_timeout(self.h, int(sleep), _stream_handle(None)))
+
     def selftest_mma_mn(self, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
         """128 x n x k BF16 product with both operands MN-major in shared memory."""
         n, k = b.shape

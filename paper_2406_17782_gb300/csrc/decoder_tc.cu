@@ -957,6 +957,27 @@ cudaError_t launch_decoder_tc_segments(const SegDesc *segs, const int64_t *seg_t
   return launch_tc(a, true, precision, sm_count, ctas_per_sm, warpgroups, tile_wgs, s);
 }
 
+// ---- self-test of the bounded waits: an mbarrier that nothing arrives on.
+// Every thread waits on it with the same helpers the kernels use (spinning,
+// or try_wait with a suspend hint); each wait gives up after `max_cycles`,
+// the block records a timeout in the status word and returns normally.
+__global__ void __launch_bounds__(64, 1) selftest_wait_kernel(int sleep, long long max_cycles, int *status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);   // one arrival expected; none ever comes
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = sleep ? tc::mbar_wait_sleep(&bar, 0, max_cycles) : tc::mbar_wait(&bar, 0, max_cycles);
+  const bool expired = __syncthreads_or(!ok);
+  if (expired && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+}
+
+cudaError_t launch_selftest_wait(int sleep, int *status, cudaStream_t s) {
+  selftest_wait_kernel<<<1, 64, 0, s>>>(sleep, 2000000ll /* about 1 ms */, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, int a_in_tmem, float *d, int *status,
                                 cudaStream_t s) {
   if (a_in_tmem == 2)

@@ -618,6 +618,13 @@ fabric_status fabric_selftest_mma_e4m3(fabric_ctx *ctx, const float *a_dev, cons
   return FABRIC_OK;
 }
 
+fabric_status fabric_selftest_wait_timeout(fabric_ctx *ctx, int sleep, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  FAB_CUDA(ctx, launch_selftest_wait(sleep ? 1 : 0, ctx->d_status, static_cast<cudaStream_t>(stream)),
+           "selftest launch");
+  return FABRIC_OK;
+}
+
 fabric_status fabric_selftest_mma_mn(fabric_ctx *ctx, const float *a_dev, const float *b_dev, int n, int k,
                                      float *d_dev, void *stream) {
   FAB_CHECK_CTX(ctx);

@@ -230,6 +230,7 @@ cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const
 size_t train_tc_blob_bytes();
 int train_tc_grid(int64_t n, int sm_count);
 int train_tc_partial_width(int n_lat);
+cudaError_t launch_selftest_wait(int sleep, int *status, cudaStream_t s);
 cudaError_t launch_selftest_mn(const float *a, const float *b, int n, int k, float *d, int *status, cudaStream_t s);
 cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                             const float *target, int loss_mode, void *blob, float *partial, double *loss_partial,

@@ -11,6 +11,7 @@ import torch
 import oracle
 import workloads as W
 from oracle import mlp as M
+from paper_2406_17782_gb300 import FabricError
 from paper_2406_17782_gb300.api import GBuffer
 
 pytestmark = pytest.mark.gpu
@@ -88,3 +89,23 @@ def test_decoder_on_degenerate_inputs(fab, prec):
     assert np.isfinite(got).all()
     rel = np.sqrt(((got - want_c) ** 2).sum() / (want_c ** 2).sum())
     assert rel <= (2e-5 if prec == "fp32" else 5e-3), rel
+
+
+@pytest.mark.parametrize("sleep", [False, True])
+def test_expired_wait_is_reported_and_context_survives(fab, sleep):
+    """A kernel wait that nothing completes gives up after its cycle limit,
+    records a timeout in the status word and returns: the next status check
+    raises FABRIC_ERR_TIMEOUT, clears the word, and the context keeps
+    working (a reference draw afterwards is clean)."""
+    fab.sync_status()
+    fab.selftest_wait_timeout(sleep)
+    with pytest.raises(FabricError) as info:
+        fab.sync_status()
+    assert info.value.status == 4   # FABRIC_ERR_TIMEOUT
+    fab.sync_status()               # cleared
+    mats = W.frame_materials()
+    fab.set_materials(mats)
+    g = W.subset(W.frame_gbuffer(), np.arange(0, 64))
+    rgb, _ = fab.shade_reference(GBuffer.from_numpy(g), 2, 2, 1)
+    fab.sync_status()
+    assert torch.isfinite(rgb).all()
