@@ -5,12 +5,14 @@ for profilers (ncu) and quick timing:
   python -m paper_2406_17782_gb300.profile_case decoder [--precision fp16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case train [--batch 65536] [--train-precision fp32|bf16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case error [--elements 33554432] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case batched [--precision fp16] [--reps 3]
 
 The workload is the 1920 x 1080 G-buffer of eight weave materials (random-init
 networks); the training case uses a batch of queries over 256 training
 materials with targets from the reference kernel at 4 x 4 samples; the error
 case reduces two arrays of uniform random floats (2^25 elements each by
-default, 268 MB together: more than L2).  Prints the
+default, 268 MB together: more than L2); the batched case shades the 4K
+view plus 256 ragged segments through one plan (one launch per call).  Prints the
 mean time per launch (CUDA events) as one JSON line.
 """
 from __future__ import annotations
@@ -33,7 +35,7 @@ from .api import Fabric, GBuffer  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["reference", "decoder", "train", "error"])
+    ap.add_argument("case", choices=["reference", "decoder", "train", "error", "batched"])
     ap.add_argument("--spp", type=int, default=16, help="samples per axis (reference)")
     ap.add_argument("--precision", default="fp16")
     ap.add_argument("--batch", type=int, default=65536)
@@ -45,7 +47,17 @@ def main(argv=None):
     mats = W.frame_materials()
     fab.set_materials(mats)
     fab.set_params(W.decoder_init(), W.encoder_init())
-    if args.case == "error":
+    if args.case == "batched":
+        segs_host, n_b = W.batched_4k()
+        keep = []
+        for h in segs_host:
+            g = GBuffer.from_numpy(h)
+            keep.append((g, torch.empty((g.n, 3), dtype=torch.float32, device=fab.device), None))
+        fab.prepare_neural(fab.encode_params(mats), args.precision)
+        plan = fab.plan(keep)
+        fn = lambda: plan.shade(args.precision)
+        points = n_b
+    elif args.case == "error":
         ea = torch.rand(args.elements, device=fab.device)
         eb = torch.rand(args.elements, device=fab.device)
         out = torch.empty(3, dtype=torch.float64, device=fab.device)
