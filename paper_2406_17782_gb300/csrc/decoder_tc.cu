@@ -863,7 +863,7 @@ int tc_default_ctas_per_sm(int n_mat, int precision) {
   const int wg = 1;
   const int pr = prec_code(precision);
   const void *fn = pick_kernel(pr, wg, 1, false);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  ensure_max_dyn_smem(fn, 200 * 1024);
   return tc_resident_ctas(fn, tc_smem_bytes(n_mat, k1, pr == kPrE4M3), wg, 1);
 }
 
@@ -874,11 +874,9 @@ static cudaError_t launch_tc(TcArgs &a, bool multi, int precision, int sm_count,
   const int h = norm_h(tile_wgs, wg);
   const size_t smem = tc_smem_bytes(a.n_mat, a.k1, pr == kPrE4M3);
   const void *fn = pick_kernel(pr, wg, h, multi);
-  static bool attr_set[3][5][3][2] = {};
-  if (!attr_set[pr][wg][h][multi]) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  {
+    const cudaError_t e = ensure_max_dyn_smem(fn, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set[pr][wg][h][multi] = true;
   }
   const int resident = tc_resident_ctas(fn, smem, wg, h);
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : resident;

@@ -186,17 +186,20 @@ bool check_gbuffer(fabric_ctx *ctx, const fabric_gbuffer *g) {
 }
 
 // CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bytewise.
-static uint32_t crc32_update(uint32_t crc, const void *data, size_t n) {
-  static uint32_t table[256];
-  static bool init = false;
-  if (!init) {
+struct Crc32Table {
+  uint32_t v[256];
+  Crc32Table() {
     for (uint32_t i = 0; i < 256; ++i) {
       uint32_t c = i;
       for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
-      table[i] = c;
+      v[i] = c;
     }
-    init = true;
   }
+};
+
+static uint32_t crc32_update(uint32_t crc, const void *data, size_t n) {
+  static const Crc32Table tab;   // initialised once, thread-safe
+  const uint32_t *table = tab.v;
   const uint8_t *p = static_cast<const uint8_t *>(data);
   crc = ~crc;
   for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);

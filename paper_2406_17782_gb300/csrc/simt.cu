@@ -904,12 +904,10 @@ size_t bwd_smem_bytes() {
 cudaError_t launch_decoder_fp32(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, const float *latents,
                                 const float *dec, float *rgb, float *comps, float *y_raw, int *status,
                                 cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(decoder_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes());
+  {
+    const cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void *>(decoder_fp32_kernel),
+                                              (int)fwd_smem_bytes());
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   FwdArgs a;
   a.g = g;
@@ -929,12 +927,10 @@ cudaError_t launch_decoder_fp32(const fabric_gbuffer &g, const DevMaterial *mats
 
 cudaError_t launch_decoder_raw(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                                float *y_raw, int *status, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(decoder_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes());
+  {
+    const cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void *>(decoder_fp32_kernel),
+                                              (int)fwd_smem_bytes());
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   FwdArgs a;
   a.g = g;
@@ -982,12 +978,10 @@ void latent_sums(const fabric_gbuffer &g, int n_lat, const float *rows, float *d
 cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                                     const float *dy, const float *target, int loss_mode, float *ddec, float *dlat,
                                     double *loss, void *work, int sm_count, int *status, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(decoder_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bwd_smem_bytes());
+  {
+    const cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void *>(decoder_bwd_kernel),
+                                              (int)bwd_smem_bytes());
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int grid = bwd_grid(g.n, sm_count);
   uint8_t *w = static_cast<uint8_t *>(work);

@@ -527,11 +527,9 @@ int train_tc_grid(int64_t n, int sm_count) {
 cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                             const float *target, int loss_mode, void *blob, float *partial, double *loss_partial,
                             float *dlat_rows, int sm_count, int *status, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+  {
+    const cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void *>(train_tc_kernel), (int)kDynSmem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   launch_dependent(train_pack_kernel, 8, 256, 0, s, dec, static_cast<uint8_t *>(blob));
   TrainTcArgs a;
