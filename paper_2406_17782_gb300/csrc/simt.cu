@@ -827,10 +827,13 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
         two_prod(bh, bh, qq, qe);
         E.add(p, __fmaf_rn(2.0f * dh, dl, pe));   // (dh + dl)^2 without the dl^2 term (below 2^-48)
         B.add(qq, __fmaf_rn(2.0f * bh, bl, qe));
-        const float sh = fabsf(dh), sl = dh < 0.0f ? -dl : dl;
-        if (sh > mh || (sh == mh && sl > ml)) {
-          mh = sh;
-          ml = sl;
+        const float sh = fabsf(dh);
+        if (sh >= mh) {   // rare once the running maximum has grown: one compare per element
+          const float sl = dh < 0.0f ? -dl : dl;
+          if (sh > mh || sl > ml) {
+            mh = sh;
+            ml = sl;
+          }
         }
       }
     }
