@@ -87,8 +87,13 @@ __device__ __forceinline__ void put(uint8_t *base, uint32_t off, float v) {
   *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(v);
 }
 
+// Launched right after the encoder forward, on which it does not depend: it
+// reads the parameters the previous step's Adam wrote, which completed before
+// the encoder forward got past its own dependency wait -- the point from
+// which this kernel may start.  So it packs at once, overlapping the encoder,
+// and waits for the encoder only at its end, so that its completion still
+// implies the encoder's for the kernel after it.
 __global__ void __launch_bounds__(256) train_pack_kernel(const float *__restrict__ dec, uint8_t *__restrict__ blob) {
-  grid_dependency_wait();
   grid_dependents_launch();
   for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < 64 * 80; e += blockDim.x * gridDim.x) {
     const int o = e / 80, j = e % 80;
@@ -111,6 +116,7 @@ __global__ void __launch_bounds__(256) train_pack_kernel(const float *__restrict
     if (j < 32) put(blob, kW1t + tc::core_offset(j, o, 64), dec[kOffW1 + o * kDecIn + j]);
     if (o < 16) put(blob, kW4t + tc::core_offset(j, o, 16), o < kOut ? dec[kOffW4 + o * kHidden + j] : 0.0f);
   }
+  grid_dependency_wait();
 }
 
 struct TrainTcArgs {
