@@ -279,3 +279,23 @@ def test_e4m3_emulation_reduces_to_the_network_without_rounding(M):
     q, _ = M.shade_neural_e4m3(P, z, mats, g)
     rel = np.sqrt(((q - want) ** 2).sum() / (want ** 2).sum())
     assert 1e-2 < rel < 0.3
+
+
+def test_recombine_eq8_hand_values(M):
+    """Eq. 8 on hand-set components and albedos, the colours worked out by
+    hand: material 0 has every albedo different (a warp / weft or diffuse /
+    specular swap changes the result), material 1 only a specular weft
+    albedo."""
+    mats = np.zeros(2, W.MATERIAL_DTYPE)
+    mats[0]["kd"] = [[0.125, 0.25, 0.375], [0.5, 0.0, 0.0]]
+    mats[0]["ks"] = [[0.0, 0.25, 0.0], [0.0, 0.0, 1.0]]
+    mats[1]["ks"] = [[0.0, 0.0, 0.0], [2.0, 4.0, 8.0]]
+    comps = np.array([[1.0, 2.0, 3.0, 4.0],       # C_warp, C_weft, S_warp, S_weft
+                      [0.5, 0.0, 0.0, 0.25],
+                      [1.0, 2.0, 3.0, 4.0]])
+    rgb = M.recombine(comps, mats, np.array([0, 1, 1]))
+    # R = 0.125*1 + 0.5*2 + 0*3 + 0*4; G = 0.25*1 + 0*2 + 0.25*3 + 0*4; B = 0.375*1 + 0 + 0 + 1*4
+    want = np.array([[1.125, 1.0, 4.375],
+                     [0.5, 1.0, 2.0],
+                     [8.0, 16.0, 32.0]])
+    np.testing.assert_array_equal(rgb, want)

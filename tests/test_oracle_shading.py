@@ -497,3 +497,56 @@ def test_paper_direction_pair_counts():
     assert abs(per_mat - g["queries_per_material_about"]["value"]) / g["queries_per_material_about"]["value"] < 0.05
     m = g["materials"]
     assert m["plain"] == 9 * 9 and m["twill"] == 3 * 4 * 16 and m["satin"] == 3 * 4 * 16
+
+
+# ------------------------------------------------------- Eq. 8 recombination
+def test_eq8_rgb_from_hand_set_albedos(oracle_mod):
+    """Eq. 8 in the estimator's RGB output, on values worked out by hand.
+
+    Flat isotropic yarns (alpha = 1, beta = 0, inclination 0) at a single
+    point (r = 2^-30 periods), wi = (0.8, 0, 0.6), wo = (0, 0, 1), w = 0.5:
+    Eq. 1-2 give C = 0.6 / pi for the visible yarn and
+    S = 0.6 (1 - exp(-16/3)) / (6.4 pi) (D = 1/pi, sigma = 1,
+    G = ci co (1 - exp(-2 (ci + co) / (ci co))) / (ci + co), divided by
+    4 co); the hidden yarn's components are 0.  Every albedo differs, so a
+    warp / weft or diffuse / specular swap in the recombination changes the
+    expected colour.  Plain weave: cell (0, 0) shows the warp at its centre
+    (u, v) = (0.25, 0.25), cell (0, 1) shows the weft at (0.75, 0.25)."""
+    C = 0.6 / math.pi
+    S = 0.6 * (1.0 - math.exp(-16.0 / 3.0)) / (6.4 * math.pi)
+    mat = W.make_material(pattern=0, twist_deg=0.0, incl_deg=0.0, alpha=[1.0, 1.0], beta=[0.0, 0.0],
+                          kd=[[0.2, 0.4, 0.6], [0.9, 0.1, 0.3]],
+                          ks=[[1.0, 0.0, 0.5], [0.05, 0.7, 0.25]], gap=0.2, w_blend=0.5)
+    g = dict(u=np.array([16.25, 16.75], np.float32), v=np.array([3.25, 3.25], np.float32),
+             radius=np.full(2, 2.0 ** -30, np.float32),
+             wi=np.array([[0.8, 0.0, 0.6]] * 2, np.float32), wo=np.array([[0.0, 0.0, 1.0]] * 2, np.float32),
+             material=np.zeros(2, np.uint16))
+    comps, rgb = oracle_mod.shade_reference(np.atleast_1d(mat), g, 4, 4, 5)
+    f32 = lambda x: float(np.float32(x))   # albedos are stored as float32
+    np.testing.assert_allclose(comps[0], [C, 0.0, S, 0.0], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(comps[1], [0.0, C, 0.0, S], rtol=1e-6, atol=1e-12)
+    # warp point: kd_warp C + ks_warp S
+    want_warp = [f32(0.2) * C + f32(1.0) * S, f32(0.4) * C + 0.0 * S, f32(0.6) * C + f32(0.5) * S]
+    # weft point: kd_weft C + ks_weft S
+    want_weft = [f32(0.9) * C + f32(0.05) * S, f32(0.1) * C + f32(0.7) * S, f32(0.3) * C + f32(0.25) * S]
+    np.testing.assert_allclose(rgb[0], want_warp, rtol=1e-6)
+    np.testing.assert_allclose(rgb[1], want_weft, rtol=1e-6)
+
+
+def test_eq8_rgb_is_linear_in_each_albedo(oracle_mod):
+    """Eq. 8 is linear in each albedo with the matching component as its
+    coefficient: with one albedo set to the unit colour and the other three
+    to zero, the RGB output is that component in all three channels."""
+    rng = np.random.default_rng(21)
+    g = _rand_gbuf(rng, 64, 1, uv_max=10.0)
+    names = [("kd", 0), ("kd", 1), ("ks", 0), ("ks", 1)]   # C_warp, C_weft, S_warp, S_weft
+    for k, (field, yarn) in enumerate(names):
+        kd = np.zeros((2, 3))
+        ks = np.zeros((2, 3))
+        (kd if field == "kd" else ks)[yarn] = 1.0
+        mat = W.make_material(pattern=2, twist_deg=12.0, incl_deg=25.0, alpha=[0.3, 0.5], beta=[1.0, 0.6],
+                              kd=kd, ks=ks)
+        comps, rgb = oracle_mod.shade_reference(np.atleast_1d(mat), g, 4, 4, 9)
+        assert (comps[:, k] > 0).any()
+        for ch in range(3):
+            np.testing.assert_array_equal(rgb[:, ch], comps[:, k])
