@@ -403,21 +403,45 @@ def measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream):
     return out
 
 
+def _ladder_entry(sp, errs, ms):
+    return {"spp": sp * sp, "rmse_fp": errs["rmse_fp"], "rel_l2_fp": errs["rel_l2_fp"], "rmse_tm": errs["rmse_tm"],
+            "rmse_lit": errs["rmse"], "ms": ms}
+
+
+def _target(neural, ladder, metric):
+    """The headline target on one metric: the neural frame at RMSE <= 0.01,
+    at >= 10x the speed of the cheapest reference variant reaching 0.01."""
+    ref = next((r for r in ladder if r[metric] <= 0.01), None)
+    speed = (ref["ms"] / neural["ms"]) if ref else None
+    eq = next((r for r in ladder if r[metric] <= neural[metric]), None)
+    return {"metric": metric, "neural_rmse": neural[metric], "neural_ms": neural["ms"],
+            "neural_meets_0.01": neural[metric] <= 0.01,
+            "cheapest_reference_at_0.01": ref, "speedup_vs_that_reference": speed,
+            "target_met": bool(neural[metric] <= 0.01 and speed is not None and speed >= 10.0),
+            "reference_at_neural_rmse": eq,
+            "speedup_at_equal_rmse": (eq["ms"] / neural["ms"]) if eq else None}
+
+
 def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     """Train the decoder and encoder with the library's kernels on data from
     the reference kernel (once with the paper's Eq. 11 loss, once with the
-    rendered-space loss option), then measure the 1080p frame's RMSE
-    (rendered under a unit directional light) of the neural path and of the
-    reference at 1-64 spp against the reference at 1024 spp, and time each
-    of them: the speed ratio at equal quality, and where the reference
-    reaches 0.01."""
+    rendered-space loss option), then measure the error of the neural 1080p
+    frame and of the reference at 1-256 spp against the reference at 1024
+    spp, and time each of them: where the reference reaches RMSE 0.01, and
+    whether the neural frame meets the target (RMSE <= 0.01 at >= 10x the
+    speed of that reference).  The primary metric is the RMSE of the linear
+    f_P over all pixels and RGB channels, unclamped; the tone-mapped
+    x / (1 + x) variant and the frame lit by a unit directional light are
+    reported beside it.  The same on the multi-scale frame (Table 2
+    footprints), against the reference at 4096 spp."""
     from paper_2406_17782_gb300 import train as T
     tm = W.training_materials(32)
     t0 = time.time()
     g_tr, target = T.generate_dataset(fab, tm, args.quality_queries, (64, 32), frame_share=0.5)
     torch.cuda.synchronize()
     t_data = time.time() - t0
-    spps = (1, 2, 4, 8)
+    spps = (1, 2, 4, 8, 16)
+    ms_spps = (1, 2, 4, 8, 16)
     copies = len(gbufs)
     runs = {}
     ladder = None
@@ -447,54 +471,65 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
             for sp in spps:
                 fab.shade_reference(gbufs[0], sp, sp, 5, out_rgb=rgbs[0])
                 ms_r = timed(torch, stream, lambda k: fab.shade_reference(gbufs[k % copies], sp, sp, 5,
-                                                                          out_rgb=rgbs[k % copies]), 20)
-                ladder.append({"spp": sp * sp, "rmse": rm[f"reference_{sp * sp}spp"]["rmse"], "ms": ms_r})
-            gt_rms = rm["gt_rms"]
+                                                                          out_rgb=rgbs[k % copies]), 10)
+                ladder.append(_ladder_entry(sp, rm[f"reference_{sp * sp}spp"], ms_r))
+            gt_info = {k: rm[k] for k in ("gt_rms", "gt_rms_fp", "gt_noise", "gt_noise_fp")}
         # the multi-scale frame: footprints of Table 2's sizes, ground truth at 4096 spp
-        rm_ms = T.frame_rmse(fab, "fp16", gt_spp=(64, 64), ref_spps=(1, 2, 4, 8, 16) if ms_ladder is None else (),
+        rm_ms = T.frame_rmse(fab, "fp16", gt_spp=(64, 64), ref_spps=ms_spps if ms_ladder is None else (),
                              gbuf=ms_host)
         if ms_ladder is None:
             ms_ladder = []
-            for sp in (1, 2, 4, 8, 16):
+            for sp in ms_spps:
                 fab.shade_reference(ms_dev, sp, sp, 5, out_rgb=rgbs[0])
                 ms_r = timed(torch, stream, lambda k: fab.shade_reference(ms_dev, sp, sp, 5, out_rgb=rgbs[0]), 10)
-                ms_ladder.append({"spp": sp * sp, "rmse": rm_ms[f"reference_{sp * sp}spp"]["rmse"], "ms": ms_r})
-            ms_gt_rms = rm_ms["gt_rms"]
+                ms_ladder.append(_ladder_entry(sp, rm_ms[f"reference_{sp * sp}spp"], ms_r))
+            ms_gt_info = {k: rm_ms[k] for k in ("gt_rms", "gt_rms_fp", "gt_noise", "gt_noise_fp")}
         fab.sync_status()
-        neural = {"rmse": rm["neural"]["rmse"], "rel_l2": rm["neural"]["rel_l2"], "ms": ms["fp16"]}
-        eq = next((r for r in ladder if r["rmse"] <= neural["rmse"]), None)
-        neural_ms = {"rmse": rm_ms["neural"]["rmse"], "rel_l2": rm_ms["neural"]["rel_l2"], "ms": ms["fp16"]}
-        eq_ms = next((r for r in ms_ladder if r["rmse"] <= neural_ms["rmse"]), None)
+        neural = {k: rm["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
+        neural.update(rmse_lit=rm["neural"]["rmse"], ms=ms["fp16"])
+        neural8 = {k: rm8["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
+        neural8.update(rmse_lit=rm8["neural"]["rmse"], ms=ms["fp8"])
+        neural_ms = {k: rm_ms["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
+        neural_ms.update(rmse_lit=rm_ms["neural"]["rmse"], ms=ms["fp16"])
         runs[loss] = {
             "neural_fp16": neural,
-            "neural_fp8": {"rmse": rm8["neural"]["rmse"], "rel_l2": rm8["neural"]["rel_l2"], "ms": ms["fp8"]},
-            "neural_meets_0.01": neural["rmse"] <= 0.01,
-            "reference_at_neural_rmse": eq,
-            "speedup_at_equal_rmse": (eq["ms"] / neural["ms"]) if eq else None,
+            "neural_fp8": neural8,
+            "target_fp": _target(neural, ladder, "rmse_fp"),
+            "target_tone_mapped": _target(neural, ladder, "rmse_tm"),
+            "target_lit": _target(neural, ladder, "rmse_lit"),
             "multiscale": {
                 "neural_fp16": neural_ms,
-                "neural_meets_0.01": neural_ms["rmse"] <= 0.01,
-                "reference_at_neural_rmse": eq_ms,
-                "speedup_at_equal_rmse": (eq_ms["ms"] / neural_ms["ms"]) if eq_ms else None,
+                "target_fp": _target(neural_ms, ms_ladder, "rmse_fp"),
+                "target_lit": _target(neural_ms, ms_ladder, "rmse_lit"),
             },
             "train_seconds": t_train,
         }
     del g_tr, target
     interp = measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream)
+    best = min(runs, key=lambda k: runs[k]["neural_fp16"]["rmse_fp"])
     return {
+        "target_met": runs[best]["target_fp"]["target_met"],
+        "target": dict(runs[best]["target_fp"], frame="1080p G-buffer of the workload (8 weaves)", loss=best,
+                       definition="RMSE of linear f_P over all pixels and RGB channels, unclamped, against the "
+                                  "reference at 1024 spp; target RMSE <= 0.01 at >= 10x the speed of the cheapest "
+                                  "reference variant (1-256 spp) with RMSE <= 0.01"),
         "interpolation": interp,
-        "metric": "RMSE of the 1080p frame, f_P <wi.n> per RGB channel (unit directional light), "
-                  "against the reference at 1024 spp",
-        "gt_rms": gt_rms,
+        "metric": "rmse_fp: RMSE of linear f_P over all pixels and RGB channels, unclamped, against the reference "
+                  "at 1024 spp (32 x 32, seed independent of the ladder); rmse_tm: the same after x / (1 + x); "
+                  "rmse_lit: f_P <wi.n_s> per channel (unit directional light)",
+        "ground_truth": dict(gt_info, spp=1024,
+                             note="gt_noise*: RMS Monte Carlo deviation of the ground truth from the integral, "
+                                  "from a second ground-truth frame with an independent seed; the reference "
+                                  "kernel equals the FP64 oracle on the same sample sequence to 1e-4 per "
+                                  "component (GPU tests, including a 65,536-pixel subset of this frame at "
+                                  "1024 spp)"),
         "reference": ladder,
-        "reference_at_0.01": next((r for r in ladder if r["rmse"] <= 0.01), None),
         "multiscale": {
             "frame": "the 1080p frame with footprint sides drawn as in Table 2 (half U(0,1), half U(1,5) "
                      "periods); ground truth: the reference at 4096 spp; neural ms from the 1080p frame "
                      "(the decoder's cost does not depend on the footprint)",
-            "gt_rms": ms_gt_rms,
+            "ground_truth": dict(ms_gt_info, spp=4096),
             "reference": ms_ladder,
-            "reference_at_0.01": next((r for r in ms_ladder if r["rmse"] <= 0.01), None),
         },
         "loss_eq11": runs["eq11"],
         "loss_rendered": runs["rendered"],
@@ -576,10 +611,60 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     fab.shade_neural_host(host, args.precision, out_rgb=rgb_host, chunk_points=262144)
     ms_staged = timed(torch, stream, lambda k: fab.shade_neural_host(host, args.precision, out_rgb=rgb_host,
                                                                      chunk_points=262144), reps)
+    # the host link's own rate: one 1 GiB copy of page-locked memory each way
+    # (cudaMemcpyAsync through torch), CUDA events
+    link_h = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    link_d = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    link_d.copy_(link_h, non_blocking=True)
+    link_h.copy_(link_d, non_blocking=True)
+    ms_h2d = timed(torch, stream, lambda k: link_d.copy_(link_h, non_blocking=True), 5)
+    ms_d2h = timed(torch, stream, lambda k: link_h.copy_(link_d, non_blocking=True), 5)
+    del link_h, link_d
+    h2d_gbs, d2h_gbs = (1 << 30) / (ms_h2d * 1e-3) / 1e9, (1 << 30) / (ms_d2h * 1e-3) / 1e9
+    b_in, b_out = host.nbytes(), rgb_host.numel() * 4
+    floor_duplex = max(b_in / (h2d_gbs * 1e9), b_out / (d2h_gbs * 1e9)) * 1e3
+    floor_serial = (b_in / (h2d_gbs * 1e9) + b_out / (d2h_gbs * 1e9)) * 1e3
     out["e2e"] = {"value": N_POINTS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
-                  "h2d_bytes_per_step": host.nbytes(), "d2h_bytes_per_step": rgb_host.numel() * 4,
+                  "h2d_bytes_per_step": b_in, "d2h_bytes_per_step": b_out,
                   "call": "fabric_shade_neural_host (page-locked buffers: the decoder reads and writes host memory)",
-                  "staged_3_streams_ms": ms_staged, "serial_copy_launch_copy_ms": ms_serial}
+                  "staged_3_streams_ms": ms_staged, "serial_copy_launch_copy_ms": ms_serial,
+                  "host_link": {"h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs,
+                                "floor_ms_full_duplex": floor_duplex, "floor_ms_one_way_at_a_time": floor_serial,
+                                "frac_of_full_duplex_floor": floor_duplex / ms_e2e,
+                                "frac_of_one_way_floor": floor_serial / ms_e2e,
+                                "how": "one 1 GiB cudaMemcpyAsync of page-locked memory per direction, CUDA "
+                                       "events; floor = the step's bytes at those rates, both directions at "
+                                       "once (full duplex) or one after the other"}}
+    # the paper's data generation (Sec. 5.1): per material about 3.2 M
+    # queries (8x8 footprint centres x 20 sizes x valid pairs of
+    # 8x8-stratified directions) integrated at 2048 spp, three materials
+    pm = W.paper_materials()
+    fab.set_materials(pm)
+    gen = []
+    for m_idx in (0, 81, 300):
+        t0 = time.time()
+        q = W.paper_queries(m_idx)
+        host_s = time.time() - t0
+        gq = GBuffer.from_numpy(q)
+        comps_q = torch.empty((gq.n, 4), dtype=torch.float32, device="cuda")
+        rgb_q = torch.empty((gq.n, 3), dtype=torch.float32, device="cuda")
+        fab.shade_reference(gq, 64, 32, 0xDA7A, out_rgb=rgb_q, out_comps=comps_q)
+        ms_q = timed(torch, stream, lambda k: fab.shade_reference(gq, 64, 32, 0xDA7A + k, out_rgb=rgb_q,
+                                                                  out_comps=comps_q), 3)
+        gen.append({"material": m_idx, "weave": int(pm[m_idx]["pattern"]), "queries": gq.n,
+                    "gpu_ms": ms_q, "host_query_build_s": host_s})
+        del gq, comps_q, rgb_q
+    fab.sync_status()
+    fab.set_materials(mats)
+    per_mat_s = float(np.mean([r["gpu_ms"] for r in gen])) * 1e-3
+    out["paper_data_generation"] = {
+        "materials_timed": gen, "spp": 2048, "gpu_s_per_material": per_mat_s,
+        "gpu_s_all_465_materials": per_mat_s * len(pm),
+        "sample_evals_per_s": float(np.mean([r["queries"] * 2048 / (r["gpu_ms"] * 1e-3) for r in gen])),
+        "paper": "about 22 min per material, 165 h for 465 materials (Sec. 5.1; hardware not stated, with "
+                 "transmission and inter-yarn shadowing-masking, which this model leaves out)",
+        "note": "reference kernel over the paper's query set of one material, CUDA events; the host-side "
+                "construction of the query set (numpy) is reported separately"}
     # batched 4K: one persistent launch over a 3840x2160 frame with materials
     # interleaved per 16x16 tile plus 4 views x 64 ragged tiles, from a CUDA
     # graph, per operand precision; the reference at 256 spp on the 4K view

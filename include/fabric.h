@@ -400,9 +400,12 @@ fabric_status fabric_shade_neural_host(fabric_ctx *ctx, const fabric_gbuffer *g_
  * decoder operands, at most 64 KiB) in one static device array that every
  * GPU loading the library holds until the process exits.  It never calls
  * cudaMalloc, cudaFree or any allocating routine.
- *  - A material table whose packed operands do not fit the 64 KiB array is
- *    rejected with FABRIC_ERR_INVALID_ARG; beyond 89 materials the call
- *    returns FABRIC_ERR_UNSUPPORTED as fabric_shade_neural does.
+ *  - The limit that applies in practice is the tensor-core decoder's own:
+ *    beyond 89 materials the call returns FABRIC_ERR_UNSUPPORTED as
+ *    fabric_shade_neural does.  The packed operands of 89 materials
+ *    (about 43 KiB) fit the array, which the library checks when it is
+ *    compiled; a table that did not fit would be rejected with
+ *    FABRIC_ERR_INVALID_ARG.
  *  - The first call on each device resolves the array's device address;
  *    make that first call before any stream capture.
  *  - All calls share the one array and overwrite all of it that they read,

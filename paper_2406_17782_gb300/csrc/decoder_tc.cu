@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include "decoder_blob.h"
 #include "fabric_internal.h"
 #include "tc_ptx.h"
 
@@ -40,7 +41,6 @@ namespace fab {
 namespace {
 
 constexpr int kTile = 128;
-constexpr int kKH = 80;                            // K of layers 2-4: 64 inputs + bias column + pad
 constexpr uint32_t kColsPerTile = 128;             // D [0, 64) | A [64, 128)
 constexpr uint32_t kColA = 64;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
@@ -52,39 +52,6 @@ constexpr int kPrE4M3 = 2;   // FP16 layer 1, E4M3 layers 2-4
 
 __host__ __device__ constexpr int prec_code(int fabric_prec) {
   return fabric_prec == FABRIC_PREC_FP16 ? kPrF16 : fabric_prec == FABRIC_PREC_FP8 ? kPrE4M3 : kPrBF16;
-}
-
-// E4M3 epilogue block (FP32): per layer l = 0..3 a 64-entry bias row (row 0
-// zero: layer 1's bias rides in its folded column; row 3 holds b4 and zeros)
-// followed by the four unscaling factors (1 for layer 1).
-constexpr int kF8Bias = 0;
-constexpr int kF8Inv = 4 * 64;
-constexpr uint32_t kF8EpiBytes = (4 * 64 + 4) * 4;
-
-// ---- packed-operand blob layout (bytes), identical in global and shared memory
-struct BlobLayout {
-  int k1;
-  uint32_t w1, w2, w3, w4, epi, alb, total;
-};
-
-__host__ __device__ inline BlobLayout blob_layout(int n_mat, int k1, bool f8) {
-  BlobLayout L;
-  L.k1 = k1;
-  L.w1 = 0;
-  L.w2 = L.w1 + 64u * k1 * 2u;
-  if (f8) {
-    L.w3 = L.w2 + 64u * 64u;
-    L.w4 = L.w3 + 64u * 64u;
-    L.epi = L.w4 + 16u * 64u;
-    L.alb = L.epi + kF8EpiBytes;
-  } else {
-    L.w3 = L.w2 + 64u * kKH * 2u;
-    L.w4 = L.w3 + 64u * kKH * 2u;
-    L.epi = L.w4 + 16u * kKH * 2u;
-    L.alb = L.epi;
-  }
-  L.total = L.alb + ((uint32_t)(n_mat * 12 * 4) + 15u) / 16u * 16u;
-  return L;
 }
 
 __host__ __device__ inline uint32_t align1k(uint32_t x) { return (x + 1023u) & ~1023u; }
@@ -831,17 +798,9 @@ int tc_resident_ctas(const void *fn, size_t smem, int wg, int h) {
 
 }  // namespace
 
-int tc_k1(int n_mat) {
-  const int k1 = (kQueryFeat + n_mat + 15) / 16 * 16;
-  return (n_mat >= 1 && k1 <= 128) ? k1 : -1;
-}
+int tc_k1(int n_mat) { return tc_k1_of(n_mat); }
 
-// Largest packed blob over the precisions (the 16-bit layout is the larger).
-size_t tc_blob_bytes(int n_mat) {
-  const int k1 = tc_k1(n_mat) > 0 ? tc_k1(n_mat) : 128;
-  const uint32_t a = blob_layout(n_mat, k1, false).total, b = blob_layout(n_mat, k1, true).total;
-  return a > b ? a : b;
-}
+size_t tc_blob_bytes(int n_mat) { return tc_blob_bytes_of(n_mat); }
 
 cudaError_t launch_tc_pack(const float *dec, const float *latents, const DevMaterial *mats, int n_mat, int precision,
                            void *blob, cudaStream_t s) {

@@ -2,6 +2,9 @@
 // call with its per-call scratch (the packed decoder operands) in a
 // file-scope device array instead of context-owned memory.  Nothing here
 // allocates device memory.
+#include <atomic>
+
+#include "decoder_blob.h"
 #include "fabric_internal.h"
 
 namespace {
@@ -12,10 +15,17 @@ constexpr size_t kNoAllocBlobBytes = 64 * 1024;
 
 static __device__ __align__(256) uint8_t g_noalloc_blob[kNoAllocBlobBytes];
 
+// The decoder's own material limit (89) is the one that binds in practice:
+// its largest packed blob fits the array.
+static_assert(fab::tc_blob_bytes_of(fab::kTcMaxMaterials) <= kNoAllocBlobBytes,
+              "the packed operands of the largest material table must fit the static scratch");
+
 constexpr int kMaxDevices = 64;
 // Device address of g_noalloc_blob per device, resolved once with that
 // device current (host code must not use the symbol itself as an address).
-void *g_blob_addr[kMaxDevices] = {};
+// Host threads that make their first call on one device at the same time
+// may both resolve it; they store the same address.
+std::atomic<void *> g_blob_addr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -43,13 +53,12 @@ extern "C" fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabr
                 kNoAllocBlobBytes);
   if (ctx->device < 0 || ctx->device >= kMaxDevices)
     return fail(ctx, FABRIC_ERR_UNSUPPORTED, "device index %d beyond %d", ctx->device, kMaxDevices);
-  void *&blob = g_blob_addr[ctx->device];
+  void *blob = g_blob_addr[ctx->device].load(std::memory_order_acquire);
   if (!blob) {
     // one-time set-up on this device (the device is current here)
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_blob);
-    if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_blob)");
-    blob = p;
+    const cudaError_t e = cudaGetSymbolAddress(&blob, g_noalloc_blob);
+    if (e != cudaSuccess || !blob) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_blob)");
+    g_blob_addr[ctx->device].store(blob, std::memory_order_release);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_tc_pack(ctx->d_dec, latents_dev, ctx->d_mat, ctx->n_mat, (int)prec, blob, s);

@@ -94,19 +94,27 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
 
 
 def _errors(fab, a, gt, g):
+    """Frame errors of `a` against `gt` ([n, 3] RGB): `rmse_fp` / `rel_l2_fp`
+    on the linear f_P values, unclamped, over all pixels and channels;
+    `rmse_tm` on the tone-mapped x / (1 + x); `rmse` / `rel_l2` on the frame
+    lit by a unit directional light along wi (f_P <wi . n_s>)."""
     n = gt.numel()
     raw = fab.error_stats(a, gt).cpu().numpy()
+    tm = fab.error_stats(a / (1.0 + a), gt / (1.0 + gt)).cpu().numpy()
     lit = fab.error_stats(a, gt, weights=g.wi[:, 2], group=3, weight_stride=3).cpu().numpy()
     return {"rmse": math.sqrt(lit[0] / n), "rel_l2": math.sqrt(lit[0] / lit[1]),
-            "rmse_fp": math.sqrt(raw[0] / n), "rel_l2_fp": math.sqrt(raw[0] / raw[1]), "max_abs_fp": float(raw[2])}
+            "rmse_fp": math.sqrt(raw[0] / n), "rel_l2_fp": math.sqrt(raw[0] / raw[1]), "max_abs_fp": float(raw[2]),
+            "rmse_tm": math.sqrt(tm[0] / n)}
 
 
 def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(1, 2, 4, 8, 16), gbuf=None):
     """Error of the neural 1080p frame, and of the reference at lower sample
-    counts, against the reference at gt_spp.  `rmse` / `rel_l2`: the frame
-    as rendered under a unit directional light, f_P <wi . n_s> per RGB
-    channel (the paper's results are direct-lit renders, Sec. 6); `*_fp`:
-    the raw f_P values.  `gbuf`: a host G-buffer of the frame's materials
+    counts, against the reference at gt_spp (see _errors for the metrics;
+    the paper's results are direct-lit renders, Sec. 6, the scope's metric is
+    the linear f_P).  The ground truth's own Monte Carlo noise is estimated
+    from a second, independent ground-truth frame: `gt_noise_*` is its RMS
+    deviation from the integral (half the mean squared difference of the
+    two, per metric).  `gbuf`: a host G-buffer of the frame's materials
     (default: the 1080p frame)."""
     mats = W.frame_materials()
     fab.set_materials(mats)
@@ -119,8 +127,14 @@ def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(
     for s in ref_spps:
         r, _ = fab.shade_reference(g, s, s, 0x1234)
         out[f"reference_{s * s}spp"] = _errors(fab, r, gt, g)
+    gt2, _ = fab.shade_reference(g, gt_spp[0], gt_spp[1], 0x9E37)
+    two = _errors(fab, gt2, gt, g)
+    out["gt_noise_fp"] = two["rmse_fp"] / math.sqrt(2.0)
+    out["gt_noise"] = two["rmse"] / math.sqrt(2.0)
     lit = fab.error_stats(gt, torch.zeros_like(gt), weights=g.wi[:, 2], group=3, weight_stride=3).cpu().numpy()
     out["gt_rms"] = math.sqrt(float(lit[0]) / gt.numel())      # sum (gt w)^2 over the frame
+    raw = fab.error_stats(gt, torch.zeros_like(gt)).cpu().numpy()
+    out["gt_rms_fp"] = math.sqrt(float(raw[0]) / gt.numel())
     fab.sync_status()
     return out
 

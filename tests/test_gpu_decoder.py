@@ -1,15 +1,20 @@
 """Parity of the neural decoder kernels with the FP64 network oracle.
 
-* FP32 SIMT: per point |dy| <= max(1e-5 |y*|, B) on the raw head, where B is
-  the first-order FP32 forward rounding bound (gamma_n = n 2^-24 per dot
-  product, propagated through the layers) that takes over where y* is too
-  close to zero for a relative error to mean anything.
+* FP32 SIMT: per point and output |dy| <= 1e-5 max(|y*|, 1e-3 rms(y*)) (the
+  stated FP32 bound) plus 4 sigma, where sigma is the spread of FP32
+  arithmetic itself at that point, estimated by Monte Carlo arithmetic
+  (every rounding of an FP32 evaluation replaced by a random relative
+  perturbation of up to one unit roundoff; Parker, 1997).  Away from
+  cancellation sigma is far below the bound; where the head is a cancelling
+  sum no FP32 evaluation can meet the bound alone (about 2 % of the sampled
+  outputs, for the GPU and for a sequential FP32 evaluation on the CPU
+  alike), and the kernel must then be no noisier than FP32 itself.
 * FP16 tensor cores (the default tensor-core precision): relative L2
-  <= 5e-3 over the sampled frame against FP64, and <= 2e-3 against the FP16
+  <= 5e-3 over the sampled frame against FP64, and <= 5e-4 against the FP16
   operand-rounding emulation of the same network.
 * BF16 tensor cores: relative L2 <= 1.2e-2 against FP64 (BF16 operand
   rounding alone costs 8.2e-3 on this network, see the emulation), and
-  <= 2e-3 against the BF16 emulation.
+  <= 5e-4 against the BF16 emulation.
 """
 import numpy as np
 import pytest
@@ -24,7 +29,7 @@ from paper_2406_17782_gb300.api import GBuffer
 pytestmark = pytest.mark.gpu
 
 TOL_FP64 = {"fp16": 5e-3, "bf16": 1.2e-2}
-TOL_EMU = 2e-3
+TOL_EMU = 5e-4
 
 
 def rel_l2(got, want):
@@ -67,21 +72,36 @@ def emulate(prec, dec_flat, z, mats, g):
     return comps, M.recombine(comps, mats, g["material"])
 
 
-def fp32_forward_bound(P, x):
-    """First-order bound on the FP32 evaluation error of the raw head:
-    |d a| <= |W| |d x| + gamma_n (|W| |x| + |b|), gamma_n = n u, u = 2^-24,
-    input features carrying one rounding each; ReLU is 1-Lipschitz."""
+def fp32_arithmetic_spread(P, x, trials=8, seed=0):
+    """Per point and output, the standard deviation of the raw head over
+    Monte Carlo arithmetic evaluations of the network: features perturbed by
+    a relative U(-2u, 2u) (the kernel computes them with library sin, cos
+    and log), every multiply-add result by a relative U(-u, u), u = 2^-24."""
     u = 2.0 ** -24
-    dx = u * np.abs(x) + 1e-300
-    h = x
+    rng = np.random.default_rng(seed)
+    h = np.repeat(x[None], trials, 0)
+    h = h * (1.0 + rng.uniform(-2 * u, 2 * u, h.shape))
     for Wn, bn in (("W1", "b1"), ("W2", "b2"), ("W3", "b3"), ("W4", "b4")):
         Wm, b = P[Wn], P[bn]
-        n = Wm.shape[1]
-        a = h @ Wm.T + b
-        da = dx @ np.abs(Wm).T + n * u * (np.abs(h) @ np.abs(Wm).T + np.abs(b))
-        h = np.maximum(a, 0) if Wn != "W4" else a
-        dx = da
-    return dx
+        acc = np.broadcast_to(b, (trials, x.shape[0], len(b))).copy()
+        for k in range(Wm.shape[1]):
+            acc = (acc + h[:, :, k:k + 1] * Wm[None, None, :, k]) * (1.0 + rng.uniform(-u, u, acc.shape))
+        h = np.maximum(acc, 0.0) if Wn != "W4" else acc
+    return h.std(0)
+
+
+def fp32_sequential_forward(P, x):
+    """A plain FP32 evaluation on the CPU: features rounded to FP32, each
+    output a chain of multiply-adds from its bias in input order."""
+    h = x.astype(np.float32)
+    for Wn, bn in (("W1", "b1"), ("W2", "b2"), ("W3", "b3"), ("W4", "b4")):
+        Wm = P[Wn].astype(np.float32).astype(np.float64)
+        acc = np.tile(P[bn].astype(np.float32), (h.shape[0], 1))
+        h64 = h.astype(np.float64)
+        for k in range(Wm.shape[1]):
+            acc = (acc.astype(np.float64) + h64[:, k:k + 1] * Wm[None, :, k]).astype(np.float32)
+        h = np.maximum(acc, 0) if Wn != "W4" else acc
+    return h.astype(np.float64)
 
 
 @pytest.mark.parametrize("a_in_tmem", [False, True])
@@ -101,22 +121,26 @@ def test_fp32_decoder_per_point(fab, setup):
     g = W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 4096, stream="dec-fp32"))
     gd = GBuffer.from_numpy(g)
     zt = torch.from_numpy(z).cuda()
-    y_gpu = fab.decoder_forward(gd, zt, torch.from_numpy(dec).cuda()).cpu().numpy()
+    y_gpu = fab.decoder_forward(gd, zt, torch.from_numpy(dec).cuda()).cpu().numpy().astype(np.float64)
     rgb, comps = fab.shade_neural(gd, zt, "fp32", comps=True)
     fab.sync_status()
     P = M.unpack(dec, M.DEC_SHAPES)
     x = M.decoder_inputs(z, g["material"], g)
     y = M.decoder_forward(P, x)
-    tol = np.maximum(1e-5 * np.abs(y), fp32_forward_bound(P, x))
-    worst = np.max(np.abs(y_gpu - y) / tol)
-    rel = np.abs(y_gpu - y) / np.maximum(np.abs(y), 1e-30)
-    print(f"fp32 decoder: worst |dy|/tol {worst:.3f}; median rel {np.median(rel):.1e}; "
-          f"fraction within 1e-5 rel {np.mean(rel <= 1e-5):.4f}")
+    tol7 = 1e-5 * np.maximum(np.abs(y), 1e-3 * np.sqrt((y ** 2).mean(0))[None, :])
+    sigma = fp32_arithmetic_spread(P, x)
+    dy = np.abs(y_gpu - y)
+    dy_cpu = np.abs(fp32_sequential_forward(P, x) - y)
+    within, within_cpu = np.mean(dy <= tol7), np.mean(dy_cpu <= tol7)
+    worst = np.max(dy / (tol7 + 4.0 * sigma))
+    print(f"fp32 decoder: outputs within 1e-5 max(|y|, 1e-3 rms): GPU {within:.4f}, CPU FP32 {within_cpu:.4f}; "
+          f"worst |dy| / (bound + 4 sigma) {worst:.3f}; rel-L2 {rel_l2(y_gpu, y):.2e}")
     assert worst <= 1.0
+    assert within >= within_cpu - 0.01
     assert rel_l2(y_gpu, y) <= 1e-6
     want_c = M.head_to_components(y)
     slope = np.concatenate([np.ones_like(y[:, :2]), np.exp(y[:, 2:]) / M.K_SPEC], axis=1)
-    assert np.all(np.abs(comps.cpu().numpy() - want_c) <= tol * slope * 1.01 + 1e-12)
+    assert np.all(np.abs(comps.cpu().numpy() - want_c) <= (tol7 + 4.0 * sigma) * slope * 1.01 + 1e-12)
     want_rgb = M.recombine(want_c, mats, g["material"])
     np.testing.assert_allclose(rgb.cpu().numpy(), want_rgb, rtol=2e-5, atol=1e-6)
 
@@ -145,8 +169,12 @@ def test_fp16_decoder_multiscale_footprints(fab, setup):
     rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp16", comps=True)
     fab.sync_status()
     want_c, want_rgb = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, g)
+    emu_c, _ = emulate("fp16", dec, z, mats, g)
+    e_emu = rel_l2(comps.cpu().numpy(), emu_c)
+    print(f"fp16 multi-scale: rel-L2 vs FP64 {rel_l2(comps.cpu().numpy(), want_c):.2e}, vs emulation {e_emu:.2e}")
     assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
     assert rel_l2(rgb.cpu().numpy(), want_rgb) <= TOL_FP64["fp16"]
+    assert e_emu <= TOL_EMU
 
 
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
@@ -156,7 +184,11 @@ def test_fp16_ragged_tiles(fab, setup, n):
     rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp16", comps=True)
     fab.sync_status()
     want_c, _ = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, g)
+    emu_c, _ = emulate("fp16", dec, z, mats, g)
+    e_emu = rel_l2(comps.cpu().numpy(), emu_c)
+    print(f"fp16 ragged n={n}: rel-L2 vs FP64 {rel_l2(comps.cpu().numpy(), want_c):.2e}, vs emulation {e_emu:.2e}")
     assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
+    assert e_emu <= TOL_EMU
 
 
 def test_fp16_full_frame_sampled(fab, setup):
@@ -172,8 +204,13 @@ def test_fp16_full_frame_sampled(fab, setup):
     idx = W.sample_indices(len(g["u"]), 8192, stream="dec-full")
     sub = W.subset(g, idx)
     want_c, want_rgb = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), z, mats, sub)
+    emu_c, _ = emulate("fp16", dec, z, mats, sub)
+    e_emu = rel_l2(comps.cpu().numpy()[idx], emu_c)
+    print(f"fp16 full frame: rel-L2 vs FP64 {rel_l2(comps.cpu().numpy()[idx], want_c):.2e}, "
+          f"vs emulation {e_emu:.2e}")
     assert rel_l2(comps.cpu().numpy()[idx], want_c) <= TOL_FP64["fp16"]
     assert rel_l2(rgb.cpu().numpy()[idx], want_rgb) <= TOL_FP64["fp16"]
+    assert e_emu <= TOL_EMU
     assert np.isfinite(rgb.cpu().numpy()).all()
     # the prepared state is refused once the parameters change
     fab.set_params(dec, W.encoder_init())
@@ -211,8 +248,12 @@ def test_fp16_many_materials_wider_first_layer(fab, setup):
     _, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(zz).cuda(), "fp16", comps=True)
     fab.sync_status()
     want_c, _ = M.shade_neural(M.unpack(dec, M.DEC_SHAPES), zz, many, g)
+    emu_c, _ = emulate("fp16", dec, zz, many, g)
     fab.set_materials(mats)
+    e_emu = rel_l2(comps.cpu().numpy(), emu_c)
+    print(f"fp16 40 materials: rel-L2 vs FP64 {rel_l2(comps.cpu().numpy(), want_c):.2e}, vs emulation {e_emu:.2e}")
     assert rel_l2(comps.cpu().numpy(), want_c) <= TOL_FP64["fp16"]
+    assert e_emu <= TOL_EMU
 
 
 def test_error_stats_mixed_magnitudes(fab):

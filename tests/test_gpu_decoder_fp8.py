@@ -3,9 +3,10 @@
 Layer 1 keeps FP16 operands; layers 2-4 run kind::f8f6f4 with E4M3
 activations and per-layer power-of-two-scaled E4M3 weights.  The kernel is
 held to the oracle's operand-rounding emulation of exactly that path
-(relative L2 <= 5e-3 over the sampled frame: the two sides round FP32
-values that differ in their last bits, and a rare E4M3 rounding decision
-that flips moves one operand by a 3-bit-mantissa ulp).  Its distance to the
+(relative L2 <= 1e-6: the two sides sum the same rounded products in
+different orders, so their FP32 values differ in the last bits; an E4M3
+rounding decision that such a difference flipped would move one operand
+by a 3-bit-mantissa ulp and show far above this bound).  Its distance to the
 unrounded FP64 network is the cost of E4M3 itself (~0.12 relative L2 for
 the random-initialised decoder); it is printed and bounded loosely here so
 that a broken scale or bias, which costs O(1), still fails.
@@ -20,7 +21,7 @@ from paper_2406_17782_gb300.api import GBuffer
 
 pytestmark = pytest.mark.gpu
 
-TOL_EMU_E4M3 = 5e-3
+TOL_EMU_E4M3 = 1e-6
 LOOSE_FP64 = 0.25
 
 
@@ -82,8 +83,8 @@ def test_fp8_decoder_matches_e4m3_emulation(fab, setup):
 def test_fp8_ragged_tiles(fab, setup, n):
     g = W.subset(W.frame_gbuffer(), np.arange(9000, 9000 + n))
     e_c, e_rgb, _ = _check(fab, setup, g)
-    # a handful of points: one flipped rounding weighs more than over 8192
-    assert e_c <= 3 * TOL_EMU_E4M3 and e_rgb <= 3 * TOL_EMU_E4M3
+    print(f"fp8 ragged n={n}: rel-L2 vs E4M3 emulation comps {e_c:.2e} rgb {e_rgb:.2e}")
+    assert e_c <= TOL_EMU_E4M3 and e_rgb <= TOL_EMU_E4M3
 
 
 def test_fp8_full_frame_sampled(fab, setup):
@@ -98,6 +99,7 @@ def test_fp8_full_frame_sampled(fab, setup):
     idx = W.sample_indices(len(g["u"]), 8192, stream="dec-full-fp8")
     sub = W.subset(g, idx)
     emu_c, emu_rgb = M.shade_neural_e4m3(M.unpack(dec, M.DEC_SHAPES), z, mats, sub)
+    print(f"fp8 full frame: rel-L2 vs E4M3 emulation comps {rel_l2(comps.cpu().numpy()[idx], emu_c):.2e}")
     assert rel_l2(comps.cpu().numpy()[idx], emu_c) <= TOL_EMU_E4M3
     assert rel_l2(rgb.cpu().numpy()[idx], emu_rgb) <= TOL_EMU_E4M3
     assert np.isfinite(rgb.cpu().numpy()).all()
@@ -122,4 +124,5 @@ def test_fp8_weight_scales_follow_the_layer_amax(fab, setup):
     finally:
         fab.set_params(dec, W.encoder_init())
     emu_c, _ = M.shade_neural_e4m3(M.unpack(dec2.astype(np.float64), M.DEC_SHAPES), z, mats, g)
+    print(f"fp8 rescaled layers: rel-L2 vs E4M3 emulation {rel_l2(comps.cpu().numpy(), emu_c):.2e}")
     assert rel_l2(comps.cpu().numpy(), emu_c) <= TOL_EMU_E4M3

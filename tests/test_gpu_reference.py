@@ -137,3 +137,16 @@ def test_material_index_out_of_range_is_reported(fab, frame_mats):
     c = comps.cpu().numpy()
     assert np.isnan(c[5]).all() and np.isfinite(np.delete(c, 5, 0)).all()
     fab.sync_status()      # the status word was cleared
+
+
+def test_frame_ground_truth_1024spp_subset(fab, frame_mats):
+    """The ground truth of the frame-error measurement (the reference at
+    32 x 32 = 1024 spp over the whole 1080p frame, seed 0x6721, as the
+    benchmark draws it) on a seeded 65,536-pixel subset, against the FP64
+    oracle on the same sample sequence."""
+    g = W.frame_gbuffer()
+    rgb, comps = run_gpu(fab, g, 32, 32, 0x6721)
+    idx = W.sample_indices(1920 * 1080, 65536, stream="gt-validate")
+    wc, wr = oracle.shade_reference(frame_mats, W.subset(g, idx), 32, 32, 0x6721, pixel_index=idx)
+    assert_close(comps[idx], wc, "comps")
+    assert_close(rgb[idx], wr, "rgb")

@@ -2,7 +2,10 @@
 FP64 oracle and the FP32 path.  The gradient of one step is read back from
 Adam's first moment (m = (1 - beta1) g after a step with lr = 0, saved in the
 checkpoint), so the comparison needs no extra interface.  BF16 operands
-(8-bit mantissas) in every product give about 1e-2 relative error."""
+(8-bit mantissas) in every product give about 1.5e-3 relative L2 error in
+the decoder's gradient and 5-8e-3 in the encoder's (which receives the
+latent gradients, sums of BF16 products over every query of a material);
+the gates are 5e-3 and 2e-2."""
 import os
 
 import numpy as np
@@ -16,6 +19,8 @@ from paper_2406_17782_gb300.api import GBuffer
 pytestmark = pytest.mark.gpu
 
 ND, NE = M.n_params(M.DEC_SHAPES), M.n_params(M.ENC_SHAPES)
+TOL_DEC_BF16 = 5e-3
+TOL_ENC_BF16 = 2e-2
 
 
 def rel_l2(a, b):
@@ -77,7 +82,7 @@ def test_tensor_core_gradient_matches_oracle(fab, tmp_path, loss_mode, n):
     assert abs(loss_32 - want_loss) <= 1e-5 * abs(want_loss)
     assert rel_l2(g_32, want) <= 1e-4
     assert abs(loss_bf - want_loss) <= 2e-2 * abs(want_loss)
-    assert rel_l2(g_bf[:ND], want[:ND]) <= 3e-2 and rel_l2(g_bf[ND:], want[ND:]) <= 3e-2
+    assert rel_l2(g_bf[:ND], want[:ND]) <= TOL_DEC_BF16 and rel_l2(g_bf[ND:], want[ND:]) <= TOL_ENC_BF16
 
 
 def test_tensor_core_gradient_many_materials(fab, tmp_path):
@@ -92,8 +97,10 @@ def test_tensor_core_gradient_many_materials(fab, tmp_path):
     dec, enc = W.decoder_init(weight_bound="small"), W.encoder_init(weight_bound="small")
     want_loss, want = oracle_gradient(mats, g, target, dec, enc, "eq11")
     loss_bf, g_bf = one_step_gradient(fab, tmp_path, "bf16", "eq11", mats, gd, tt, dec, enc)
+    print(f"1600 materials: loss bf16 {loss_bf:.6g} fp64 {want_loss:.6g}; grad rel-L2 decoder "
+          f"{rel_l2(g_bf[:ND], want[:ND]):.2e}, encoder {rel_l2(g_bf[ND:], want[ND:]):.2e}")
     assert abs(loss_bf - want_loss) <= 2e-2 * abs(want_loss)
-    assert rel_l2(g_bf[:ND], want[:ND]) <= 3e-2 and rel_l2(g_bf[ND:], want[ND:]) <= 3e-2
+    assert rel_l2(g_bf[:ND], want[:ND]) <= TOL_DEC_BF16 and rel_l2(g_bf[ND:], want[ND:]) <= TOL_ENC_BF16
 
 
 def test_tensor_core_training_is_repeatable_and_learns(fab):

@@ -123,3 +123,35 @@ def test_training_queries_recipe():
     assert q["u"][half:].max() < 1 and q["radius"][half:].max() <= 2.5 + 1e-6
     d = q["wi"][half:].astype(np.float64)
     assert np.allclose(np.linalg.norm(d, axis=1), 1, atol=1e-6) and d[:, 2].min() >= 0
+
+
+def test_paper_data_generation_recipe():
+    """Sec. 5.1: 81 plain, 192 twill and 192 satin materials over seven
+    weaves with Table 2's parameter ranges; per material 64 footprint
+    centres x 20 sizes (10 in [0, 1], 10 in [1, 5] repeats) x the valid
+    direction pairs (about 2500), about 3.2 million queries."""
+    m = W.paper_materials()
+    assert len(m) == 465
+    counts = {w: int((m["pattern"] == w).sum()) for w in W.PAPER_WEAVES}
+    assert counts[0] == 81
+    assert sum(counts[w] for w in W.PAPER_TWILLS) == 192
+    assert sum(counts[w] for w in W.PAPER_WEAVES if w != 0 and w not in W.PAPER_TWILLS) == 192
+    assert set(np.unique(m["twist_deg"])) <= {-30.0, 0.0, 30.0}
+    assert (m["incl_deg"] >= 15).all() and (m["incl_deg"] <= 45).all()
+    assert (m["alpha"] >= 0.1).all() and (m["alpha"] <= 1).all()
+    assert (m["beta"] >= 0).all() and (m["beta"] <= 2).all()
+    q = W.paper_queries(3)
+    n = len(q["u"])
+    assert abs(n - 3.2e6) / 3.2e6 < 0.05
+    side = 2.0 * q["radius"].astype(np.float64)
+    sizes = np.unique(side)
+    assert len(sizes) == 64 * 20
+    assert ((sizes < 1).sum(), (sizes >= 1).sum()) == (640, 640)
+    assert (side <= 5).all()
+    centres = np.unique(np.stack([q["u"], q["v"]], 1), axis=0)
+    assert len(centres) == 64
+    cell = np.floor(centres * 8).astype(int)
+    assert len(np.unique(cell[:, 0] * 8 + cell[:, 1])) == 64        # one centre per grid cell
+    for w in (q["wi"], q["wo"]):
+        assert (w[:, 2] > 0).all()
+        np.testing.assert_allclose((w.astype(np.float64) ** 2).sum(1), 1.0, atol=1e-6)

@@ -1,8 +1,10 @@
 """fabric_shade_neural_noalloc: neural shading for callers that may not
-allocate device memory while drawing (e.g. a frame captured into a CUDA
-graph, or a host application that forbids plug-in allocations).  Its output
-must match fabric_shade_neural within the decoder tests' tolerance, call
-after call, although every call reuses the same static scratch array."""
+allocate device memory while drawing (e.g. a host application that owns all
+device memory and forbids plug-ins to allocate at draw time).  It runs the
+same operand packing and tensor-core decoder kernels as fabric_shade_neural,
+only with its packed operands in a static array, so its outputs must equal
+that call's bit for bit, call after call, although every call reuses and
+overwrites the same array."""
 import ctypes
 
 import numpy as np
@@ -15,14 +17,6 @@ from paper_2406_17782_gb300.api import GBuffer
 
 pytestmark = pytest.mark.gpu
 
-TOL = 5e-3    # relative L2, as for the FP16 decoder against the FP64 oracle
-
-
-def rel_l2(a, b):
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
-    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
-
 
 def call_noalloc(fab, g: GBuffer, latents, prec, rgb, comps):
     gs = g.struct()
@@ -32,22 +26,25 @@ def call_noalloc(fab, g: GBuffer, latents, prec, rgb, comps):
                                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
-def test_noalloc_matches_allocating_call_twice(fab, prec):
+def test_noalloc_matches_allocating_call_twice(fab):
+    """Two calls in a row per precision, in an order that changes the
+    array's layout from one precision to the next (E4M3 blobs are smaller
+    than 16-bit ones), so stale bytes from an earlier call would show."""
     mats = W.frame_materials()
     fab.set_materials(mats)
     fab.set_params(W.decoder_init(), W.encoder_init())
     lat = torch.from_numpy(W.random_latents(len(mats))).cuda()
     g = GBuffer.from_numpy(W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 50_000, stream="noalloc")))
-    want_rgb, want_c = fab.shade_neural(g, lat, prec, comps=True)
-    fab.sync_status()
-    for call in range(2):
-        rgb = torch.full((g.n, 3), float("nan"), device="cuda")
-        comps = torch.full((g.n, 4), float("nan"), device="cuda")
-        check(call_noalloc(fab, g, lat, prec, rgb, comps), fab.h)
+    for prec in ("fp8", "fp16", "bf16", "fp8"):
+        want_rgb, want_c = fab.shade_neural(g, lat, prec, comps=True)
         fab.sync_status()
-        assert rel_l2(rgb.cpu().numpy(), want_rgb.cpu().numpy()) <= TOL, call
-        assert rel_l2(comps.cpu().numpy(), want_c.cpu().numpy()) <= TOL, call
+        for call in range(2):
+            rgb = torch.full((g.n, 3), float("nan"), device="cuda")
+            comps = torch.full((g.n, 4), float("nan"), device="cuda")
+            check(call_noalloc(fab, g, lat, prec, rgb, comps), fab.h)
+            fab.sync_status()
+            assert torch.equal(rgb, want_rgb), (prec, call)
+            assert torch.equal(comps, want_c), (prec, call)
 
 
 def test_noalloc_rejects_what_it_cannot_hold(fab):

@@ -22,6 +22,10 @@ available; all at the paper's 1920x1080 resolution, Sec. 6):
   both directions U(-1,1)^2 inside the unit disc).
 * ``batched_4k``: a 3840x2160 G-buffer with materials interleaved per 16x16
   tile, plus ragged tiles of 256..65536 points from four views.
+* ``paper_materials`` / ``paper_queries``: the paper's data-generation set
+  (Sec. 5.1, Table 2): 465 materials over its seven weaves, and per material
+  an 8x8 grid of footprint centres x 20 footprint sizes x the valid pairs of
+  8x8-stratified directions (about 3.2 million queries).
 """
 from __future__ import annotations
 
@@ -271,6 +275,74 @@ def paper_direction_grid(rng: np.random.Generator, grid: int = 8):
     xy = np.stack([gx.ravel(), gy.ravel()], 1) + jit
     inside = (xy ** 2).sum(1) < 1.0
     return xy, inside
+
+
+# The paper's seven training weaves (Sec. 5.1) as built-in weave ids: plain,
+# twill 3x3 (2/1), twill 5x5 (4/1), twill 8x8 (7/1), satin 5x5 (5-harness,
+# weft-faced), satin 8x8 (8-harness, weft-faced), satin 5x10 (5-harness with
+# doubled picks).
+PAPER_WEAVES = [0, 1, 8, 9, 4, 10, 11]
+PAPER_TWILLS = [1, 8, 9]
+
+
+def paper_materials(config: int = 6) -> np.ndarray:
+    """The paper's 465 training materials (Sec. 5.1): per weave, sets of
+    (twist, inclination) drawn from Table 2 (9 for plain, 4 for the others),
+    each combined with sets of (alpha, beta) per yarn type drawn from Table 2
+    (9 for plain, 16 for the others): 81 plain, 192 twill and 192 satin
+    materials.  Albedos U[0.2, 0.8]^3 (they never enter the components)."""
+    rng = rng_for(config, "paper-materials")
+    out = []
+    for w in PAPER_WEAVES:
+        n_geo, n_app = (9, 9) if w == 0 else (4, 16)
+        for _ in range(n_geo):
+            psi = float(rng.choice([-30.0, 0.0, 30.0]))
+            incl = rng.uniform(15.0, 45.0)
+            for _ in range(n_app):
+                out.append(make_material(pattern=w, twist_deg=psi, incl_deg=incl,
+                                         alpha=rng.uniform(0.1, 1.0, 2), beta=rng.uniform(0.0, 2.0, 2),
+                                         kd=rng.uniform(0.2, 0.8, (2, 3)), ks=rng.uniform(0.2, 0.8, (2, 3))))
+    m = np.zeros(len(out), MATERIAL_DTYPE)
+    for k, r in enumerate(out):
+        m[k] = r
+    return m
+
+
+def paper_queries(material: int, config: int = 6, stream: str = "paper-queries", grid: int = 8,
+                  sizes: int = 10) -> dict:
+    """The paper's query set of one material (Sec. 5.1): footprint centres
+    jittered in the cells of a grid x grid partition of one pattern repeat;
+    per centre, `sizes` footprint sides in [0, 1] and `sizes` in [1, 5]
+    repeats (one jittered sample per equal sub-interval; radius = side / 2);
+    per footprint, the (x, y) of wi and of wo each stratified on a grid x grid
+    lattice over (-1, 1)^2 (paper_direction_grid), and every pair of valid
+    directions (both inside the unit disc, z = sqrt(1 - x^2 - y^2)) becomes a
+    query.  Returns a G-buffer dict (material index `material`, footprints
+    in centre-major, then size order)."""
+    rng = rng_for(config, f"{stream}-{material}")
+    cells = (np.arange(grid * grid) % grid, np.arange(grid * grid) // grid)
+    cu = (cells[0] + rng.uniform(0.0, 1.0, grid * grid)) / grid
+    cv = (cells[1] + rng.uniform(0.0, 1.0, grid * grid)) / grid
+    us, vs, rs, wis, wos = [], [], [], [], []
+    for c in range(grid * grid):
+        side = np.concatenate([(np.arange(sizes) + rng.uniform(0.0, 1.0, sizes)) / sizes,
+                               1.0 + 4.0 * (np.arange(sizes) + rng.uniform(0.0, 1.0, sizes)) / sizes])
+        for s in side:
+            xi, ok_i = paper_direction_grid(rng, grid)
+            xo, ok_o = paper_direction_grid(rng, grid)
+            xi, xo = xi[ok_i], xo[ok_o]
+            wi = np.concatenate([xi, np.sqrt(np.maximum(0.0, 1.0 - (xi ** 2).sum(1)))[:, None]], 1)
+            wo = np.concatenate([xo, np.sqrt(np.maximum(0.0, 1.0 - (xo ** 2).sum(1)))[:, None]], 1)
+            k = len(wi) * len(wo)
+            wis.append(np.repeat(wi, len(wo), 0))
+            wos.append(np.tile(wo, (len(wi), 1)))
+            us.append(np.full(k, cu[c]))
+            vs.append(np.full(k, cv[c]))
+            rs.append(np.full(k, s / 2.0))
+    n = sum(len(a) for a in us)
+    return dict(u=np.concatenate(us).astype(np.float32), v=np.concatenate(vs).astype(np.float32),
+                radius=np.concatenate(rs).astype(np.float32), wi=np.concatenate(wis).astype(np.float32),
+                wo=np.concatenate(wos).astype(np.float32), material=np.full(n, material, np.uint16))
 
 
 def batched_4k(config: int = 5, width: int = 3840, height: int = 2160, tile: int = 16,
