@@ -1,0 +1,207 @@
+"""FP64 numpy oracle for the paper's own decoder structure (Sec. 4.2,
+"Decoder"; Fig. 3): one-blob encoding of the footprint's position and size,
+a two-layer spatial fusion of the material latent with them, and an angular
+decoder of five fully connected layers with one skip connection.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Written from the
+paper's description, with this build's readings where it is silent:
+
+* One-blob encoding (Mueller et al., "Neural Importance Sampling", 2019):
+  a scalar s in [0, 1] becomes k = 8 bins, bin i holding a Gaussian of
+  standard deviation 1/k centred at s, evaluated at the bin centre
+  (i + 1/2) / k.  The footprint centre (frac u, frac v) is periodic in the
+  weave repeat, so its distance to a bin centre wraps around the unit
+  interval (the Gaussian is wrapped: summed over all its periodic
+  images); the footprint size enters as
+  t = ln(max(r, 2^-20) / 1e-4) / ln(2.5 / 1e-4), which maps the half sides
+  1e-4 (the 1080p frame's smallest) and 2.5 (the largest of Table 2, a side
+  of five repeats) to 0 and 1.  3 inputs -> 24 channels, as the paper says.
+* Latent z in R^64 (the paper's size), from the parameter encoder of the
+  workload with 64 outputs.
+* Spatial fusion: h = lrelu(S2 lrelu(S1 [z | onehot-blob] + s1) + s2),
+  width W.
+* Angular decoder on [h | wi (x, y, z) | wo (x, y)] (the paper's angular
+  inputs): k1 = lrelu(A1 x + a1); a residual block of two layers whose skip
+  joins before the last leaky ReLU, k3 = lrelu(A3 lrelu(A2 k1 + a2) + a3 + k1);
+  k4 = lrelu(A4 k3 + a4); y = A5 k4 + a5 (four components, Eq. 7).  Five
+  fully connected layers, one skip.
+* Leaky ReLU slope 0.01; widths W = 64 or 128 (the paper gives none).
+
+Parameter layout (flat float vectors, weights [out][in]; shared as an
+interface with the CUDA library, each side implementing it on its own):
+  S1[W][88] s1[W] S2[W][W] s2[W] A1[W][W+5] a1[W] A2[W][W] a2[W]
+  A3[W][W] a3[W] A4[W][W] a4[W] A5[4][W] a5[4]
+Encoder: E1[128][22] e1[128] E2[128][128] e2[128] E3[64][128] e3[64], the
+workload's residual encoder (oracle.mlp) with a 64-wide output.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import mlp
+
+LATENT = 64
+BINS = 8
+SIGMA = 1.0 / BINS
+N_BLOB = 3 * BINS                         # 24 one-blob channels
+N_ANG = 5                                 # wi (x, y, z), wo (x, y)
+SLOPE = 0.01
+R_LO = 1e-4
+R_HI = 2.5
+WIDTHS = (64, 128)
+
+
+def dec_shapes(w: int):
+    return [("S1", (w, LATENT + N_BLOB)), ("s1", (w,)), ("S2", (w, w)), ("s2", (w,)),
+            ("A1", (w, w + N_ANG)), ("a1", (w,)), ("A2", (w, w)), ("a2", (w,)),
+            ("A3", (w, w)), ("a3", (w,)), ("A4", (w, w)), ("a4", (w,)),
+            ("A5", (mlp.N_OUT, w)), ("a5", (mlp.N_OUT,))]
+
+
+ENC_SHAPES = [("E1", (mlp.ENC_HIDDEN, mlp.ENC_IN)), ("e1", (mlp.ENC_HIDDEN,)),
+              ("E2", (mlp.ENC_HIDDEN, mlp.ENC_HIDDEN)), ("e2", (mlp.ENC_HIDDEN,)),
+              ("E3", (LATENT, mlp.ENC_HIDDEN)), ("e3", (LATENT,))]
+
+
+def lrelu(x):
+    return np.where(x > 0, x, SLOPE * x)
+
+
+def dlrelu(x):
+    return np.where(x > 0, 1.0, SLOPE)
+
+
+# --------------------------------------------------------------------------
+# one-blob encoding
+# --------------------------------------------------------------------------
+def oneblob(s: np.ndarray, periodic: bool) -> np.ndarray:
+    """[n] -> [n, 8]: exp(-d^2 / (2 sigma^2)) with d the distance from s to
+    bin centre (i + 1/2) / 8.  Periodic: the Gaussian wrapped around the
+    unit interval, i.e. summed over the images d + m of every integer m
+    (here m = -2..2; farther images weigh below exp(-200))."""
+    s = np.asarray(s, np.float64)[:, None]
+    c = (np.arange(BINS) + 0.5) / BINS
+    d = s - c[None, :]
+    if not periodic:
+        return np.exp(-d * d / (2.0 * SIGMA * SIGMA))
+    d = d - np.round(d)
+    return sum(np.exp(-(d + m) ** 2 / (2.0 * SIGMA * SIGMA)) for m in range(-2, 3))
+
+
+def size_coordinate(r: np.ndarray) -> np.ndarray:
+    r = np.maximum(np.asarray(r, np.float64), mlp.R_FLOOR)
+    return np.log(r / R_LO) / math.log(R_HI / R_LO)
+
+
+def spatial_features(u, v, r) -> np.ndarray:
+    """The 24 one-blob channels: frac(u) (8, periodic) | frac(v) (8,
+    periodic) | footprint size (8)."""
+    u = np.asarray(u, np.float64)
+    v = np.asarray(v, np.float64)
+    return np.concatenate([oneblob(u - np.floor(u), True), oneblob(v - np.floor(v), True),
+                           oneblob(size_coordinate(r), False)], axis=1)
+
+
+def angular_features(wi, wo) -> np.ndarray:
+    wi = np.asarray(wi, np.float64)
+    wo = np.asarray(wo, np.float64)
+    return np.concatenate([wi[:, :3], wo[:, :2]], axis=1)
+
+
+# --------------------------------------------------------------------------
+# decoder
+# --------------------------------------------------------------------------
+def decoder_forward(p: dict, z: np.ndarray, blob: np.ndarray, ang: np.ndarray, keep: bool = False):
+    """Raw head y [n, 4] from per-point latents z [n, 64], one-blob channels
+    [n, 24] and angular inputs [n, 5]."""
+    x0 = np.concatenate([np.asarray(z, np.float64), blob], axis=1)
+    g1 = x0 @ p["S1"].T + p["s1"]
+    h1 = lrelu(g1)
+    g2 = h1 @ p["S2"].T + p["s2"]
+    hs = lrelu(g2)
+    xa = np.concatenate([hs, ang], axis=1)
+    q1 = xa @ p["A1"].T + p["a1"]
+    k1 = lrelu(q1)
+    q2 = k1 @ p["A2"].T + p["a2"]
+    k2 = lrelu(q2)
+    q3 = k2 @ p["A3"].T + p["a3"] + k1            # skip joins before the last leaky ReLU
+    k3 = lrelu(q3)
+    q4 = k3 @ p["A4"].T + p["a4"]
+    k4 = lrelu(q4)
+    y = k4 @ p["A5"].T + p["a5"]
+    if keep:
+        return y, dict(x0=x0, g1=g1, h1=h1, g2=g2, xa=xa, q1=q1, k1=k1, q2=q2, k2=k2, q3=q3, k3=k3, q4=q4, k4=k4)
+    return y
+
+
+def decoder_backward(p: dict, c: dict, dy: np.ndarray):
+    """Gradients of sum(dy * y) w.r.t. every parameter, the latents and the
+    angular inputs: (grads, dz [n, 64], dang [n, 5])."""
+    g = {}
+    g["A5"] = dy.T @ c["k4"]
+    g["a5"] = dy.sum(0)
+    dq4 = (dy @ p["A5"]) * dlrelu(c["q4"])
+    g["A4"] = dq4.T @ c["k3"]
+    g["a4"] = dq4.sum(0)
+    dq3 = (dq4 @ p["A4"]) * dlrelu(c["q3"])
+    g["A3"] = dq3.T @ c["k2"]
+    g["a3"] = dq3.sum(0)
+    dq2 = (dq3 @ p["A3"]) * dlrelu(c["q2"])
+    g["A2"] = dq2.T @ c["k1"]
+    g["a2"] = dq2.sum(0)
+    dq1 = (dq2 @ p["A2"] + dq3) * dlrelu(c["q1"])  # through A2 and through the skip
+    g["A1"] = dq1.T @ c["xa"]
+    g["a1"] = dq1.sum(0)
+    dxa = dq1 @ p["A1"]
+    w = p["S2"].shape[0]
+    dg2 = dxa[:, :w] * dlrelu(c["g2"])
+    g["S2"] = dg2.T @ c["h1"]
+    g["s2"] = dg2.sum(0)
+    dg1 = (dg2 @ p["S2"]) * dlrelu(c["g1"])
+    g["S1"] = dg1.T @ c["x0"]
+    g["s1"] = dg1.sum(0)
+    dx0 = dg1 @ p["S1"]
+    return g, dx0[:, :LATENT], dxa[:, w:]
+
+
+def shade(p: dict, z_mat: np.ndarray, materials, gbuf: dict):
+    """Per-point shading with the paper's decoder: (components [n, 4],
+    rgb [n, 3]); z_mat [n_mat, 64] per material."""
+    mat = np.asarray(gbuf["material"], np.int64)
+    y = decoder_forward(p, np.asarray(z_mat, np.float64)[mat], spatial_features(gbuf["u"], gbuf["v"], gbuf["radius"]),
+                        angular_features(gbuf["wi"], gbuf["wo"]))
+    comps = mlp.head_to_components(y)
+    return comps, mlp.recombine(comps, materials, mat)
+
+
+def shade_rounded(p: dict, z_mat: np.ndarray, materials, gbuf: dict, r):
+    """Operand-rounding emulation of the tensor-core path: `r` rounds to the
+    16-bit operand type.  The one-blob channels, the angular inputs, every
+    weight, every activation after its leaky ReLU and every bias of layers
+    2-7 (they ride in a constant-one input column) are rounded; the latent
+    enters folded into a rounded per-material bias column
+    S1[:, :64] z_m + s1; the skip adds the rounded operand of k1; products
+    accumulate in FP32 (FP64 here).  With r = identity this is shade()."""
+    mat = np.asarray(gbuf["material"], np.int64)
+    blob = r(spatial_features(gbuf["u"], gbuf["v"], gbuf["radius"]))
+    ang = r(angular_features(gbuf["wi"], gbuf["wo"]))
+    fold = p["s1"][None, :] + np.asarray(z_mat, np.float64) @ p["S1"][:, :LATENT].T
+    h1 = r(lrelu(blob @ r(p["S1"][:, LATENT:]).T + r(fold)[mat]))
+    hs = r(lrelu(h1 @ r(p["S2"]).T + r(p["s2"])))
+    xa = np.concatenate([hs, ang], axis=1)
+    k1 = r(lrelu(xa @ r(p["A1"]).T + r(p["a1"])))
+    k2 = r(lrelu(k1 @ r(p["A2"]).T + r(p["a2"])))
+    k3 = r(lrelu(k2 @ r(p["A3"]).T + r(p["a3"]) + k1))
+    k4 = r(lrelu(k3 @ r(p["A4"]).T + r(p["a4"])))
+    y = k4 @ r(p["A5"]).T + r(p["a5"])
+    comps = mlp.head_to_components(y)
+    return comps, mlp.recombine(comps, materials, mat)
+
+
+def flops_per_point(w: int, folded: bool = True) -> int:
+    """Multiply-adds x 2 of one decoder evaluation; with the latent folded
+    into a bias, the first layer's K is the 24 one-blob channels."""
+    k0 = N_BLOB if folded else LATENT + N_BLOB
+    return 2 * (k0 * w + w * w + (w + N_ANG) * w + 3 * w * w + w * mlp.N_OUT)
