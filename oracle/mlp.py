@@ -361,8 +361,22 @@ def e4m3_scale_exponent(w) -> int:
     return 8 - int(e)
 
 
+def e4m3_rounding_margin(x) -> np.ndarray:
+    """Relative distance of each value to the nearest E4M3 rounding
+    boundary (the midpoint between two neighbouring E4M3 values): where it
+    is tiny, two evaluations whose FP32 sums differ in their last bits can
+    round the value to different E4M3 neighbours.  inf at exact zeros."""
+    a = np.abs(np.asarray(x, np.float64))
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -6)))
+    q = 2.0 ** (e - 3)
+    t = a / q
+    d = np.abs(t - (np.floor(t) + 0.5)) * q
+    with np.errstate(divide="ignore"):
+        return np.where(a > 0, d / a, np.inf)
+
+
 def shade_neural_e4m3(dec: dict, z: np.ndarray, materials, gbuf: dict,
-                      r16=round_fp16, r8=round_e4m3):
+                      r16=round_fp16, r8=round_e4m3, margins: list | None = None):
     """Operand-rounding emulation of the E4M3 tensor-core decoder.
 
     Layer 1 keeps 16-bit operands (r16): its weight block carries the latent
@@ -373,17 +387,27 @@ def shade_neural_e4m3(dec: dict, z: np.ndarray, materials, gbuf: dict,
     undoing of the scale are applied in FP32 to the FP32 product.  Every
     value is rounded to FP32 before it is rounded to an operand type, as in
     the kernel.  With r16 = r8 = identity this is the FP64 network up to
-    those FP32 roundings.  Returns (components [n, 4], rgb [n, 3])."""
+    those FP32 roundings.  Returns (components [n, 4], rgb [n, 3]); when
+    `margins` is a list, the per-point minimum of e4m3_rounding_margin over
+    the activations rounded to E4M3 is appended to it."""
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
     q = r16(f32(query_features(gbuf["u"], gbuf["v"], gbuf["radius"], gbuf["wi"], gbuf["wo"])))
     mat = np.asarray(gbuf["material"], np.int64)
     zf = np.asarray(z, np.float64)
     fold = dec["b1"][None, :] + zf @ dec["W1"][:, :LATENT].T            # [n_mat, 64]
     a = q @ r16(f32(dec["W1"][:, LATENT:])).T + r16(f32(fold))[mat]
-    h = r8(np.maximum(f32(a), 0.0))
+    margin = np.full(len(mat), np.inf)
+    pre = np.maximum(f32(a), 0.0)
+    margin = np.minimum(margin, e4m3_rounding_margin(pre).min(1))
+    h = r8(pre)
     for wn, bn, last in (("W2", "b2", False), ("W3", "b3", False), ("W4", "b4", True)):
         s = 2.0 ** e4m3_scale_exponent(dec[wn])
         a = f32(f32(h @ r8(f32(dec[wn]) * s).T) / s + f32(dec[bn]))
-        h = a if last else r8(np.maximum(a, 0.0))
+        if not last:
+            pre = np.maximum(a, 0.0)
+            margin = np.minimum(margin, e4m3_rounding_margin(pre).min(1))
+        h = a if last else r8(pre)
+    if margins is not None:
+        margins.append(margin)
     comps = head_to_components(h)
     return comps, recombine(comps, materials, gbuf["material"])

@@ -84,7 +84,7 @@ def test_plan_equals_per_segment_draws(fab, prepared, prec):
     P = M.unpack(dec, M.DEC_SHAPES)
     want_c, _ = M.shade_neural_e4m3(P, z, mats, host) if prec == "fp8" else M.shade_neural(P, z, mats, host)
     d = comps.cpu().numpy() - want_c
-    assert np.sqrt((d ** 2).sum() / (want_c ** 2).sum()) < {"fp16": 5e-3, "bf16": 1.2e-2, "fp8": 5e-3}[prec]
+    assert np.sqrt((d ** 2).sum() / (want_c ** 2).sum()) < {"fp16": 5e-3, "bf16": 1.2e-2, "fp8": 2e-3}[prec]
     plan.close()
 
 

@@ -2,11 +2,15 @@
 
 Layer 1 keeps FP16 operands; layers 2-4 run kind::f8f6f4 with E4M3
 activations and per-layer power-of-two-scaled E4M3 weights.  The kernel is
-held to the oracle's operand-rounding emulation of exactly that path
-(relative L2 <= 1e-6: the two sides sum the same rounded products in
-different orders, so their FP32 values differ in the last bits; an E4M3
-rounding decision that such a difference flipped would move one operand
-by a 3-bit-mantissa ulp and show far above this bound).  Its distance to the
+held to the oracle's operand-rounding emulation of exactly that path, point
+by point: the two sides sum the same rounded products in different orders,
+so their FP32 values differ in the last bits, and where an activation lies
+within that distance of an E4M3 rounding midpoint the two may round it to
+neighbouring E4M3 values (one 3-bit-mantissa ulp, a visible change of that
+point).  The emulation reports each point's smallest relative distance to
+a midpoint; every point farther than 1e-5 from one must match the emulation
+to 1e-5 (relative to max(|c|, 1e-3 rms)), the few nearer ones are counted,
+and the whole sample stays within 2e-3 relative L2.  Its distance to the
 unrounded FP64 network is the cost of E4M3 itself (~0.12 relative L2 for
 the random-initialised decoder); it is printed and bounded loosely here so
 that a broken scale or bias, which costs O(1), still fails.
@@ -21,13 +25,35 @@ from paper_2406_17782_gb300.api import GBuffer
 
 pytestmark = pytest.mark.gpu
 
-TOL_EMU_E4M3 = 1e-6
+AMBIGUOUS = 1e-5      # rounding margin below which the two sides may round differently
+TOL_POINT = 1e-5      # per point, where no rounding is ambiguous
+TOL_ALL = 2e-3        # relative L2 over the whole sample
 LOOSE_FP64 = 0.25
 
 
 def rel_l2(got, want):
     got = np.asarray(got, np.float64)
     return float(np.sqrt(((got - want) ** 2).sum() / (want ** 2).sum()))
+
+
+def emulate(P, z, mats, g):
+    margins = []
+    c, r = M.shade_neural_e4m3(P, z, mats, g, margins=margins)
+    return c, r, margins[0]
+
+
+def check_against_emulation(what, c, r, emu_c, emu_rgb, margin):
+    """Per point where no E4M3 rounding is ambiguous, the whole sample in
+    relative L2; prints the counts."""
+    amb = margin < AMBIGUOUS
+    scale = np.maximum(np.abs(emu_c), 1e-3 * np.sqrt((emu_c ** 2).mean()))
+    err = (np.abs(np.asarray(c, np.float64) - emu_c) / scale).max(1)
+    worst = float(err[~amb].max()) if (~amb).any() else 0.0
+    e_c, e_rgb = rel_l2(c, emu_c), rel_l2(r, emu_rgb)
+    print(f"fp8 {what}: {amb.sum()} of {len(amb)} points with an ambiguous E4M3 rounding, "
+          f"{(err > TOL_POINT).sum()} beyond 1e-5; worst elsewhere {worst:.1e}; rel-L2 comps {e_c:.2e} rgb {e_rgb:.2e}")
+    assert worst <= TOL_POINT
+    assert e_c <= TOL_ALL and e_rgb <= TOL_ALL
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +79,7 @@ def test_e4m3_product_layout(fab, n, k):
     np.testing.assert_array_equal(d, a.astype(np.float64) @ b.astype(np.float64).T)
 
 
-def _check(fab, setup, g, prepared=False):
+def _check(fab, setup, g, what, prepared=False):
     mats, dec, z = setup
     gd = GBuffer.from_numpy(g)
     zt = torch.from_numpy(z).cuda()
@@ -64,27 +90,25 @@ def _check(fab, setup, g, prepared=False):
         rgb, comps = fab.shade_neural(gd, zt, "fp8", comps=True)
     fab.sync_status()
     P = M.unpack(dec, M.DEC_SHAPES)
-    emu_c, emu_rgb = M.shade_neural_e4m3(P, z, mats, g)
+    emu_c, emu_rgb, margin = emulate(P, z, mats, g)
     want_c, _ = M.shade_neural(P, z, mats, g)
     c, r = comps.cpu().numpy(), rgb.cpu().numpy()
     assert np.isfinite(c).all() and np.isfinite(r).all()
-    return rel_l2(c, emu_c), rel_l2(r, emu_rgb), rel_l2(c, want_c)
+    check_against_emulation(what, c, r, emu_c, emu_rgb, margin)
+    return rel_l2(c, want_c)
 
 
 def test_fp8_decoder_matches_e4m3_emulation(fab, setup):
     g = W.subset(W.frame_gbuffer(), W.sample_indices(1920 * 1080, 8192, stream="dec-fp8"))
-    e_c, e_rgb, e_64 = _check(fab, setup, g)
-    print(f"fp8 rel-L2 vs E4M3 emulation: comps {e_c:.2e} rgb {e_rgb:.2e}; vs FP64 network {e_64:.3f}")
-    assert e_c <= TOL_EMU_E4M3 and e_rgb <= TOL_EMU_E4M3
+    e_64 = _check(fab, setup, g, "sampled frame")
+    print(f"fp8 rel-L2 vs FP64 network {e_64:.3f}")
     assert e_64 <= LOOSE_FP64
 
 
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
 def test_fp8_ragged_tiles(fab, setup, n):
     g = W.subset(W.frame_gbuffer(), np.arange(9000, 9000 + n))
-    e_c, e_rgb, _ = _check(fab, setup, g)
-    print(f"fp8 ragged n={n}: rel-L2 vs E4M3 emulation comps {e_c:.2e} rgb {e_rgb:.2e}")
-    assert e_c <= TOL_EMU_E4M3 and e_rgb <= TOL_EMU_E4M3
+    _check(fab, setup, g, f"ragged n={n}")
 
 
 def test_fp8_full_frame_sampled(fab, setup):
@@ -98,10 +122,8 @@ def test_fp8_full_frame_sampled(fab, setup):
     fab.sync_status()
     idx = W.sample_indices(len(g["u"]), 8192, stream="dec-full-fp8")
     sub = W.subset(g, idx)
-    emu_c, emu_rgb = M.shade_neural_e4m3(M.unpack(dec, M.DEC_SHAPES), z, mats, sub)
-    print(f"fp8 full frame: rel-L2 vs E4M3 emulation comps {rel_l2(comps.cpu().numpy()[idx], emu_c):.2e}")
-    assert rel_l2(comps.cpu().numpy()[idx], emu_c) <= TOL_EMU_E4M3
-    assert rel_l2(rgb.cpu().numpy()[idx], emu_rgb) <= TOL_EMU_E4M3
+    emu_c, emu_rgb, margin = emulate(M.unpack(dec, M.DEC_SHAPES), z, mats, sub)
+    check_against_emulation("full frame", comps.cpu().numpy()[idx], rgb.cpu().numpy()[idx], emu_c, emu_rgb, margin)
     assert np.isfinite(rgb.cpu().numpy()).all()
 
 
@@ -119,10 +141,9 @@ def test_fp8_weight_scales_follow_the_layer_amax(fab, setup):
     dec2 = M.pack(P, M.DEC_SHAPES).astype(np.float32)
     fab.set_params(dec2, W.encoder_init())
     try:
-        _, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp8", comps=True)
+        rgb, comps = fab.shade_neural(GBuffer.from_numpy(g), torch.from_numpy(z).cuda(), "fp8", comps=True)
         fab.sync_status()
     finally:
         fab.set_params(dec, W.encoder_init())
-    emu_c, _ = M.shade_neural_e4m3(M.unpack(dec2.astype(np.float64), M.DEC_SHAPES), z, mats, g)
-    print(f"fp8 rescaled layers: rel-L2 vs E4M3 emulation {rel_l2(comps.cpu().numpy(), emu_c):.2e}")
-    assert rel_l2(comps.cpu().numpy(), emu_c) <= TOL_EMU_E4M3
+    emu_c, emu_rgb, margin = emulate(M.unpack(dec2.astype(np.float64), M.DEC_SHAPES), z, mats, g)
+    check_against_emulation("rescaled layers", comps.cpu().numpy(), rgb.cpu().numpy(), emu_c, emu_rgb, margin)

@@ -299,3 +299,16 @@ def test_recombine_eq8_hand_values(M):
                      [0.5, 1.0, 2.0],
                      [8.0, 16.0, 32.0]])
     np.testing.assert_array_equal(rgb, want)
+
+
+def test_e4m3_rounding_margin(M):
+    """The margin is the relative distance to the nearest E4M3 rounding
+    midpoint: zero exactly at a midpoint (1.0625 between 1 and 1.125; the
+    subnormal midpoint 2^-10 below 2^-9), half a spacing at a representable
+    value, and the rounding of values nudged across a midpoint flips."""
+    np.testing.assert_allclose(M.e4m3_rounding_margin(np.array([1.0625, 2.0 ** -10, -3.125])), 0.0, atol=1e-15)
+    np.testing.assert_allclose(M.e4m3_rounding_margin(np.array([1.0, 1.125, 416.0])),
+                               [0.0625, 0.0625 / 1.125, 16.0 / 416.0], rtol=1e-14)
+    mid = 1.0625
+    assert M.round_e4m3(mid * (1 - 1e-9)) == 1.0 and M.round_e4m3(mid * (1 + 1e-9)) == 1.125
+    assert np.isinf(M.e4m3_rounding_margin(np.array([0.0]))).all()
