@@ -383,6 +383,58 @@ fabric_status fabric_shade_neural_host(fabric_ctx *ctx, const fabric_gbuffer *g_
                                        float *rgb_host, float *comps_host, int64_t chunk_points, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* The paper's decoder structure                                      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The decoder of Sec. 4.2 ("Decoder", Fig. 3) beside the workload's: the
+ * footprint centre (frac u, frac v) and size one-blob encoded (3 inputs ->
+ * 24 channels, 8 Gaussian bins each of standard deviation 1/8; the centre's
+ * Gaussians wrap around the weave repeat; size t = ln(max(r, 2^-20) / 1e-4) /
+ * ln(2.5e4)), fused with a 64-wide material latent z by two fully connected
+ * layers of width W (the spatial feature h), then with wi (x, y, z) and
+ * wo (x, y) decoded by five fully connected layers with one skip:
+ *   k1 = lrelu(A1 [h | wi | wo.xy] + a1),
+ *   k3 = lrelu(A3 lrelu(A2 k1 + a2) + a3 + k1),
+ *   y  = A5 lrelu(A4 k3 + a4) + a5,
+ * leaky ReLU of slope 0.01, W = 64 or 128; y becomes the four components and
+ * RGB exactly as for fabric_shade_neural.  Flat FP32 parameters, weights
+ * [out][in]:
+ *   S1[W][88] s1[W] S2[W][W] s2[W] A1[W][W+5] a1[W] A2[W][W] a2[W]
+ *   A3[W][W] a3[W] A4[W][W] a4[W] A5[4][W] a5[4]
+ * (S1's inputs are [z (64) | one-blob (24)]); the encoder is the workload's
+ * with a 64-wide output: E1[128][22] e1 E2[128][128] e2 E3[64][128] e3.
+ * One paper network per context, separate from the workload's network.
+ */
+
+/* Parameter count of the paper decoder of width 64 or 128 (encoder != 0: of
+ * its encoder); -1 for another width. */
+int64_t fabric_paper_param_count(int width, int encoder);
+
+/* Copy host FP32 parameters in (either pointer NULL leaves that network
+ * unchanged; a width different from the current one needs both).  Resets
+ * the paper network's Adam state.  Synchronous. */
+fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *decoder, const float *encoder);
+
+/* Copy the paper network's parameters out (NULL skips).  Synchronous. */
+fabric_status fabric_paper_get_params(fabric_ctx *ctx, float *decoder, float *encoder);
+
+/* Fold latents_dev [n_mat][64] (n_mat = the material table's size, at most
+ * 104) into the first layer and pack the operands for FABRIC_PREC_FP16 or
+ * FABRIC_PREC_BF16 (one small kernel on `stream`). */
+fabric_status fabric_paper_prepare(fabric_ctx *ctx, const float *latents_dev, fabric_precision prec, void *stream);
+
+/* Shade a G-buffer with the last prepared paper network of `prec` (one
+ * persistent tensor-core launch); outputs, alignment and errors as for
+ * fabric_shade_neural_prepared. */
+fabric_status fabric_paper_shade_prepared(fabric_ctx *ctx, const fabric_gbuffer *g, fabric_precision prec,
+                                          float *rgb_dev, float *comps_dev, void *stream);
+
+/* fabric_paper_prepare followed by fabric_paper_shade_prepared. */
+fabric_status fabric_paper_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                        fabric_precision prec, float *rgb_dev, float *comps_dev, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Neural shading without any device allocation                       */
 /* ------------------------------------------------------------------ */
 

@@ -111,6 +111,14 @@ def load(path: str | None = None):
         "fabric_plan_shade": (st, [vp, vp, st, vp]),
         "fabric_plan_points": (i64, [vp]),
         "fabric_plan_destroy": (None, [vp]),
+        "fabric_paper_param_count": (i64, [i32, i32]),
+        "fabric_paper_set_params": (st, [vp, i32, vp, vp]),
+        "fabric_paper_get_params": (st, [vp, vp, vp]),
+        "fabric_paper_prepare": (st, [vp, vp, st, vp]),
+        "fabric_paper_shade_prepared": (st, [vp, P(FabricGBuffer), st, vp, vp, vp]),
+        "fabric_paper_shade_neural": (st, [vp, P(FabricGBuffer), vp, st, vp, vp, vp]),
+        "fabric_paper_encode_params": (st, [vp, vp, i32, vp, vp]),
+        "fabric_paper_train_step": (st, [vp, P(FabricTrainBatch), ctypes.c_float, vp, vp]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):

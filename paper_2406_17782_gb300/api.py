@@ -289,6 +289,71 @@ class Fabric:
                                                     _ptr(d), _stream_handle(None)))
         return d
 
+    # ------------------------------- the paper's decoder structure (Sec. 4.2)
+    def paper_set_params(self, width: int, decoder=None, encoder=None):
+        """Parameters of the paper's decoder (width 64 or 128) and its 64-wide
+        latent encoder; a new width needs both."""
+        nd = int(self.lib.fabric_paper_param_count(int(width), 0))
+        ne = int(self.lib.fabric_paper_param_count(int(width), 1))
+        d = None if decoder is None else np.ascontiguousarray(decoder, np.float32)
+        e = None if encoder is None else np.ascontiguousarray(encoder, np.float32)
+        if d is not None and d.size != nd:
+            raise ValueError(f"paper decoder of width {width} needs {nd} parameters")
+        if e is not None and e.size != ne:
+            raise ValueError(f"paper encoder needs {ne} parameters")
+        self._check(self.lib.fabric_paper_set_params(self.h, int(width),
+                                                     None if d is None else d.ctypes.data_as(ctypes.c_void_p),
+                                                     None if e is None else e.ctypes.data_as(ctypes.c_void_p)))
+        self.paper_width = int(width)
+
+    def paper_get_params(self):
+        nd = int(self.lib.fabric_paper_param_count(self.paper_width, 0))
+        ne = int(self.lib.fabric_paper_param_count(self.paper_width, 1))
+        d = np.empty(nd, np.float32)
+        e = np.empty(ne, np.float32)
+        self._check(self.lib.fabric_paper_get_params(self.h, d.ctypes.data_as(ctypes.c_void_p),
+                                                     e.ctypes.data_as(ctypes.c_void_p)))
+        return d, e
+
+    def paper_encode_params(self, materials, stream=None) -> torch.Tensor:
+        arr = material_array(materials)
+        z = torch.empty((len(arr), 64), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fabric_paper_encode_params(self.h, arr, len(arr), _ptr(z), _stream_handle(stream)))
+        return z
+
+    def paper_prepare(self, latents: torch.Tensor, precision: str = "fp16", stream=None):
+        self._paper_latents = latents.contiguous()
+        self._check(self.lib.fabric_paper_prepare(self.h, _ptr(self._paper_latents), _abi.PREC[precision],
+                                                  _stream_handle(stream)))
+
+    def paper_shade_prepared(self, g: GBuffer, precision: str = "fp16", comps: bool = False, out_rgb=None,
+                             out_comps=None, stream=None):
+        rgb = out_rgb if out_rgb is not None else torch.empty((g.n, 3), dtype=torch.float32, device=self.device)
+        cp = out_comps if out_comps is not None else (
+            torch.empty((g.n, 4), dtype=torch.float32, device=self.device) if comps else None)
+        gs = g.struct()
+        self._check(self.lib.fabric_paper_shade_prepared(self.h, ctypes.byref(gs), _abi.PREC[precision], _ptr(rgb),
+                                                         _ptr(cp), _stream_handle(stream)))
+        return rgb, cp
+
+    def paper_shade_neural(self, g: GBuffer, latents: torch.Tensor, precision: str = "fp16", comps: bool = False,
+                           out_rgb=None, out_comps=None, stream=None):
+        rgb = out_rgb if out_rgb is not None else torch.empty((g.n, 3), dtype=torch.float32, device=self.device)
+        cp = out_comps if out_comps is not None else (
+            torch.empty((g.n, 4), dtype=torch.float32, device=self.device) if comps else None)
+        lat = latents.contiguous()
+        gs = g.struct()
+        self._check(self.lib.fabric_paper_shade_neural(self.h, ctypes.byref(gs), _ptr(lat), _abi.PREC[precision],
+                                                       _ptr(rgb), _ptr(cp), _stream_handle(stream)))
+        return rgb, cp
+
+    def paper_train_step(self, batch: GBuffer, target: torch.Tensor, lr: float, loss_out=None, stream=None):
+        loss = loss_out if loss_out is not None else torch.empty((), dtype=torch.float64, device=self.device)
+        tb = FabricTrainBatch(batch.struct(), target.contiguous().data_ptr())
+        self._check(self.lib.fabric_paper_train_step(self.h, ctypes.byref(tb), ctypes.c_float(lr), _ptr(loss),
+                                                     _stream_handle(stream)))
+        return loss
+
     # ---------------------------------------------- autograd building blocks
     def decoder_forward(self, g: GBuffer, latents, dec, stream=None):
         y = torch.empty((g.n, 4), dtype=torch.float32, device=self.device)

@@ -290,6 +290,7 @@ void fabric_destroy(fabric_ctx *ctx) {
   cudaFree(ctx->d_blob);
   cudaFree(ctx->d_err_work);
   host_pipeline_release(ctx);
+  paper_release(ctx);
   delete ctx;
 }
 

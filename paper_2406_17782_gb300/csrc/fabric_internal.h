@@ -185,6 +185,18 @@ struct fabric_ctx {
   cudaEvent_t host_start = nullptr;
   void *host_stage = nullptr;   // kHostSlots x host_slot_bytes
   size_t host_slot_bytes = 0;
+  // the paper's decoder structure (fabric_paper_*): width, FP32 master
+  // parameters, Adam moments over [decoder | encoder], packed operands and
+  // the state of the last fabric_paper_prepare
+  int pn_width = 0;
+  float *d_pn_dec = nullptr;
+  float *d_pn_enc = nullptr;
+  float *d_pn_adam = nullptr;
+  int64_t pn_adam_step = 0;
+  void *d_pn_blob = nullptr;
+  uint64_t pn_version = 1;          // bumped when the paper network's parameters change
+  int pn_prepared_prec = -1;
+  uint64_t pn_prepared_version = 0;  // (ctx->version, pn_version) folded at prepare time
 };
 
 namespace fab {
@@ -198,6 +210,8 @@ bool check_gbuffer(fabric_ctx *ctx, const fabric_gbuffer *g);
 bool is_aligned16(const void *p);
 // Free the host-pipeline streams, events and staging of a context.
 void host_pipeline_release(fabric_ctx *ctx);
+// Free the paper network's parameters and buffers of a context.
+void paper_release(fabric_ctx *ctx);
 
 // Launchers implemented in the kernel translation units.
 cudaError_t launch_reference(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, int spp_x, int spp_y,
@@ -256,6 +270,15 @@ cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n
                             float *dlat_rows, int sm_count, int *status, cudaStream_t s);
 cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const float *grad, float *m, float *v, float lr,
                         int64_t step, cudaStream_t s);
+// The paper's decoder structure (paper_decoder.cu): K of its first layer for
+// n_mat materials (-1 beyond 104), packed-operand bytes, packing and the
+// tensor-core decoder (FP16 or BF16 operands), width 64 or 128.
+int paper_k1(int n_mat);
+size_t paper_blob_bytes(int width, int n_mat);
+cudaError_t launch_paper_pack(int width, int precision, const float *params, const float *latents,
+                              const DevMaterial *mats, int n_mat, void *blob, cudaStream_t s);
+cudaError_t launch_paper_decoder(int width, int precision, const fabric_gbuffer &g, const void *blob, int n_mat,
+                                 float *rgb, float *comps, int *status, int sm_count, cudaStream_t s);
 cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
                                double *out, void *work, cudaStream_t s);
 size_t error_stats_work_bytes(int64_t n);

@@ -1,0 +1,56 @@
+// paper_net.h -- parameter layout of the paper's decoder structure (Sec. 4.2,
+// "Decoder"; Fig. 3): a spatial fusion of the material latent with the
+// one-blob-encoded footprint (two layers), then an angular decoder of five
+// layers with one skip, leaky ReLU; width W = 64 or 128.
+//
+// Flat FP32 parameters, weights [out][in]:
+//   S1[W][88] s1[W] S2[W][W] s2[W] A1[W][W+5] a1[W] A2[W][W] a2[W]
+//   A3[W][W] a3[W] A4[W][W] a4[W] A5[4][W] a5[4]
+// S1's inputs are [z (64) | one-blob (24)], A1's are [h (W) | wi (3) | wo.xy (2)].
+// Encoder: the workload's parameter encoder with a 64-wide latent,
+//   E1[128][22] e1[128] E2[128][128] e2[128] E3[64][128] e3[64].
+#pragma once
+
+#include <cstdint>
+
+namespace fab {
+
+constexpr int kPnLatent = 64;
+constexpr int kPnBins = 8;
+constexpr int kPnBlob = 3 * kPnBins;   // one-blob channels of (frac u, frac v, size)
+constexpr int kPnAng = 5;              // wi (x, y, z), wo (x, y)
+constexpr float kPnSlope = 0.01f;      // leaky ReLU
+// size coordinate t = ln(max(r, 2^-20) / 1e-4) / ln(2.5 / 1e-4)
+constexpr float kPnLnRLo = -9.210340371976182f;     // ln 1e-4
+constexpr float kPnInvLnSpan = 0.09874952387865506f; // 1 / ln(2.5e4)
+
+struct PaperOffsets {
+  int S1, s1, S2, s2, A1, a1, A2, a2, A3, a3, A4, a4, A5, a5, total;
+};
+
+__host__ __device__ constexpr PaperOffsets paper_offsets(int w) {
+  PaperOffsets o{};
+  o.S1 = 0;
+  o.s1 = o.S1 + w * (kPnLatent + kPnBlob);
+  o.S2 = o.s1 + w;
+  o.s2 = o.S2 + w * w;
+  o.A1 = o.s2 + w;
+  o.a1 = o.A1 + w * (w + kPnAng);
+  o.A2 = o.a1 + w;
+  o.a2 = o.A2 + w * w;
+  o.A3 = o.a2 + w;
+  o.a3 = o.A3 + w * w;
+  o.A4 = o.a3 + w;
+  o.a4 = o.A4 + w * w;
+  o.A5 = o.a4 + w;
+  o.a5 = o.A5 + 4 * w;
+  o.total = o.a5 + 4;
+  return o;
+}
+
+// Encoder with a 64-wide latent (same layout as the workload's encoder).
+constexpr int kPnEncParams = 128 * 22 + 128 + 128 * 128 + 128 + kPnLatent * 128 + kPnLatent;
+
+constexpr bool paper_width_ok(int w) { return w == 64 || w == 128; }
+
+}  // namespace fab

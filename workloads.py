@@ -407,6 +407,26 @@ def encoder_init(seed: int = 4, weight_bound: str = "he") -> np.ndarray:
                        [(o * i, o) for o, i in ENC_LAYERS], seed, weight_bound)
 
 
-def random_latents(n_mat: int, seed: int = 5, scale: float = 1.0) -> np.ndarray:
+def random_latents(n_mat: int, seed: int = 5, scale: float = 1.0, dim: int = 32) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE, seed])))
-    return (scale * rng.standard_normal((n_mat, 32))).astype(np.float32)
+    return (scale * rng.standard_normal((n_mat, dim))).astype(np.float32)
+
+
+def paper_decoder_layers(width: int):
+    """(out, in) of the paper decoder's seven layers: S1, S2, A1..A5."""
+    return [(width, 64 + 24), (width, width), (width, width + 5), (width, width), (width, width),
+            (width, width), (4, width)]
+
+
+PAPER_ENC_LAYERS = [(128, 22), (128, 128), (64, 128)]
+
+
+def paper_decoder_init(width: int, seed: int = 13, weight_bound: str = "he") -> np.ndarray:
+    layers = paper_decoder_layers(width)
+    return init_params(sum(o * i + o for o, i in layers), [i for _, i in layers], [(o * i, o) for o, i in layers],
+                       seed, weight_bound)
+
+
+def paper_encoder_init(seed: int = 14, weight_bound: str = "he") -> np.ndarray:
+    return init_params(sum(o * i + o for o, i in PAPER_ENC_LAYERS), [i for _, i in PAPER_ENC_LAYERS],
+                       [(o * i, o) for o, i in PAPER_ENC_LAYERS], seed, weight_bound)
