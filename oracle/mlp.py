@@ -361,22 +361,31 @@ def e4m3_scale_exponent(w) -> int:
     return 8 - int(e)
 
 
+def rounding_midpoint_distance(x, mant_bits: int, emin: int) -> np.ndarray:
+    """Absolute distance of each value to the nearest rounding boundary (the
+    midpoint between two neighbouring representable values) of a binary
+    format with `mant_bits` stored mantissa bits and smallest normal
+    exponent `emin` (subnormals below 2^emin)."""
+    a = np.abs(np.asarray(x, np.float64))
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** emin)))
+    q = 2.0 ** (e - mant_bits)
+    t = a / q
+    return np.abs(t - (np.floor(t) + 0.5)) * q
+
+
 def e4m3_rounding_margin(x) -> np.ndarray:
     """Relative distance of each value to the nearest E4M3 rounding
     boundary (the midpoint between two neighbouring E4M3 values): where it
     is tiny, two evaluations whose FP32 sums differ in their last bits can
     round the value to different E4M3 neighbours.  inf at exact zeros."""
     a = np.abs(np.asarray(x, np.float64))
-    e = np.floor(np.log2(np.maximum(a, 2.0 ** -6)))
-    q = 2.0 ** (e - 3)
-    t = a / q
-    d = np.abs(t - (np.floor(t) + 0.5)) * q
+    d = rounding_midpoint_distance(a, 3, -6)
     with np.errstate(divide="ignore"):
         return np.where(a > 0, d / a, np.inf)
 
 
 def shade_neural_e4m3(dec: dict, z: np.ndarray, materials, gbuf: dict,
-                      r16=round_fp16, r8=round_e4m3, margins: list | None = None):
+                      r16=round_fp16, r8=round_e4m3, diag: dict | None = None):
     """Operand-rounding emulation of the E4M3 tensor-core decoder.
 
     Layer 1 keeps 16-bit operands (r16): its weight block carries the latent
@@ -388,26 +397,30 @@ def shade_neural_e4m3(dec: dict, z: np.ndarray, materials, gbuf: dict,
     value is rounded to FP32 before it is rounded to an operand type, as in
     the kernel.  With r16 = r8 = identity this is the FP64 network up to
     those FP32 roundings.  Returns (components [n, 4], rgb [n, 3]); when
-    `margins` is a list, the per-point minimum of e4m3_rounding_margin over
-    the activations rounded to E4M3 is appended to it."""
+    `diag` is a dict, the values that the path rounds are stored in it (to
+    find where another evaluation whose features or sums differ in their
+    last bits may round differently): "features" (FP32 query features
+    [n, 39], before FP16 rounding), "w1" (the rounded layer-1 feature
+    weights [64, 39]), "fold" (the FP32 folded bias columns [n_mat, 64],
+    before FP16 rounding) and "pre" (per E4M3 layer, the ReLU'd FP32 values
+    before E4M3 rounding, [n, 64] each)."""
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
-    q = r16(f32(query_features(gbuf["u"], gbuf["v"], gbuf["radius"], gbuf["wi"], gbuf["wo"])))
+    q32 = f32(query_features(gbuf["u"], gbuf["v"], gbuf["radius"], gbuf["wi"], gbuf["wo"]))
+    q = r16(q32)
     mat = np.asarray(gbuf["material"], np.int64)
     zf = np.asarray(z, np.float64)
     fold = dec["b1"][None, :] + zf @ dec["W1"][:, :LATENT].T            # [n_mat, 64]
-    a = q @ r16(f32(dec["W1"][:, LATENT:])).T + r16(f32(fold))[mat]
-    margin = np.full(len(mat), np.inf)
-    pre = np.maximum(f32(a), 0.0)
-    margin = np.minimum(margin, e4m3_rounding_margin(pre).min(1))
-    h = r8(pre)
+    w1 = r16(f32(dec["W1"][:, LATENT:]))
+    a = q @ w1.T + r16(f32(fold))[mat]
+    pres = [np.maximum(f32(a), 0.0)]
+    h = r8(pres[0])
     for wn, bn, last in (("W2", "b2", False), ("W3", "b3", False), ("W4", "b4", True)):
         s = 2.0 ** e4m3_scale_exponent(dec[wn])
         a = f32(f32(h @ r8(f32(dec[wn]) * s).T) / s + f32(dec[bn]))
         if not last:
-            pre = np.maximum(a, 0.0)
-            margin = np.minimum(margin, e4m3_rounding_margin(pre).min(1))
-        h = a if last else r8(pre)
-    if margins is not None:
-        margins.append(margin)
+            pres.append(np.maximum(a, 0.0))
+        h = a if last else r8(pres[-1])
+    if diag is not None:
+        diag.update(features=q32, w1=w1, fold=f32(fold), pre=pres)
     comps = head_to_components(h)
     return comps, recombine(comps, materials, gbuf["material"])

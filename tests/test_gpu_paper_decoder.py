@@ -6,7 +6,8 @@ Against the oracle's operand-rounding emulation of the same path (16-bit
 one-blob channels, angular inputs, weights, biases and activations; the
 latent folded into a rounded per-material bias; the skip adding the rounded
 k1; FP32 accumulation): relative L2 <= 5e-4.  Against the unrounded FP64
-network: FP16 <= 5e-3, BF16 <= 3e-2 (BF16 operand rounding alone; printed).
+network: FP16 <= 5e-3, BF16 <= 1.5e-2 (BF16 operand rounding alone: 3e-3 at width
+64, 7e-3 at 128).
 Widths 64 and 128."""
 import numpy as np
 import pytest
@@ -21,7 +22,7 @@ from paper_2406_17782_gb300.api import GBuffer
 pytestmark = pytest.mark.gpu
 
 TOL_EMU = 5e-4
-TOL_FP64 = {"fp16": 5e-3, "bf16": 3e-2}
+TOL_FP64 = {"fp16": 5e-3, "bf16": 1.5e-2}
 ROUND = {"fp16": M.round_fp16, "bf16": M.round_bf16}
 
 

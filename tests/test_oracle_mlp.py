@@ -312,3 +312,9 @@ def test_e4m3_rounding_margin(M):
     mid = 1.0625
     assert M.round_e4m3(mid * (1 - 1e-9)) == 1.0 and M.round_e4m3(mid * (1 + 1e-9)) == 1.125
     assert np.isinf(M.e4m3_rounding_margin(np.array([0.0]))).all()
+    # FP16 (10 mantissa bits, normals from 2^-14): 1 + 2^-11 is the midpoint
+    # between 1 and 1 + 2^-10; 0.75 is representable, half a spacing from both
+    # midpoints around it
+    np.testing.assert_allclose(M.rounding_midpoint_distance(np.array([1 + 2.0 ** -11, 0.75]), 10, -14),
+                               [0.0, 2.0 ** -12], atol=0)
+    assert np.float16(1 + 2.0 ** -11 * (1 - 1e-6)) == 1.0 and np.float16(1 + 2.0 ** -11 * (1 + 1e-6)) > 1.0
