@@ -434,6 +434,27 @@ fabric_status fabric_paper_shade_prepared(fabric_ctx *ctx, const fabric_gbuffer 
 fabric_status fabric_paper_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
                                         fabric_precision prec, float *rgb_dev, float *comps_dev, void *stream);
 
+/* The paper network's encoder (Sec. 4.2, "Encoder"; residual block):
+ * n_mat host records -> latents_dev [n_mat][64] FP32, features as for
+ * fabric_encode_params. */
+fabric_status fabric_paper_encode_params(fabric_ctx *ctx, const fabric_material *m, int n_mat, float *latents_dev,
+                                         void *stream);
+
+/* One training step of the paper network (Sec. 4.3, Sec. 5.2), as
+ * fabric_train_step does for the workload's network: its encoder over the
+ * training material table, the decoder over the batch in FP32, the loss set
+ * by fabric_set_train_loss, the backward pass (fixed-order reductions:
+ * bitwise repeatable), one Adam update of the paper network's parameters.
+ * *loss_dev (device double, or NULL) receives the batch loss before the
+ * update.  Batch size 1..1048576. */
+fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr, double *loss_dev,
+                                      void *stream);
+
+/* Copy the gradient [decoder | encoder] of the last fabric_paper_train_step
+ * to host memory (fabric_paper_param_count(width, 0) + (.., 1) floats).
+ * Synchronous.  Used by the tests. */
+fabric_status fabric_paper_get_gradient(fabric_ctx *ctx, float *grad);
+
 /* ------------------------------------------------------------------ */
 /* Neural shading without any device allocation                       */
 /* ------------------------------------------------------------------ */

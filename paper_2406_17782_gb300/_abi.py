@@ -119,6 +119,7 @@ def load(path: str | None = None):
         "fabric_paper_shade_neural": (st, [vp, P(FabricGBuffer), vp, st, vp, vp, vp]),
         "fabric_paper_encode_params": (st, [vp, vp, i32, vp, vp]),
         "fabric_paper_train_step": (st, [vp, P(FabricTrainBatch), ctypes.c_float, vp, vp]),
+        "fabric_paper_get_gradient": (st, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):

@@ -354,6 +354,14 @@ class Fabric:
                                                      _stream_handle(stream)))
         return loss
 
+    def paper_gradient(self) -> np.ndarray:
+        """The last paper-network training step's gradient [decoder | encoder]."""
+        n = int(self.lib.fabric_paper_param_count(self.paper_width, 0)) + int(
+            self.lib.fabric_paper_param_count(self.paper_width, 1))
+        out = np.empty(n, np.float32)
+        self._check(self.lib.fabric_paper_get_gradient(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
     # ---------------------------------------------- autograd building blocks
     def decoder_forward(self, g: GBuffer, latents, dec, stream=None):
         y = torch.empty((g.n, 4), dtype=torch.float32, device=self.device)

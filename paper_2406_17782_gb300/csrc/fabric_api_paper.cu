@@ -12,7 +12,8 @@ void paper_release(fabric_ctx *ctx) {
   cudaFree(ctx->d_pn_enc);
   cudaFree(ctx->d_pn_adam);
   cudaFree(ctx->d_pn_blob);
-  ctx->d_pn_dec = ctx->d_pn_enc = ctx->d_pn_adam = nullptr;
+  cudaFree(ctx->d_pn_grad);
+  ctx->d_pn_dec = ctx->d_pn_enc = ctx->d_pn_adam = ctx->d_pn_grad = nullptr;
   ctx->d_pn_blob = nullptr;
   ctx->pn_width = 0;
 }
@@ -64,6 +65,7 @@ fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *d
     if (cudaMalloc(&ctx->d_pn_dec, nd * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&ctx->d_pn_enc, ne * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&ctx->d_pn_adam, 2 * (nd + ne) * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_pn_grad, (nd + ne) * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&ctx->d_pn_blob, paper_blob_bytes(width, kPnMaxMaterials)) != cudaSuccess) {
       paper_release(ctx);
       cudaGetLastError();
@@ -75,6 +77,7 @@ fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *d
   if (decoder) PN_CUDA(ctx, cudaMemcpy(ctx->d_pn_dec, decoder, nd * sizeof(float), cudaMemcpyHostToDevice), "params");
   if (encoder) PN_CUDA(ctx, cudaMemcpy(ctx->d_pn_enc, encoder, ne * sizeof(float), cudaMemcpyHostToDevice), "params");
   PN_CUDA(ctx, cudaMemset(ctx->d_pn_adam, 0, 2 * (nd + ne) * sizeof(float)), "adam reset");
+  PN_CUDA(ctx, cudaMemset(ctx->d_pn_grad, 0, (nd + ne) * sizeof(float)), "gradient reset");
   ctx->pn_adam_step = 0;
   ctx->pn_version += 1;
   PN_CUDA(ctx, cudaDeviceSynchronize(), "set params");
@@ -136,6 +139,75 @@ fabric_status fabric_paper_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g
   const fabric_status st = fabric_paper_prepare(ctx, latents_dev, prec, stream);
   if (st != FABRIC_OK) return st;
   return fabric_paper_shade_prepared(ctx, g, prec, rgb_dev, comps_dev, stream);
+}
+
+fabric_status fabric_paper_encode_params(fabric_ctx *ctx, const fabric_material *m, int n_mat, float *latents_dev,
+                                         void *stream) {
+  PN_CHECK_CTX(ctx);
+  if (!ctx->pn_width) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network parameters set");
+  if (n_mat == 0) return FABRIC_OK;
+  if (!m || !latents_dev || n_mat < 0 || n_mat > 65535)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "need materials, a latent buffer and 0..65535 records");
+  for (int k = 0; k < n_mat; ++k) {
+    DevMaterial tmp;
+    std::string why;
+    if (!build_material(m[k], &tmp, &why)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "material %d: %s", k, why.c_str());
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ctx->enc_raw_cap < n_mat) {
+    PN_CUDA(ctx, cudaStreamSynchronize(s), "encode staging");
+    cudaFree(ctx->d_enc_raw);
+    ctx->d_enc_raw = nullptr;
+    ctx->enc_raw_cap = 0;
+    PN_CUDA(ctx, cudaMalloc(&ctx->d_enc_raw, n_mat * sizeof(fabric_material)), "encode staging");
+    ctx->enc_raw_cap = n_mat;
+  }
+  PN_CUDA(ctx, cudaMemcpyAsync(ctx->d_enc_raw, m, n_mat * sizeof(fabric_material), cudaMemcpyHostToDevice, s),
+          "encode upload");
+  PN_CUDA(ctx, launch_paper_encoder(ctx->d_enc_raw, n_mat, ctx->d_pn_enc, latents_dev, s), "paper encoder");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr, double *loss_dev,
+                                      void *stream) {
+  PN_CHECK_CTX(ctx);
+  if (!ctx->pn_width) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network parameters set");
+  if (!batch) return fail(ctx, FABRIC_ERR_INVALID_ARG, "batch is NULL");
+  const fabric_gbuffer &q = batch->queries;
+  if (!check_gbuffer(ctx, &q)) return FABRIC_ERR_INVALID_ARG;
+  if (q.n < 1 || q.n > (1 << 20)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "batch size must be 1..1048576");
+  if (!batch->target) return fail(ctx, FABRIC_ERR_INVALID_ARG, "targets are NULL");
+  if (!(lr >= 0.0f)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "learning rate must be >= 0");
+  if (ctx->n_train_mat < 1) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no training materials set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int M = ctx->n_train_mat;
+  const size_t need = paper_train_work_bytes(ctx->pn_width, q.n, M) + 256;
+  void *work = scratch(ctx, need);
+  if (!work) return fail(ctx, FABRIC_ERR_OOM, "training scratch (%zu bytes)", need);
+  double *loss = loss_dev ? loss_dev
+                          : reinterpret_cast<double *>(static_cast<uint8_t *>(work) + need - 256);
+  PN_CUDA(ctx,
+          launch_paper_train(ctx->pn_width, q, batch->target, ctx->loss_mode, ctx->d_train_raw, M, ctx->d_pn_dec,
+                             ctx->d_pn_enc, ctx->d_pn_grad, loss, work, ctx->d_status, s),
+          "paper network forward/backward");
+  ctx->pn_adam_step += 1;
+  ctx->pn_version += 1;
+  const size_t nd = (size_t)paper_offsets(ctx->pn_width).total, ne = (size_t)kPnEncParams;
+  float *m = ctx->d_pn_adam, *v = ctx->d_pn_adam + nd + ne;
+  PN_CUDA(ctx,
+          launch_adam(ctx->d_pn_dec, (int64_t)nd, ctx->d_pn_enc, (int64_t)ne, ctx->d_pn_grad, m, v, lr,
+                      ctx->pn_adam_step, s),
+          "adam");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_paper_get_gradient(fabric_ctx *ctx, float *grad) {
+  PN_CHECK_CTX(ctx);
+  if (!ctx->pn_width || !grad) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network, or grad is NULL");
+  PN_CUDA(ctx, cudaDeviceSynchronize(), "get gradient");
+  const size_t n = (size_t)paper_offsets(ctx->pn_width).total + kPnEncParams;
+  PN_CUDA(ctx, cudaMemcpy(grad, ctx->d_pn_grad, n * sizeof(float), cudaMemcpyDeviceToHost), "gradient");
+  return FABRIC_OK;
 }
 
 }  // extern "C"

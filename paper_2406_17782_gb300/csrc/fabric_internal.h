@@ -192,6 +192,7 @@ struct fabric_ctx {
   float *d_pn_dec = nullptr;
   float *d_pn_enc = nullptr;
   float *d_pn_adam = nullptr;
+  float *d_pn_grad = nullptr;       // the last training step's gradient [decoder | encoder]
   int64_t pn_adam_step = 0;
   void *d_pn_blob = nullptr;
   uint64_t pn_version = 1;          // bumped when the paper network's parameters change
@@ -279,6 +280,13 @@ cudaError_t launch_paper_pack(int width, int precision, const float *params, con
                               const DevMaterial *mats, int n_mat, void *blob, cudaStream_t s);
 cudaError_t launch_paper_decoder(int width, int precision, const fabric_gbuffer &g, const void *blob, int n_mat,
                                  float *rgb, float *comps, int *status, int sm_count, cudaStream_t s);
+// Its FP32 training forward, loss and backward (paper_train.cu): the
+// gradient [decoder | encoder] and the batch loss; and its encoder alone.
+size_t paper_train_work_bytes(int width, int64_t batch, int n_mat);
+cudaError_t launch_paper_train(int width, const fabric_gbuffer &q, const float *target, int loss_mode,
+                               const fabric_material *raw, int n_mat, const float *dec, const float *enc, float *grad,
+                               double *loss, void *work, int *status, cudaStream_t s);
+cudaError_t launch_paper_encoder(const fabric_material *raw, int n_mat, const float *enc, float *z, cudaStream_t s);
 cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
                                double *out, void *work, cudaStream_t s);
 size_t error_stats_work_bytes(int64_t n);

@@ -1,0 +1,90 @@
+"""Training of the paper's decoder structure (fabric_paper_train_step)
+against the FP64 oracle: the encoder's latents, the loss and the full
+gradient [decoder | encoder] of one step (read back after a step with
+lr = 0), at both widths and both losses; repeatability and learning."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import mlp as M
+from oracle import paper_net as PN
+from paper_2406_17782_gb300.api import GBuffer
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def oracle_step(w, mats, g, target, dec, enc, loss_mode):
+    P = M.unpack(dec.astype(np.float64), PN.dec_shapes(w))
+    E = M.unpack(enc.astype(np.float64), PN.ENC_SHAPES)
+    z, ec = M.encoder_forward(E, M.encoder_features(mats), keep=True)
+    mat = np.asarray(g["material"], np.int64)
+    y, dc = PN.decoder_forward(P, z[mat], PN.spatial_features(g["u"], g["v"], g["radius"]),
+                               PN.angular_features(g["wi"], g["wo"]), keep=True)
+    loss, dy = M.loss_and_grad(y, target.astype(np.float64), loss_mode, np.asarray(g["wi"], np.float64)[:, 2])
+    gd, dzr, _ = PN.decoder_backward(P, dc, dy)
+    dz = np.zeros_like(z)
+    np.add.at(dz, mat, dzr)
+    ge = M.encoder_backward(E, ec, dz)
+    return loss, np.concatenate([M.pack(gd, PN.dec_shapes(w)), M.pack(ge, PN.ENC_SHAPES)])
+
+
+@pytest.mark.parametrize("w", [64, 128])
+def test_paper_encoder_matches_oracle(fab, w):
+    mats = W.training_materials(4)
+    enc = W.paper_encoder_init()
+    fab.paper_set_params(w, W.paper_decoder_init(w), enc)
+    z = fab.paper_encode_params(mats).cpu().numpy()
+    want = M.encoder_forward(M.unpack(enc, PN.ENC_SHAPES), M.encoder_features(mats))
+    np.testing.assert_allclose(z, want, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("loss_mode", ["eq11", "rendered"])
+@pytest.mark.parametrize("w,n", [(64, 4096), (128, 4096), (64, 1000)])
+def test_paper_gradient_matches_oracle(fab, w, n, loss_mode):
+    mats = W.training_materials(2)
+    g = W.training_queries(n, len(mats), stream=f"paper-grad-{n}")
+    target = np.abs(np.random.default_rng(18).standard_normal((n, 4)) * 0.2).astype(np.float32)
+    dec, enc = W.paper_decoder_init(w, weight_bound="small"), W.paper_encoder_init(weight_bound="small")
+    want_loss, want = oracle_step(w, mats, g, target, dec, enc, loss_mode)
+    fab.paper_set_params(w, dec, enc)
+    fab.set_train_materials(mats)
+    fab.set_train_loss(loss_mode)
+    try:
+        loss = float(fab.paper_train_step(GBuffer.from_numpy(g), torch.from_numpy(target).cuda(), 0.0).item())
+        fab.sync_status()
+        got = fab.paper_gradient()
+    finally:
+        fab.set_train_loss("eq11")
+    nd = M.n_params(PN.dec_shapes(w))
+    print(f"paper W={w} {loss_mode} n={n}: loss {loss:.7g} vs {want_loss:.7g}; grad rel-L2 decoder "
+          f"{rel_l2(got[:nd], want[:nd]):.2e}, encoder {rel_l2(got[nd:], want[nd:]):.2e}")
+    assert abs(loss - want_loss) <= 1e-5 * abs(want_loss)
+    assert rel_l2(got[:nd], want[:nd]) <= 1e-4 and rel_l2(got[nd:], want[nd:]) <= 1e-4
+    # the one step with lr = 0 left the parameters unchanged
+    d, e = fab.paper_get_params()
+    assert np.array_equal(d, dec) and np.array_equal(e, enc)
+
+
+def test_paper_training_is_repeatable_and_learns(fab):
+    w = 64
+    mats = W.training_materials(2)
+    g = W.training_queries(8192, len(mats), stream="paper-learn")
+    target = np.abs(np.random.default_rng(19).standard_normal((8192, 4)) * 0.2).astype(np.float32)
+    gd, tt = GBuffer.from_numpy(g), torch.from_numpy(target).cuda()
+    fab.set_train_materials(mats)
+    runs = []
+    for _ in range(2):
+        fab.paper_set_params(w, W.paper_decoder_init(w, weight_bound="small"),
+                             W.paper_encoder_init(weight_bound="small"))
+        losses = [float(fab.paper_train_step(gd, tt, 3e-3).item()) for _ in range(100)]
+        fab.sync_status()
+        runs.append((losses, fab.paper_get_params()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1][0], runs[1][1][0]) and np.array_equal(runs[0][1][1], runs[1][1][1])
+    assert runs[0][0][-1] < 0.5 * runs[0][0][0]
