@@ -19,11 +19,19 @@ Also measured in the same run and reported on the JSON line:
     weights), and on the FP32 SIMT path;
   * the FP64-accurate error reduction (a frame pair, and arrays larger than
     L2), timed through CUDA-graph replays;
-  * the quality ladder (--no-quality skips it): the network trained with the
-    library's kernels, then the RMSE of the neural frame and of the
-    reference at 1-256 spp with their times, on the 1080p frame and on the
-    multi-scale frame (Table 2 footprints); latent interpolation and the
-    editing latency;
+  * the paper's own decoder structure (one-blob encoding, spatial fusion,
+    angular decoder with a skip) at widths 64 and 128: ms per frame,
+    fraction of the tensor peak, and its FP32 training step;
+  * the host link's copy rate (1 GiB each way) beside the end-to-end figure,
+    and the paper's data generation (about 3.2 M queries per material at
+    2048 spp) per material;
+  * the quality ladder (--no-quality skips it): the networks trained with
+    the library's kernels (the workload's with Eq. 11 and with the
+    rendered-space loss, the paper's structure with the latter), then the
+    error of the neural frame and of the reference at 1-256 spp with their
+    times, on the 1080p frame and on the multi-scale frame (Table 2
+    footprints), on the linear f_P (the headline target), tone-mapped and
+    lit; latent interpolation and the editing latency;
   * SM clocks during the timed region, and the FP64 oracle on the host cores.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-extras | --no-quality]
@@ -221,6 +229,9 @@ def main():
                     help="training forward/backward: FP32 SIMT or BF16 tensor-core kernels")
     ap.add_argument("--quality-lr", type=float, default=3e-3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--paper-steps", type=int, default=20000,
+                    help="training steps of the paper's decoder structure in the quality section")
+    ap.add_argument("--paper-width", type=int, default=128, choices=[64, 128])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -504,9 +515,42 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
             },
             "train_seconds": t_train,
         }
+    # the paper's decoder structure (Sec. 4.2), trained on the same data with
+    # the rendered-space loss, on both frames
+    pw = args.paper_width
+    fab.paper_set_params(pw, W.paper_decoder_init(pw, weight_bound="small"),
+                         W.paper_encoder_init(weight_bound="small"))
+    fab.set_train_loss("rendered")
+    t0 = time.time()
+    T.train(fab, tm, g_tr, target, args.paper_steps, 65536, args.quality_lr, log_every=1000, verbose=False,
+            paper=True)
+    torch.cuda.synchronize()
+    t_paper = time.time() - t0
+    fab.set_train_loss("eq11")
+    rp = T.frame_rmse(fab, "fp16", gt_spp=(32, 32), ref_spps=(), paper=True)
+    rp_ms = T.frame_rmse(fab, "fp16", gt_spp=(64, 64), ref_spps=(), gbuf=ms_host, paper=True)
+    latp = fab.paper_encode_params(W.frame_materials())
+    fab.paper_prepare(latp, "fp16")
+    ms_p = timed(torch, stream, lambda k: fab.paper_shade_prepared(gbufs[k % copies], "fp16",
+                                                                   out_rgb=rgbs[k % copies]), 100)
+    fab.sync_status()
+    neural_p = {k: rp["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
+    neural_p.update(rmse_lit=rp["neural"]["rmse"], ms=ms_p)
+    neural_pms = {k: rp_ms["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
+    neural_pms.update(rmse_lit=rp_ms["neural"]["rmse"], ms=ms_p)
+    runs["paper_structure"] = {
+        "network": f"paper's decoder structure, width {pw} (one-blob spatial encoding, spatial fusion 2 FC, "
+                   f"angular decoder 5 FC with one skip, leaky ReLU, 64-wide latent), rendered-space loss",
+        "neural_fp16": neural_p,
+        "target_fp": _target(neural_p, ladder, "rmse_fp"),
+        "target_lit": _target(neural_p, ladder, "rmse_lit"),
+        "multiscale": {"neural_fp16": neural_pms, "target_fp": _target(neural_pms, ms_ladder, "rmse_fp"),
+                       "target_lit": _target(neural_pms, ms_ladder, "rmse_lit")},
+        "train_steps": args.paper_steps, "train_seconds": t_paper,
+    }
     del g_tr, target
     interp = measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream)
-    best = min(runs, key=lambda k: runs[k]["neural_fp16"]["rmse_fp"])
+    best = min(("eq11", "rendered", "paper_structure"), key=lambda k: runs[k]["neural_fp16"]["rmse_fp"])
     return {
         "target_met": runs[best]["target_fp"]["target_met"],
         "target": dict(runs[best]["target_fp"], frame="1080p G-buffer of the workload (8 weaves)", loss=best,
@@ -533,6 +577,7 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
         },
         "loss_eq11": runs["eq11"],
         "loss_rendered": runs["rendered"],
+        "paper_structure": runs["paper_structure"],
         "training": {"queries": args.quality_queries, "data_spp": 2048, "steps": args.quality_steps,
                      "batch": 65536, "lr": args.quality_lr, "precision": args.quality_precision,
                      "data_seconds": t_data},
@@ -720,6 +765,29 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     out["fp8"] = {"ms_per_frame": ms_f8, "pts_per_s": N_POINTS / (ms_f8 * 1e-3),
                   "rel_l2_vs_fp16_frame": math.sqrt(float(st[0]) / float(st[1])),
                   "note": "E4M3 operands in layers 2-4 (layer 1 FP16), per-layer power-of-two weight scale"}
+    # the paper's decoder structure (Sec. 4.2) at widths 64 and 128 on the
+    # same frame: one persistent tensor-core launch per frame, and its FP32
+    # training step (batch 65536)
+    pd = {}
+    zp = torch.from_numpy(W.random_latents(len(mats), seed=31, dim=64)).cuda()
+    for pw in (64, 128):
+        fab.paper_set_params(pw, W.paper_decoder_init(pw), W.paper_encoder_init())
+        fl = 2 * (24 * pw + pw * pw + (pw + 5) * pw + 3 * pw * pw + pw * 4)
+        row = {"flop_per_point": fl}
+        for prec in ("fp16", "bf16"):
+            fab.paper_prepare(zp, prec)
+            for k in range(3):
+                fab.paper_shade_prepared(gbufs[k % copies], prec, out_rgb=rgbs[k % copies])
+            ms_pd = timed(torch, stream, lambda k: fab.paper_shade_prepared(gbufs[k % copies], prec,
+                                                                            out_rgb=rgbs[k % copies]), 200)
+            tf = fl * N_POINTS / (ms_pd * 1e-3) / 1e12
+            row[prec] = {"ms_per_frame": ms_pd, "pts_per_s": N_POINTS / (ms_pd * 1e-3), "tflops": tf,
+                         "frac_of_bf16_peak": tf / peaks()[0]["bf16_tflops"]}
+        fab.sync_status()
+        pd[f"width_{pw}"] = row
+    pd["note"] = ("FLOP/pt with the latent folded into the first layer's bias column; frac of the measured "
+                  "dense BF16 burst peak (FP16 has the same dense rate)")
+    out["paper_decoder"] = pd
     # one training step, batch 65536, over 256 training materials
     tm = W.training_materials(32)
     fab.set_train_materials(tm)
@@ -742,6 +810,14 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
     fab.set_train_precision("fp32")
     # the training workload computes in BF16 with FP32 master weights: the
     # tensor-core path leads, the FP32 SIMT path (the accuracy anchor) beside it
+    for pw in (64, 128):
+        fab.paper_set_params(pw, W.paper_decoder_init(pw, weight_bound="small"),
+                             W.paper_encoder_init(weight_bound="small"))
+        for _ in range(3):
+            fab.paper_train_step(gq, target, 1e-3)
+        pd[f"width_{pw}"]["train_ms_per_step"] = timed(torch, stream, lambda k: fab.paper_train_step(gq, target,
+                                                                                                   1e-3), 20)
+    fab.sync_status()
     out["train"] = {"ms_per_step": ms_train_tc, "batch": 65536, "samples_per_s": 65536 / (ms_train_tc * 1e-3),
                     "materials": len(tm),
                     "path": "BF16 tensor-core decoder forward/backward, FP32 master weights, encoder and Adam "

@@ -67,7 +67,12 @@ def shuffled(g: GBuffer, target: torch.Tensor, gen: torch.Generator):
 
 
 def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch: int = 65536,
-          lr0: float = 1e-3, lr1: float = 1e-5, log_every: int = 1000, seed: int = 1, verbose: bool = True):
+          lr0: float = 1e-3, lr1: float = 1e-5, log_every: int = 1000, seed: int = 1, verbose: bool = True,
+          paper: bool = False):
+    """Adam with a cosine-decayed learning rate over shuffled epochs of the
+    dataset; `paper` trains the paper's decoder structure
+    (fabric_paper_train_step) instead of the workload's network."""
+    step_fn = fab.paper_train_step if paper else fab.train_step
     fab.set_train_materials(mats)
     gen = torch.Generator(device=fab.device)
     gen.manual_seed(seed)
@@ -83,7 +88,7 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
         sl = slice(k * batch, (k + 1) * batch)
         bg = GBuffer(*(getattr(gs, f)[sl] for f in ("u", "v", "radius", "wi", "wo", "material")))
         lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * step / max(1, steps)))
-        fab.train_step(bg, ts[sl], lr, loss_out=loss_buf[step % log_every])
+        step_fn(bg, ts[sl], lr, loss_out=loss_buf[step % log_every])
         if (step + 1) % log_every == 0:
             mean = float(loss_buf.mean().item())
             losses.append((step + 1, mean))
@@ -107,7 +112,8 @@ def _errors(fab, a, gt, g):
             "rmse_tm": math.sqrt(tm[0] / n)}
 
 
-def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(1, 2, 4, 8, 16), gbuf=None):
+def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(1, 2, 4, 8, 16), gbuf=None,
+               paper: bool = False):
     """Error of the neural 1080p frame, and of the reference at lower sample
     counts, against the reference at gt_spp (see _errors for the metrics;
     the paper's results are direct-lit renders, Sec. 6, the scope's metric is
@@ -115,14 +121,17 @@ def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(
     from a second, independent ground-truth frame: `gt_noise_*` is its RMS
     deviation from the integral (half the mean squared difference of the
     two, per metric).  `gbuf`: a host G-buffer of the frame's materials
-    (default: the 1080p frame)."""
+    (default: the 1080p frame); `paper`: shade with the paper's decoder
+    structure instead of the workload's network."""
     mats = W.frame_materials()
     fab.set_materials(mats)
     g = GBuffer.from_numpy(W.frame_gbuffer() if gbuf is None else gbuf)
     gt, _ = fab.shade_reference(g, gt_spp[0], gt_spp[1], 0x6721)
-    lat = fab.encode_params(mats)
     out = {}
-    nrgb, _ = fab.shade_neural(g, lat, precision)
+    if paper:
+        nrgb, _ = fab.paper_shade_neural(g, fab.paper_encode_params(mats), precision)
+    else:
+        nrgb, _ = fab.shade_neural(g, fab.encode_params(mats), precision)
     out["neural"] = _errors(fab, nrgb, gt, g)
     for s in ref_spps:
         r, _ = fab.shade_reference(g, s, s, 0x1234)
