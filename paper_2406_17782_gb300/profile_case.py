@@ -6,13 +6,17 @@ for profilers (ncu) and quick timing:
   python -m paper_2406_17782_gb300.profile_case train [--batch 65536] [--train-precision fp32|bf16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case error [--elements 33554432] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case batched [--precision fp16] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case paper [--width 128] [--precision fp16] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case paper-train [--width 128] [--batch 65536] [--reps 3]
 
 The workload is the 1920 x 1080 G-buffer of eight weave materials (random-init
 networks); the training case uses a batch of queries over 256 training
 materials with targets from the reference kernel at 4 x 4 samples; the error
 case reduces two arrays of uniform random floats (2^25 elements each by
 default, 268 MB together: more than L2); the batched case shades the 4K
-view plus 256 ragged segments through one plan (one launch per call).  Prints the
+view plus 256 ragged segments through one plan (one launch per call); the
+paper cases run the paper's decoder structure (random-init, width 64 or
+128) on the 1080p G-buffer, or its FP32 training step.  Prints the
 mean time per launch (CUDA events) as one JSON line.
 """
 from __future__ import annotations
@@ -35,7 +39,8 @@ from .api import Fabric, GBuffer  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["reference", "decoder", "train", "error", "batched"])
+    ap.add_argument("case", choices=["reference", "decoder", "train", "error", "batched", "paper", "paper-train"])
+    ap.add_argument("--width", type=int, default=128, choices=[64, 128])
     ap.add_argument("--spp", type=int, default=16, help="samples per axis (reference)")
     ap.add_argument("--precision", default="fp16")
     ap.add_argument("--batch", type=int, default=65536)
@@ -63,6 +68,23 @@ def main(argv=None):
         out = torch.empty(3, dtype=torch.float64, device=fab.device)
         fn = lambda: fab.error_stats(ea, eb, out=out)
         points = args.elements
+    elif args.case in ("paper", "paper-train"):
+        fab.paper_set_params(args.width, W.paper_decoder_init(args.width), W.paper_encoder_init())
+        if args.case == "paper":
+            g = GBuffer.from_numpy(W.frame_gbuffer())
+            rgb = torch.empty((g.n, 3), dtype=torch.float32, device=fab.device)
+            fab.paper_prepare(fab.paper_encode_params(mats), args.precision)
+            fn = lambda: fab.paper_shade_prepared(g, args.precision, out_rgb=rgb)
+        else:
+            tm = W.training_materials(32)
+            q = W.training_queries(args.batch, len(tm), stream="profile-train")
+            g = GBuffer.from_numpy(q)
+            target = torch.empty((args.batch, 4), dtype=torch.float32, device=fab.device)
+            fab.set_materials(tm)
+            fab.shade_reference(g, 4, 4, 3, out_comps=target)
+            fab.set_train_materials(tm)
+            fn = lambda: fab.paper_train_step(g, target, 1e-3)
+        points = g.n
     elif args.case == "train":
         tm = W.training_materials(32)
         q = W.training_queries(args.batch, len(tm), stream="profile-train")
