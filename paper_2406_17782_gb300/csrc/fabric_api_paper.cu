@@ -181,6 +181,9 @@ fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch 
   if (ctx->n_train_mat < 1) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no training materials set");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int M = ctx->n_train_mat;
+  if (M > paper_train_max_materials(ctx->pn_width))
+    return fail(ctx, FABRIC_ERR_UNSUPPORTED, "paper network training takes at most %d materials at width %d",
+                paper_train_max_materials(ctx->pn_width), ctx->pn_width);
   const size_t need = ((paper_train_work_bytes(ctx->pn_width, q.n, M) + 255) & ~size_t(255)) + 256;
   void *work = scratch(ctx, need);
   if (!work) return fail(ctx, FABRIC_ERR_OOM, "training scratch (%zu bytes)", need);

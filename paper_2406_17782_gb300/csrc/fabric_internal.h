@@ -283,6 +283,7 @@ cudaError_t launch_paper_decoder(int width, int precision, const fabric_gbuffer 
 // Its FP32 training forward, loss and backward (paper_train.cu): the
 // gradient [decoder | encoder] and the batch loss; and its encoder alone.
 size_t paper_train_work_bytes(int width, int64_t batch, int n_mat);
+int paper_train_max_materials(int width);
 cudaError_t launch_paper_train(int width, const fabric_gbuffer &q, const float *target, int loss_mode,
                                const fabric_material *raw, int n_mat, const float *dec, const float *enc, float *grad,
                                double *loss, void *work, int *status, cudaStream_t s);

@@ -22,7 +22,7 @@ namespace {
 
 constexpr int TM = 64, TN = 64, TR = 16;
 constexpr int kGemmThreads = 256;
-constexpr int kChunkRows = 2048;   // batch rows per weight-gradient partial
+constexpr int kChunkRows = 512;    // batch rows per weight-gradient partial
 
 // Epilogue of the product: forward (bias, residual, leaky ReLU), input
 // gradient (addend, leaky ReLU derivative of the layer's own output), or
@@ -203,25 +203,43 @@ __global__ void pn_loss_final_kernel(const double *__restrict__ part, int n, dou
   }
 }
 
-// Per material m and batch segment s: sum of the rows of D [B][W] whose
-// query has material m (rows in order) -> part[m][s][W].
+// Per batch segment s: the sums of the rows of D [B][W] by material, part
+// [s][m][W].  Each thread owns one column and walks the segment's rows in
+// order, adding into its column of a shared-memory table of every
+// material, so every sum runs in row order (bitwise repeatable).
+constexpr int kSumRows = 512;   // rows per segment
+
 __global__ void pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_t n, const float *__restrict__ D,
-                                        int W, int64_t seg_rows, int segs, float *__restrict__ part) {
-  const int m = blockIdx.x, s = blockIdx.y, d = threadIdx.x;
-  const int64_t b0 = (int64_t)s * seg_rows, b1 = b0 + seg_rows < n ? b0 + seg_rows : n;
-  float acc = 0.0f;
-  for (int64_t b = b0; b < b1; ++b)
-    if (mat[b] == m && d < W) acc += D[b * W + d];
-  if (d < W) part[((int64_t)m * segs + s) * W + d] = acc;
+                                        int W, int n_mat, float *__restrict__ part) {
+  extern __shared__ float acc[];   // [n_mat][W]
+  __shared__ uint16_t smat[kSumRows];
+  const int d = threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * kSumRows;
+  const int rows = (int)(n - b0 < kSumRows ? n - b0 : kSumRows);
+  for (int e = d; e < n_mat * W; e += blockDim.x) acc[e] = 0.0f;
+  for (int r = d; r < rows; r += blockDim.x) smat[r] = mat[b0 + r];
+  __syncthreads();
+  const float *col = D + b0 * W + d;
+  int r = 0;
+  for (; r + 8 <= rows; r += 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = col[(int64_t)(r + q) * W];   // eight loads in flight
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[smat[r + q] * W + d] += v[q];
+  }
+  for (; r < rows; ++r) acc[smat[r] * W + d] += col[(int64_t)r * W];
+  float *out = part + (int64_t)blockIdx.x * n_mat * W;
+  for (int m = 0; m < n_mat; ++m) out[m * W + d] = acc[m * W + d];
 }
 
+// G[m][d] = sum over segments, in segment order.
 __global__ void pn_segment_total_kernel(const float *__restrict__ part, int n_mat, int segs, int W,
                                         float *__restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_mat * W) return;
-  const int m = e / W, d = e % W;
   float s = 0.0f;
-  for (int k = 0; k < segs; ++k) s += part[((int64_t)m * segs + k) * W + d];
+  for (int k = 0; k < segs; ++k) s += part[(int64_t)k * n_mat * W + e];
   G[e] = s;
 }
 
@@ -373,9 +391,13 @@ cudaError_t wgrad(const float *dZ, int ldz, int N, const float *X, int ldx, int 
 
 }  // namespace
 
+// Largest material table whose per-material sums fit the shared memory of
+// one CTA (n_mat x W floats); the training call refuses larger tables.
+int paper_train_max_materials(int w) { return (int)((200 * 1024) / (w * 4)); }
+
 size_t paper_train_work_bytes(int w, int64_t B, int n_mat) {
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
-  const int segs = 16;
+  const int64_t segs = (B + kSumRows - 1) / kSumRows;
   size_t f = 0;
   f += (size_t)B * (kPnLatent + kPnBlob);         // X0
   f += (size_t)B * w;                             // H1
@@ -399,7 +421,7 @@ cudaError_t launch_paper_train(int w, const fabric_gbuffer &q, const float *targ
   const PaperOffsets o = paper_offsets(w);
   const int64_t B = q.n;
   const int KX0 = kPnLatent + kPnBlob, KA = w + kPnAng;
-  const int segs = 16;
+  const int segs = (int)((B + kSumRows - 1) / kSumRows);
   float *p = static_cast<float *>(work);
   auto take = [&](size_t nfl) {
     float *r = p;
@@ -458,8 +480,9 @@ cudaError_t launch_paper_train(int w, const fabric_gbuffer &q, const float *targ
   PN_TRY(wgrad(D3, w, w, X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
   // ---- latent gradient: per-material sums of dg1, times S1's latent block
   {
-    const int64_t seg_rows = (B + segs - 1) / segs;
-    pn_material_sums_kernel<<<dim3(n_mat, segs), w, 0, s>>>(q.material, B, D3, w, seg_rows, segs, msum);
+    const size_t smem = (size_t)n_mat * w * sizeof(float);
+    PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), 200 * 1024));
+    pn_material_sums_kernel<<<segs, w, smem, s>>>(q.material, B, D3, w, n_mat, msum);
     PN_TRY(cudaGetLastError());
     pn_segment_total_kernel<<<(n_mat * w + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, w, G);
     PN_TRY(cudaGetLastError());
