@@ -874,6 +874,198 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
   }
 }
 
+// ---- the same reduction on pairs of elements with packed FP32x2
+// instructions (add/sub/mul/fma.rn.f32x2: one instruction for two lanes),
+// which halves the arithmetic instruction count of the error-free
+// transformations; used when a and b are 8-byte aligned.  Lane 0 of every
+// packed value carries the even element of a pair, lane 1 the odd one; each
+// lane has its own double-float run sums.  An element outside the fast
+// range enters its lane as zeros (an exact no-op) and is added by the FP64
+// pass as in err_partial_kernel.
+constexpr int kErrRun2 = 16;    // pairs per run
+constexpr int kErrBatch2 = 4;   // pair loads in flight per thread
+
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+constexpr uint64_t kSign2 = 0x8000000080000000ull;   // both lanes' sign bits
+
+// Packed DFloat: (h, l) += (x, y) per lane, as DFloat::add.
+__device__ __forceinline__ void dadd2(uint64_t &h, uint64_t &l, uint64_t x, uint64_t y) {
+  const uint64_t t = add2(h, x);
+  const uint64_t bv = sub2(t, h);
+  const uint64_t av = sub2(t, bv);
+  uint64_t e = add2(sub2(h, av), sub2(x, bv));
+  e = add2(e, add2(l, y));
+  h = add2(t, e);
+  l = sub2(e, sub2(h, t));
+}
+
+template <bool W, typename Idx>
+__global__ void __launch_bounds__(kErrThreads, 4) err_partial2_kernel(const float *__restrict__ a,
+                                                                   const float *__restrict__ b, int64_t n_,
+                                                                   const float *__restrict__ w, int group,
+                                                                   int w_stride, double *__restrict__ part) {
+  __shared__ double s0[kErrThreads], s1[kErrThreads], s2[kErrThreads];
+  const uint64_t *a2 = reinterpret_cast<const uint64_t *>(a);
+  const uint64_t *b2 = reinterpret_cast<const uint64_t *>(b);
+  const Idx n = (Idx)n_;
+  const Idx np = n / 2;   // pairs; an odd last element is added by the FP64 pass of thread 0
+  const Idx stride = (Idx)kErrBlocks * kErrThreads;
+  const Idx start = (Idx)blockIdx.x * kErrThreads + threadIdx.x;
+  const uint64_t two = pk2(2.0f, 2.0f);
+  double e2 = 0.0, b2s = 0.0;
+  float mh = -1.0f, ml = 0.0f;
+  bool slow = false;
+  for (Idx j0 = start; j0 < np; j0 += kErrRun2 * stride) {
+    uint64_t EH = 0, EL = 0, BH = 0, BL = 0;
+#pragma unroll 1
+    for (int r0 = 0; r0 < kErrRun2; r0 += kErrBatch2) {
+      uint64_t av[kErrBatch2], bv[kErrBatch2], wv[kErrBatch2];
+#pragma unroll
+      for (int q = 0; q < kErrBatch2; ++q) {
+        const Idx j = j0 + (Idx)(r0 + q) * stride;
+        const bool in = j < np;
+        av[q] = in ? __ldg(a2 + j) : 0ull;
+        bv[q] = in ? __ldg(b2 + j) : 0ull;
+        if (W) {
+          const float w0 = in ? w[(int64_t)((2 * j) / group) * w_stride] : 1.0f;
+          const float w1 = in ? w[(int64_t)((2 * j + 1) / group) * w_stride] : 1.0f;
+          wv[q] = pk2(w0, w1);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kErrBatch2; ++q) {
+        // w (a - b) as D + E exactly (TwoSum, then the FMA TwoProduct by w)
+        uint64_t D = sub2(av[q], bv[q]);
+        const uint64_t BV = sub2(D, av[q]);
+        const uint64_t AV = sub2(D, BV);
+        uint64_t E = sub2(sub2(av[q], AV), add2(bv[q], BV));
+        uint64_t Bh = bv[q], Bl = 0;
+        if (W) {
+          const uint64_t P = mul2(D, wv[q]);
+          const uint64_t PE = fma2(D, wv[q], P ^ kSign2);
+          E = fma2(E, wv[q], PE);
+          D = P;
+          Bh = mul2(bv[q], wv[q]);
+          Bl = fma2(bv[q], wv[q], Bh ^ kSign2);
+        }
+        float dh0, dh1, bh0, bh1;
+        upk2(D, dh0, dh1);
+        upk2(Bh, bh0, bh1);
+        bool ok0 = err_fast(dh0) && err_fast(bh0), ok1 = err_fast(dh1) && err_fast(bh1);
+        if (W) {
+          float w0, w1;
+          upk2(wv[q], w0, w1);
+          ok0 = ok0 && err_fast(w0);
+          ok1 = ok1 && err_fast(w1);
+        }
+        uint64_t PP = mul2(D, D);
+        uint64_t X = fma2(mul2(D, two), E, fma2(D, D, PP ^ kSign2));
+        uint64_t QQ = mul2(Bh, Bh);
+        uint64_t Y = fma2(mul2(Bh, two), Bl, fma2(Bh, Bh, QQ ^ kSign2));
+        if (!(ok0 && ok1)) {
+          slow = true;
+          const uint64_t keep = (ok0 ? 0xFFFFFFFFull : 0ull) | (ok1 ? 0xFFFFFFFF00000000ull : 0ull);
+          PP &= keep;
+          X &= keep;
+          QQ &= keep;
+          Y &= keep;
+        }
+        dadd2(EH, EL, PP, X);
+        dadd2(BH, BL, QQ, Y);
+        float dl0, dl1;
+        upk2(E, dl0, dl1);
+#pragma unroll
+        for (int lane = 0; lane < 2; ++lane) {
+          const float dh = lane ? dh1 : dh0, dl = lane ? dl1 : dl0;
+          if (!(lane ? ok1 : ok0)) continue;
+          const float sh = fabsf(dh);
+          if (sh >= mh) {
+            const float sl = dh < 0.0f ? -dl : dl;
+            if (sh > mh || sl > ml) {
+              mh = sh;
+              ml = sl;
+            }
+          }
+        }
+      }
+    }
+    float h0, h1, l0, l1;
+    upk2(EH, h0, h1);
+    upk2(EL, l0, l1);
+    e2 += ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+    upk2(BH, h0, h1);
+    upk2(BL, l0, l1);
+    b2s += ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+  }
+  double mx = mh < 0.0f ? 0.0 : (double)mh + (double)ml;
+  const bool odd_tail = (n & 1) && blockIdx.x == 0 && threadIdx.x == 0;
+  if (slow || odd_tail) {
+    // elements outside the fast range (and the odd last element) in FP64
+    auto fp64 = [&](Idx i, bool force) {
+      const float ai = a[i], bi = b[i];
+      const float wv = W ? w[(int64_t)(i / group) * w_stride] : 1.0f;
+      float dh, dl, bh, bl;
+      if (!force && err_pairs<W>(ai, bi, wv, dh, dl, bh, bl)) return;
+      const double wi = (double)wv;
+      const double d = ((double)ai - (double)bi) * wi;
+      const double bb = (double)bi * wi;
+      e2 += d * d;
+      b2s += bb * bb;
+      mx = fmax(mx, fabs(d));
+    };
+    if (slow)
+      for (Idx j = start; j < np; j += stride) {
+        fp64(2 * j, false);
+        fp64(2 * j + 1, false);
+      }
+    if (odd_tail) fp64(n - 1, true);
+  }
+  s0[threadIdx.x] = e2;
+  s1[threadIdx.x] = b2s;
+  s2[threadIdx.x] = mx;
+  __syncthreads();
+  for (int off = kErrThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      s0[threadIdx.x] += s0[threadIdx.x + off];
+      s1[threadIdx.x] += s1[threadIdx.x + off];
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + off]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = s0[0];
+    part[3 * blockIdx.x + 1] = s1[0];
+    part[3 * blockIdx.x + 2] = s2[0];
+  }
+}
+
 // One warp: lane l sums the partials l, l + 32, ... in order, then the 32
 // lane sums are added in lane order.
 __global__ void err_final_kernel(const double *__restrict__ part, double *__restrict__ out) {
@@ -1082,7 +1274,13 @@ cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const 
                                double *out, void *work, cudaStream_t s) {
   double *part = static_cast<double *>(work);
   const bool small = n + (int64_t)kErrRun * kErrBlocks * kErrThreads < ((int64_t)1 << 31);
-  if (w && small) err_partial_kernel<true, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  const bool packed = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 7u) == 0;
+  if (packed) {
+    if (w && small) err_partial2_kernel<true, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+    else if (w) err_partial2_kernel<true, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+    else if (small) err_partial2_kernel<false, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+    else err_partial2_kernel<false, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  } else if (w && small) err_partial_kernel<true, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
   else if (w) err_partial_kernel<true, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
   else if (small) err_partial_kernel<false, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
   else err_partial_kernel<false, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);

@@ -296,3 +296,29 @@ def test_neural_error_stats_fp64_reduction(fab, setup):
     w = np.repeat(dirs[:, 2].astype(np.float64), 3)
     np.testing.assert_allclose(out[0], ((d[:n] * w) ** 2).sum(), rtol=1e-12)
     np.testing.assert_allclose(out[1], ((b[:n].astype(np.float64) * w) ** 2).sum(), rtol=1e-12)
+
+
+def test_error_stats_packed_and_scalar_paths(fab):
+    """The reduction takes pairs of elements with packed FP32x2 instructions
+    when both arrays are 8-byte aligned and single elements otherwise: both
+    forms, odd and even lengths, with and without weights, against numpy."""
+    rng = np.random.default_rng(17)
+    n = 300_001
+    a = (rng.standard_normal(n + 1) * np.exp(rng.uniform(-30, 30, n + 1))).astype(np.float32)
+    b = (a.astype(np.float64) * (1 + 1e-3 * rng.standard_normal(n + 1))).astype(np.float32)
+    wts = rng.uniform(0.1, 2.0, n + 1).astype(np.float32)
+    ta, tb, tw = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), torch.from_numpy(wts).cuda()
+    for off_a, off_b, m in ((0, 0, n), (0, 0, n - 1), (1, 1, n), (1, 0, n - 1)):
+        for weighted in (False, True):
+            x, y = ta[off_a:off_a + m], tb[off_b:off_b + m]
+            wv = tw[:m] if weighted else None
+            out = fab.error_stats(x, y, weights=wv).cpu().numpy()
+            w64 = wts[:m].astype(np.float64) if weighted else 1.0
+            d = (a[off_a:off_a + m].astype(np.float64) - b[off_b:off_b + m].astype(np.float64)) * w64
+            bb = b[off_b:off_b + m].astype(np.float64) * w64
+            np.testing.assert_allclose(out[0], (d * d).sum(), rtol=1e-12)
+            np.testing.assert_allclose(out[1], (bb * bb).sum(), rtol=1e-12)
+            if weighted:
+                np.testing.assert_allclose(out[2], np.abs(d).max(), rtol=1e-13)
+            else:
+                assert out[2] == np.abs(d).max()
