@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
                                                                   int w_stride, double *__restrict__ part) {
   __shared__ double s0[kErrThreads], s1[kErrThreads], s2[kErrThreads];
   const Idx n = (Idx)n_;
-  const Idx stride = (Idx)kErrBlocks * kErrThreads;
+  const Idx stride = (Idx)gridDim.x * kErrThreads;
   const Idx start = (Idx)blockIdx.x * kErrThreads + threadIdx.x;
   double e2 = 0.0, b2 = 0.0;
   float mh = -1.0f, ml = 0.0f;   // largest |w(a-b)| so far as mh + ml (mh < 0: none)
@@ -884,6 +884,8 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
 // pass as in err_partial_kernel.
 constexpr int kErrRun2 = 16;    // pairs per run
 constexpr int kErrBatch2 = 4;   // pair loads in flight per thread
+constexpr int kErrPerSm2 = 4;   // resident CTAs per SM
+constexpr int kErrBlocks2 = 152 * kErrPerSm2;   // one wave on 152 SMs
 
 __device__ __forceinline__ uint64_t pk2(float lo, float hi) {
   uint64_t r;
@@ -927,7 +929,7 @@ __device__ __forceinline__ void dadd2(uint64_t &h, uint64_t &l, uint64_t x, uint
 }
 
 template <bool W, typename Idx>
-__global__ void __launch_bounds__(kErrThreads, 4) err_partial2_kernel(const float *__restrict__ a,
+__global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(const float *__restrict__ a,
                                                                    const float *__restrict__ b, int64_t n_,
                                                                    const float *__restrict__ w, int group,
                                                                    int w_stride, double *__restrict__ part) {
@@ -936,7 +938,7 @@ __global__ void __launch_bounds__(kErrThreads, 4) err_partial2_kernel(const floa
   const uint64_t *b2 = reinterpret_cast<const uint64_t *>(b);
   const Idx n = (Idx)n_;
   const Idx np = n / 2;   // pairs; an odd last element is added by the FP64 pass of thread 0
-  const Idx stride = (Idx)kErrBlocks * kErrThreads;
+  const Idx stride = (Idx)gridDim.x * kErrThreads;
   const Idx start = (Idx)blockIdx.x * kErrThreads + threadIdx.x;
   const uint64_t two = pk2(2.0f, 2.0f);
   double e2 = 0.0, b2s = 0.0;
@@ -1068,10 +1070,10 @@ __global__ void __launch_bounds__(kErrThreads, 4) err_partial2_kernel(const floa
 
 // One warp: lane l sums the partials l, l + 32, ... in order, then the 32
 // lane sums are added in lane order.
-__global__ void err_final_kernel(const double *__restrict__ part, double *__restrict__ out) {
+__global__ void err_final_kernel(const double *__restrict__ part, int n_parts, double *__restrict__ out) {
   const int lane = threadIdx.x & 31;
   double e2 = 0.0, b2 = 0.0, mx = 0.0;
-  for (int k = lane; k < kErrBlocks; k += 32) {
+  for (int k = lane; k < n_parts; k += 32) {
     e2 += part[3 * k];
     b2 += part[3 * k + 1];
     mx = fmax(mx, part[3 * k + 2]);
@@ -1275,16 +1277,17 @@ cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const 
   double *part = static_cast<double *>(work);
   const bool small = n + (int64_t)kErrRun * kErrBlocks * kErrThreads < ((int64_t)1 << 31);
   const bool packed = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 7u) == 0;
+  const int blocks = packed ? kErrBlocks2 : kErrBlocks;
   if (packed) {
-    if (w && small) err_partial2_kernel<true, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-    else if (w) err_partial2_kernel<true, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-    else if (small) err_partial2_kernel<false, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-    else err_partial2_kernel<false, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-  } else if (w && small) err_partial_kernel<true, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-  else if (w) err_partial_kernel<true, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-  else if (small) err_partial_kernel<false, int><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-  else err_partial_kernel<false, int64_t><<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
-  err_final_kernel<<<1, 32, 0, s>>>(part, out);
+    if (w && small) err_partial2_kernel<true, int><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+    else if (w) err_partial2_kernel<true, int64_t><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+    else if (small) err_partial2_kernel<false, int><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+    else err_partial2_kernel<false, int64_t><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  } else if (w && small) err_partial_kernel<true, int><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  else if (w) err_partial_kernel<true, int64_t><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  else if (small) err_partial_kernel<false, int><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  else err_partial_kernel<false, int64_t><<<blocks, kErrThreads, 0, s>>>(a, b, n, w, group, w_stride, part);
+  err_final_kernel<<<1, 32, 0, s>>>(part, blocks, out);
   return cudaGetLastError();
 }
 
