@@ -414,6 +414,13 @@ def measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream):
     return out
 
 
+def _vs_integral(rmse, gt_noise):
+    """RMSE against the integral itself: the measured RMSE against the
+    ground truth with the ground truth's own Monte Carlo variance removed
+    (errors independent of the ground truth's sampling)."""
+    return math.sqrt(max(0.0, rmse * rmse - gt_noise * gt_noise))
+
+
 def _ladder_entry(sp, errs, ms):
     return {"spp": sp * sp, "rmse_fp": errs["rmse_fp"], "rel_l2_fp": errs["rel_l2_fp"], "rmse_tm": errs["rmse_tm"],
             "rmse_lit": errs["rmse"], "ms": ms}
@@ -497,7 +504,9 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
             ms_gt_info = {k: rm_ms[k] for k in ("gt_rms", "gt_rms_fp", "gt_noise", "gt_noise_fp")}
         fab.sync_status()
         neural = {k: rm["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
-        neural.update(rmse_lit=rm["neural"]["rmse"], ms=ms["fp16"])
+        neural.update(rmse_lit=rm["neural"]["rmse"], ms=ms["fp16"],
+                      rmse_fp_vs_integral=_vs_integral(rm["neural"]["rmse_fp"], rm["gt_noise_fp"]),
+                      rmse_lit_vs_integral=_vs_integral(rm["neural"]["rmse"], rm["gt_noise"]))
         neural8 = {k: rm8["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
         neural8.update(rmse_lit=rm8["neural"]["rmse"], ms=ms["fp8"])
         neural_ms = {k: rm_ms["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
@@ -535,7 +544,9 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
                                                                    out_rgb=rgbs[k % copies]), 100)
     fab.sync_status()
     neural_p = {k: rp["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
-    neural_p.update(rmse_lit=rp["neural"]["rmse"], ms=ms_p)
+    neural_p.update(rmse_lit=rp["neural"]["rmse"], ms=ms_p,
+                    rmse_fp_vs_integral=_vs_integral(rp["neural"]["rmse_fp"], rp["gt_noise_fp"]),
+                    rmse_lit_vs_integral=_vs_integral(rp["neural"]["rmse"], rp["gt_noise"]))
     neural_pms = {k: rp_ms["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
     neural_pms.update(rmse_lit=rp_ms["neural"]["rmse"], ms=ms_p)
     runs["paper_structure"] = {
@@ -563,7 +574,9 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
                   "rmse_lit: f_P <wi.n_s> per channel (unit directional light)",
         "ground_truth": dict(gt_info, spp=1024,
                              note="gt_noise*: RMS Monte Carlo deviation of the ground truth from the integral, "
-                                  "from a second ground-truth frame with an independent seed; the reference "
+                                  "from a second ground-truth frame with an independent seed; *_vs_integral: a "
+                                  "network's RMSE with that variance removed (its error against the integral "
+                                  "itself; the measured RMSE is the upper end of the interval); the reference "
                                   "kernel equals the FP64 oracle on the same sample sequence to 1e-4 per "
                                   "component (GPU tests, including a 65,536-pixel subset of this frame at "
                                   "1024 spp)"),
