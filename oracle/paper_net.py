@@ -31,6 +31,10 @@ Parameter layout (flat float vectors, weights [out][in]; shared as an
 interface with the CUDA library, each side implementing it on its own):
   S1[W][88] s1[W] S2[W][W] s2[W] A1[W][W+5] a1[W] A2[W][W] a2[W]
   A3[W][W] a3[W] A4[W][W] a4[W] A5[4][W] a5[4]
+Ablations (Sec. 6.3 varies the one-blob encoding and the spatial fusion):
+without the one-blob encoding S1 is [W][67] over [z | frac u, frac v, t];
+without the spatial fusion S1, s1, S2, s2 are absent and A1 is [W][93] over
+[z | one-blob | wi | wo.xy].
 Encoder: E1[128][22] e1[128] E2[128][128] e2[128] E3[64][128] e3[64], the
 workload's residual encoder (oracle.mlp) with a 64-wide output.
 """
@@ -53,11 +57,26 @@ R_HI = 2.5
 WIDTHS = (64, 128)
 
 
-def dec_shapes(w: int):
-    return [("S1", (w, LATENT + N_BLOB)), ("s1", (w,)), ("S2", (w, w)), ("s2", (w,)),
-            ("A1", (w, w + N_ANG)), ("a1", (w,)), ("A2", (w, w)), ("a2", (w,)),
-            ("A3", (w, w)), ("a3", (w,)), ("A4", (w, w)), ("a4", (w,)),
+# Ablations of the structure (Sec. 6.3 studies the one-blob encoding and the
+# spatial fusion): FULL is the structure above; NO_ONEBLOB feeds the three
+# spatial inputs (frac u, frac v, size coordinate t) unencoded; NO_FUSION
+# drops the two spatial-fusion layers and feeds [z | one-blob | angular]
+# straight into the angular decoder.
+FULL, NO_ONEBLOB, NO_FUSION = 0, 1, 2
+N_RAW = 3
+
+
+def n_spatial(ablation: int = FULL) -> int:
+    return N_RAW if ablation == NO_ONEBLOB else N_BLOB
+
+
+def dec_shapes(w: int, ablation: int = FULL):
+    tail = [("A2", (w, w)), ("a2", (w,)), ("A3", (w, w)), ("a3", (w,)), ("A4", (w, w)), ("a4", (w,)),
             ("A5", (mlp.N_OUT, w)), ("a5", (mlp.N_OUT,))]
+    if ablation == NO_FUSION:
+        return [("A1", (w, LATENT + N_BLOB + N_ANG)), ("a1", (w,))] + tail
+    return [("S1", (w, LATENT + n_spatial(ablation))), ("s1", (w,)), ("S2", (w, w)), ("s2", (w,)),
+            ("A1", (w, w + N_ANG)), ("a1", (w,))] + tail
 
 
 ENC_SHAPES = [("E1", (mlp.ENC_HIDDEN, mlp.ENC_IN)), ("e1", (mlp.ENC_HIDDEN,)),
@@ -95,13 +114,16 @@ def size_coordinate(r: np.ndarray) -> np.ndarray:
     return np.log(r / R_LO) / math.log(R_HI / R_LO)
 
 
-def spatial_features(u, v, r) -> np.ndarray:
+def spatial_features(u, v, r, ablation: int = FULL) -> np.ndarray:
     """The 24 one-blob channels: frac(u) (8, periodic) | frac(v) (8,
-    periodic) | footprint size (8)."""
+    periodic) | footprint size (8); for NO_ONEBLOB the three inputs
+    themselves (frac u, frac v, t)."""
     u = np.asarray(u, np.float64)
     v = np.asarray(v, np.float64)
-    return np.concatenate([oneblob(u - np.floor(u), True), oneblob(v - np.floor(v), True),
-                           oneblob(size_coordinate(r), False)], axis=1)
+    fu, fv, t = u - np.floor(u), v - np.floor(v), size_coordinate(r)
+    if ablation == NO_ONEBLOB:
+        return np.stack([fu, fv, t], axis=1)
+    return np.concatenate([oneblob(fu, True), oneblob(fv, True), oneblob(t, False)], axis=1)
 
 
 def angular_features(wi, wo) -> np.ndarray:
@@ -114,26 +136,30 @@ def angular_features(wi, wo) -> np.ndarray:
 # decoder
 # --------------------------------------------------------------------------
 def decoder_forward(p: dict, z: np.ndarray, blob: np.ndarray, ang: np.ndarray, keep: bool = False):
-    """Raw head y [n, 4] from per-point latents z [n, 64], one-blob channels
-    [n, 24] and angular inputs [n, 5]."""
+    """Raw head y [n, 4] from per-point latents z [n, 64], spatial channels
+    [n, 24] (or [n, 3] without the one-blob encoding) and angular inputs
+    [n, 5]; without S1 (NO_FUSION) the angular decoder takes
+    [z | spatial | angular] directly."""
     x0 = np.concatenate([np.asarray(z, np.float64), blob], axis=1)
-    g1 = x0 @ p["S1"].T + p["s1"]
-    h1 = lrelu(g1)
-    g2 = h1 @ p["S2"].T + p["s2"]
-    hs = lrelu(g2)
-    xa = np.concatenate([hs, ang], axis=1)
-    q1 = xa @ p["A1"].T + p["a1"]
-    k1 = lrelu(q1)
-    q2 = k1 @ p["A2"].T + p["a2"]
-    k2 = lrelu(q2)
-    q3 = k2 @ p["A3"].T + p["a3"] + k1            # skip joins before the last leaky ReLU
-    k3 = lrelu(q3)
-    q4 = k3 @ p["A4"].T + p["a4"]
-    k4 = lrelu(q4)
-    y = k4 @ p["A5"].T + p["a5"]
-    if keep:
-        return y, dict(x0=x0, g1=g1, h1=h1, g2=g2, xa=xa, q1=q1, k1=k1, q2=q2, k2=k2, q3=q3, k3=k3, q4=q4, k4=k4)
-    return y
+    c = dict(x0=x0)
+    if "S1" in p:
+        c["g1"] = x0 @ p["S1"].T + p["s1"]
+        c["h1"] = lrelu(c["g1"])
+        c["g2"] = c["h1"] @ p["S2"].T + p["s2"]
+        xa = np.concatenate([lrelu(c["g2"]), ang], axis=1)
+    else:
+        xa = np.concatenate([x0, ang], axis=1)
+    c["xa"] = xa
+    c["q1"] = xa @ p["A1"].T + p["a1"]
+    c["k1"] = lrelu(c["q1"])
+    c["q2"] = c["k1"] @ p["A2"].T + p["a2"]
+    c["k2"] = lrelu(c["q2"])
+    c["q3"] = c["k2"] @ p["A3"].T + p["a3"] + c["k1"]     # skip joins before the last leaky ReLU
+    c["k3"] = lrelu(c["q3"])
+    c["q4"] = c["k3"] @ p["A4"].T + p["a4"]
+    c["k4"] = lrelu(c["q4"])
+    y = c["k4"] @ p["A5"].T + p["a5"]
+    return (y, c) if keep else y
 
 
 def decoder_backward(p: dict, c: dict, dy: np.ndarray):
@@ -155,22 +181,26 @@ def decoder_backward(p: dict, c: dict, dy: np.ndarray):
     g["A1"] = dq1.T @ c["xa"]
     g["a1"] = dq1.sum(0)
     dxa = dq1 @ p["A1"]
-    w = p["S2"].shape[0]
-    dg2 = dxa[:, :w] * dlrelu(c["g2"])
+    n_a = c["xa"].shape[1] - N_ANG
+    if "S1" not in p:
+        return g, dxa[:, :LATENT], dxa[:, n_a:]
+    dg2 = dxa[:, :n_a] * dlrelu(c["g2"])
     g["S2"] = dg2.T @ c["h1"]
     g["s2"] = dg2.sum(0)
     dg1 = (dg2 @ p["S2"]) * dlrelu(c["g1"])
     g["S1"] = dg1.T @ c["x0"]
     g["s1"] = dg1.sum(0)
     dx0 = dg1 @ p["S1"]
-    return g, dx0[:, :LATENT], dxa[:, w:]
+    return g, dx0[:, :LATENT], dxa[:, n_a:]
 
 
-def shade(p: dict, z_mat: np.ndarray, materials, gbuf: dict):
-    """Per-point shading with the paper's decoder: (components [n, 4],
-    rgb [n, 3]); z_mat [n_mat, 64] per material."""
+def shade(p: dict, z_mat: np.ndarray, materials, gbuf: dict, ablation: int = FULL):
+    """Per-point shading with the paper's decoder (or one of its
+    ablations): (components [n, 4], rgb [n, 3]); z_mat [n_mat, 64] per
+    material."""
     mat = np.asarray(gbuf["material"], np.int64)
-    y = decoder_forward(p, np.asarray(z_mat, np.float64)[mat], spatial_features(gbuf["u"], gbuf["v"], gbuf["radius"]),
+    y = decoder_forward(p, np.asarray(z_mat, np.float64)[mat],
+                        spatial_features(gbuf["u"], gbuf["v"], gbuf["radius"], ablation),
                         angular_features(gbuf["wi"], gbuf["wo"]))
     comps = mlp.head_to_components(y)
     return comps, mlp.recombine(comps, materials, mat)

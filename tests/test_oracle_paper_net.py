@@ -154,3 +154,74 @@ def test_flop_count(PN):
     # 2 (24*64 + 64*64 + 69*64 + 3*64*64 + 64*4) with the latent folded
     assert PN.flops_per_point(64) == 2 * (24 * 64 + 64 * 64 + 69 * 64 + 3 * 64 * 64 + 64 * 4) == 45_184
     assert PN.flops_per_point(128) == 2 * (24 * 128 + 128 * 128 + 133 * 128 + 3 * 128 * 128 + 128 * 4)
+
+
+def test_ablation_shapes_and_raw_spatial_inputs(PN):
+    """Without the one-blob encoding the spatial channels are the inputs
+    themselves; without the spatial fusion the angular decoder takes
+    [z | one-blob | angular] (64 + 24 + 5 = 93 inputs)."""
+    f = PN.spatial_features(np.float32([3.25, -0.75]), np.float32([0.5, 7.125]), np.float32([1e-4, 2.5]),
+                            PN.NO_ONEBLOB)
+    np.testing.assert_allclose(f, [[0.25, 0.5, 0.0], [0.25, 0.125, 1.0]], atol=1e-7)
+    shapes = dict(PN.dec_shapes(64, PN.NO_FUSION))
+    assert "S1" not in shapes and shapes["A1"] == (64, 93)
+    assert dict(PN.dec_shapes(128, PN.NO_ONEBLOB))["S1"] == (128, 67)
+
+
+def test_no_fusion_closed_form_through_the_skip(PN):
+    """No spatial fusion: A1 reads latent[2] (unit 0) and the one-blob
+    channel 3 with weight -2 (unit 1, through the leaky slope); A2 = 0, so
+    the residual block returns lrelu(a3 + k1)."""
+    w = 64
+    p = {k: np.zeros(s) for k, s in PN.dec_shapes(w, PN.NO_FUSION)}
+    p["A1"][0, 2] = 1.0
+    p["A1"][1, 64 + 3] = -2.0
+    p["a3"][:2] = [0.5, 0.0]
+    p["A4"][:2, :2] = np.eye(2)
+    p["A5"][0, 0] = 1.0
+    p["A5"][1, 1] = 1.0
+    z = np.zeros((1, 64))
+    z[0, 2] = 0.25
+    blob = np.zeros((1, 24))
+    blob[0, 3] = 0.5
+    y = PN.decoder_forward(p, z, blob, np.zeros((1, 5)))
+    # k1 = (0.25, lrelu(-1) = -0.01); k3 = (0.75, lrelu(-0.01) = -1e-4); k4 = (0.75, -1e-6)
+    np.testing.assert_allclose(y, [[0.75, -1e-6, 0.0, 0.0]], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("ablation", [1, 2])
+def test_ablation_backward_finite_differences(PN, ablation):
+    rng = np.random.default_rng(20 + ablation)
+    w = 64
+    p = {k: rng.standard_normal(s) / math.sqrt(s[-1]) for k, s in PN.dec_shapes(w, ablation)}
+    n = 5
+    z = rng.standard_normal((n, 64))
+    sp = PN.spatial_features(rng.uniform(0, 9, n), rng.uniform(0, 9, n), np.exp(rng.uniform(-9, 0.5, n)), ablation)
+    ang = PN.angular_features(W.hemisphere_uniform(rng, n), W.hemisphere_uniform(rng, n))
+    dy = rng.standard_normal((n, 4))
+    y, cache = PN.decoder_forward(p, z, sp, ang, keep=True)
+    g, dz, dang = PN.decoder_backward(p, cache, dy)
+    f = lambda pp, zz, aa: float(np.sum(dy * PN.decoder_forward(pp, zz, sp, aa)))
+    h = 1e-6
+    for name, shape in PN.dec_shapes(w, ablation):
+        for _ in range(4):
+            idx = tuple(rng.integers(0, s) for s in shape)
+            pp = {k: v.copy() for k, v in p.items()}
+            pp[name][idx] += h
+            fp = f(pp, z, ang)
+            pp[name][idx] -= 2 * h
+            fd = (fp - f(pp, z, ang)) / (2 * h)
+            assert abs(fd - g[name][idx]) <= 1e-6 * max(1.0, abs(fd)), (ablation, name, idx)
+    for _ in range(6):
+        i, j = rng.integers(0, n), rng.integers(0, 64)
+        zz = z.copy()
+        zz[i, j] += h
+        fp = f(p, zz, ang)
+        zz[i, j] -= 2 * h
+        assert abs((fp - f(p, zz, ang)) / (2 * h) - dz[i, j]) <= 1e-6 * max(1.0, abs(dz[i, j]))
+        j = rng.integers(0, 5)
+        aa = ang.copy()
+        aa[i, j] += h
+        fp = f(p, z, aa)
+        aa[i, j] -= 2 * h
+        assert abs((fp - f(p, z, aa)) / (2 * h) - dang[i, j]) <= 1e-6 * max(1.0, abs(dang[i, j]))
