@@ -419,6 +419,39 @@ fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *d
 /* Copy the paper network's parameters out (NULL skips).  Synchronous. */
 fabric_status fabric_paper_get_params(fabric_ctx *ctx, float *decoder, float *encoder);
 
+/*
+ * The two ablations of Sec. 6.3 ("Ablation study") beside the full
+ * structure (FABRIC_PAPER_FULL, what fabric_paper_set_params sets):
+ *   FABRIC_PAPER_NO_ONEBLOB: the footprint's three inputs enter S1 as they
+ *     are, [z (64) | frac u | frac v | t] -> S1[W][67];
+ *   FABRIC_PAPER_NO_FUSION: S1 and S2 are left out and the angular decoder
+ *     takes [z (64) | one-blob (24) | wi | wo.xy] -> A1[W][93].
+ * Parameter layout otherwise as above, absent layers omitted.  Ablations
+ * train (fabric_paper_train_step) and shade in FP32
+ * (fabric_paper_shade_fp32); the tensor-core decoder (fabric_paper_prepare,
+ * fabric_paper_shade_*) refuses them with FABRIC_ERR_UNSUPPORTED.
+ */
+enum { FABRIC_PAPER_FULL = 0, FABRIC_PAPER_NO_ONEBLOB = 1, FABRIC_PAPER_NO_FUSION = 2 };
+
+/* Decoder parameter count of `ablation` at width 64 or 128; -1 otherwise. */
+int64_t fabric_paper_structure_param_count(int width, int ablation);
+
+/* fabric_paper_set_params for a structure: a change of width or structure
+ * needs both parameter arrays (fabric_paper_structure_param_count(width,
+ * ablation) and fabric_paper_param_count(width, 1) floats).  Resets the
+ * paper network's Adam state.  Synchronous. */
+fabric_status fabric_paper_set_structure(fabric_ctx *ctx, int width, int ablation, const float *decoder,
+                                         const float *encoder);
+
+/* The paper network (any structure) in FP32 on CUDA cores, one thread per
+ * point and layer GEMMs over the G-buffer: latents_dev [n_mat][64] for the
+ * material table; rgb_dev [n][3], comps_dev [n][4] (16-byte aligned) or
+ * NULL.  Uses the context's scratch (at most (5 W + 230) * 4 bytes a point).
+ * A material index beyond the table gives NaN outputs and
+ * FABRIC_ERR_DEVICE at the next fabric_sync_status. */
+fabric_status fabric_paper_shade_fp32(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                      float *rgb_dev, float *comps_dev, void *stream);
+
 /* Fold latents_dev [n_mat][64] (n_mat = the material table's size, at most
  * 104) into the first layer and pack the operands for FABRIC_PREC_FP16 or
  * FABRIC_PREC_BF16 (one small kernel on `stream`). */
@@ -452,7 +485,8 @@ fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch 
                                       void *stream);
 
 /* Copy the gradient [decoder | encoder] of the last fabric_paper_train_step
- * to host memory (fabric_paper_param_count(width, 0) + (.., 1) floats).
+ * to host memory (fabric_paper_structure_param_count(width, ablation) +
+ * fabric_paper_param_count(width, 1) floats).
  * Synchronous.  Used by the tests. */
 fabric_status fabric_paper_get_gradient(fabric_ctx *ctx, float *grad);
 

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "FABRIC_OK", 1: "FABRIC_ERR_INVALID_ARG", 2: "FABRIC_ERR_CUDA
                 4: "FABRIC_ERR_TIMEOUT", 5: "FABRIC_ERR_IO", 6: "FABRIC_ERR_UNSUPPORTED", 7: "FABRIC_ERR_DEVICE"}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
 LOSS = {"eq11": 0, "rendered": 1}
+PAPER_STRUCTURES = {"full": 0, "no_oneblob": 1, "no_fusion": 2}   # the paper decoder and its two ablations
 
 
 class FabricMaterial(ctypes.Structure):
@@ -120,6 +121,9 @@ def load(path: str | None = None):
         "fabric_paper_encode_params": (st, [vp, vp, i32, vp, vp]),
         "fabric_paper_train_step": (st, [vp, P(FabricTrainBatch), ctypes.c_float, vp, vp]),
         "fabric_paper_get_gradient": (st, [vp, vp]),
+        "fabric_paper_structure_param_count": (i64, [i32, i32]),
+        "fabric_paper_set_structure": (st, [vp, i32, i32, vp, vp]),
+        "fabric_paper_shade_fp32": (st, [vp, P(FabricGBuffer), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import FabricGBuffer, FabricMaterial, FabricTrainBatch, check
+from ._abi import PAPER_STRUCTURES, FabricGBuffer, FabricMaterial, FabricTrainBatch, check
 
 LATENT = 32
 
@@ -290,24 +290,31 @@ class Fabric:
         return d
 
     # ------------------------------- the paper's decoder structure (Sec. 4.2)
-    def paper_set_params(self, width: int, decoder=None, encoder=None):
-        """Parameters of the paper's decoder (width 64 or 128) and its 64-wide
-        latent encoder; a new width needs both."""
-        nd = int(self.lib.fabric_paper_param_count(int(width), 0))
+    def paper_set_params(self, width: int, decoder=None, encoder=None, ablation: str = "full"):
+        """Parameters of the paper's decoder (width 64 or 128; the full
+        structure or one of its ablations, PAPER_STRUCTURES) and its 64-wide
+        latent encoder; a new width or structure needs both."""
+        a = PAPER_STRUCTURES[ablation]
+        nd = int(self.lib.fabric_paper_structure_param_count(int(width), a))
         ne = int(self.lib.fabric_paper_param_count(int(width), 1))
         d = None if decoder is None else np.ascontiguousarray(decoder, np.float32)
         e = None if encoder is None else np.ascontiguousarray(encoder, np.float32)
         if d is not None and d.size != nd:
-            raise ValueError(f"paper decoder of width {width} needs {nd} parameters")
+            raise ValueError(f"paper decoder ({ablation}) of width {width} needs {nd} parameters")
         if e is not None and e.size != ne:
             raise ValueError(f"paper encoder needs {ne} parameters")
-        self._check(self.lib.fabric_paper_set_params(self.h, int(width),
-                                                     None if d is None else d.ctypes.data_as(ctypes.c_void_p),
-                                                     None if e is None else e.ctypes.data_as(ctypes.c_void_p)))
+        self._check(self.lib.fabric_paper_set_structure(self.h, int(width), a,
+                                                        None if d is None else d.ctypes.data_as(ctypes.c_void_p),
+                                                        None if e is None else e.ctypes.data_as(ctypes.c_void_p)))
         self.paper_width = int(width)
+        self.paper_ablation = ablation
+
+    def _paper_n_dec(self) -> int:
+        return int(self.lib.fabric_paper_structure_param_count(self.paper_width,
+                                                               PAPER_STRUCTURES[self.paper_ablation]))
 
     def paper_get_params(self):
-        nd = int(self.lib.fabric_paper_param_count(self.paper_width, 0))
+        nd = self._paper_n_dec()
         ne = int(self.lib.fabric_paper_param_count(self.paper_width, 1))
         d = np.empty(nd, np.float32)
         e = np.empty(ne, np.float32)
@@ -356,11 +363,20 @@ class Fabric:
 
     def paper_gradient(self) -> np.ndarray:
         """The last paper-network training step's gradient [decoder | encoder]."""
-        n = int(self.lib.fabric_paper_param_count(self.paper_width, 0)) + int(
-            self.lib.fabric_paper_param_count(self.paper_width, 1))
+        n = self._paper_n_dec() + int(self.lib.fabric_paper_param_count(self.paper_width, 1))
         out = np.empty(n, np.float32)
         self._check(self.lib.fabric_paper_get_gradient(self.h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def paper_shade_fp32(self, g: GBuffer, latents: torch.Tensor, comps: bool = False, stream=None):
+        """The paper network (any structure) in FP32 on CUDA cores."""
+        rgb = torch.empty((g.n, 3), dtype=torch.float32, device=self.device)
+        cp = torch.empty((g.n, 4), dtype=torch.float32, device=self.device) if comps else None
+        lat = latents.contiguous()
+        gs = g.struct()
+        self._check(self.lib.fabric_paper_shade_fp32(self.h, ctypes.byref(gs), _ptr(lat), _ptr(rgb), _ptr(cp),
+                                                     _stream_handle(stream)))
+        return rgb, cp
 
     # ---------------------------------------------- autograd building blocks
     def decoder_forward(self, g: GBuffer, latents, dec, stream=None):

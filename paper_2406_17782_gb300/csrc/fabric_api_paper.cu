@@ -16,6 +16,7 @@ void paper_release(fabric_ctx *ctx) {
   ctx->d_pn_dec = ctx->d_pn_enc = ctx->d_pn_adam = ctx->d_pn_grad = nullptr;
   ctx->d_pn_blob = nullptr;
   ctx->pn_width = 0;
+  ctx->pn_ablation = 0;
 }
 
 namespace {
@@ -27,6 +28,10 @@ constexpr int kPnMaxMaterials = 104;   // 24 one-blob channels + 104 one-hot col
 bool paper_fits(int w, int n_mat) { return paper_blob_bytes(w, n_mat) + 2048 + 1024 <= 227u * 1024u; }
 
 uint64_t pn_state(const fabric_ctx *ctx) { return ctx->version * 0x9E3779B97F4A7C15ull ^ ctx->pn_version; }
+
+bool ablation_ok(int a) { return a == kPnFull || a == kPnNoOneBlob || a == kPnNoFusion; }
+
+size_t n_dec(const fabric_ctx *ctx) { return (size_t)paper_offsets_ablation(ctx->pn_width, ctx->pn_ablation).total; }
 
 }  // namespace
 }  // namespace fab
@@ -54,14 +59,20 @@ int64_t fabric_paper_param_count(int width, int encoder) {
   return paper_width_ok(width) ? paper_offsets(width).total : -1;
 }
 
-fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *decoder, const float *encoder) {
+int64_t fabric_paper_structure_param_count(int width, int ablation) {
+  return paper_width_ok(width) && ablation_ok(ablation) ? paper_offsets_ablation(width, ablation).total : -1;
+}
+
+fabric_status fabric_paper_set_structure(fabric_ctx *ctx, int width, int ablation, const float *decoder,
+                                         const float *encoder) {
   PN_CHECK_CTX(ctx);
   if (!paper_width_ok(width)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "width must be 64 or 128 (got %d)", width);
-  if (width != ctx->pn_width) {
+  if (!ablation_ok(ablation)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "unknown structure %d", ablation);
+  const size_t nd = (size_t)paper_offsets_ablation(width, ablation).total, ne = (size_t)kPnEncParams;
+  if (width != ctx->pn_width || ablation != ctx->pn_ablation) {
     if (!decoder || !encoder)
-      return fail(ctx, FABRIC_ERR_INVALID_ARG, "a new width needs both decoder and encoder parameters");
+      return fail(ctx, FABRIC_ERR_INVALID_ARG, "a new width or structure needs both decoder and encoder parameters");
     paper_release(ctx);
-    const size_t nd = (size_t)paper_offsets(width).total, ne = (size_t)kPnEncParams;
     if (cudaMalloc(&ctx->d_pn_dec, nd * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&ctx->d_pn_enc, ne * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&ctx->d_pn_adam, 2 * (nd + ne) * sizeof(float)) != cudaSuccess ||
@@ -72,8 +83,8 @@ fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *d
       return fail(ctx, FABRIC_ERR_OOM, "paper network buffers");
     }
     ctx->pn_width = width;
+    ctx->pn_ablation = ablation;
   }
-  const size_t nd = (size_t)paper_offsets(width).total, ne = (size_t)kPnEncParams;
   if (decoder) PN_CUDA(ctx, cudaMemcpy(ctx->d_pn_dec, decoder, nd * sizeof(float), cudaMemcpyHostToDevice), "params");
   if (encoder) PN_CUDA(ctx, cudaMemcpy(ctx->d_pn_enc, encoder, ne * sizeof(float), cudaMemcpyHostToDevice), "params");
   PN_CUDA(ctx, cudaMemset(ctx->d_pn_adam, 0, 2 * (nd + ne) * sizeof(float)), "adam reset");
@@ -84,11 +95,15 @@ fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *d
   return FABRIC_OK;
 }
 
+fabric_status fabric_paper_set_params(fabric_ctx *ctx, int width, const float *decoder, const float *encoder) {
+  return fabric_paper_set_structure(ctx, width, kPnFull, decoder, encoder);
+}
+
 fabric_status fabric_paper_get_params(fabric_ctx *ctx, float *decoder, float *encoder) {
   PN_CHECK_CTX(ctx);
   if (!ctx->pn_width) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network parameters set");
   PN_CUDA(ctx, cudaDeviceSynchronize(), "get params");
-  const size_t nd = (size_t)paper_offsets(ctx->pn_width).total, ne = (size_t)kPnEncParams;
+  const size_t nd = n_dec(ctx), ne = (size_t)kPnEncParams;
   if (decoder) PN_CUDA(ctx, cudaMemcpy(decoder, ctx->d_pn_dec, nd * sizeof(float), cudaMemcpyDeviceToHost), "params");
   if (encoder) PN_CUDA(ctx, cudaMemcpy(encoder, ctx->d_pn_enc, ne * sizeof(float), cudaMemcpyDeviceToHost), "params");
   return FABRIC_OK;
@@ -99,6 +114,9 @@ fabric_status fabric_paper_prepare(fabric_ctx *ctx, const float *latents_dev, fa
   if (prec != FABRIC_PREC_FP16 && prec != FABRIC_PREC_BF16)
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "the paper network runs with FP16 or BF16 operands (got %d)", (int)prec);
   if (!ctx->pn_width) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network parameters set");
+  if (ctx->pn_ablation != kPnFull)
+    return fail(ctx, FABRIC_ERR_UNSUPPORTED, "the tensor-core decoder runs the full structure only; "
+                                             "ablations shade with fabric_paper_shade_fp32");
   if (!latents_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "latents are NULL");
   if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
   if (paper_k1(ctx->n_mat) < 0 || !paper_fits(ctx->pn_width, ctx->n_mat))
@@ -190,12 +208,12 @@ fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch 
   double *loss = loss_dev ? loss_dev
                           : reinterpret_cast<double *>(static_cast<uint8_t *>(work) + need - 256);
   PN_CUDA(ctx,
-          launch_paper_train(ctx->pn_width, q, batch->target, ctx->loss_mode, ctx->d_train_raw, M, ctx->d_pn_dec,
+          launch_paper_train(ctx->pn_width, ctx->pn_ablation, q, batch->target, ctx->loss_mode, ctx->d_train_raw, M, ctx->d_pn_dec,
                              ctx->d_pn_enc, ctx->d_pn_grad, loss, work, ctx->d_status, s),
           "paper network forward/backward");
   ctx->pn_adam_step += 1;
   ctx->pn_version += 1;
-  const size_t nd = (size_t)paper_offsets(ctx->pn_width).total, ne = (size_t)kPnEncParams;
+  const size_t nd = n_dec(ctx), ne = (size_t)kPnEncParams;
   float *m = ctx->d_pn_adam, *v = ctx->d_pn_adam + nd + ne;
   PN_CUDA(ctx,
           launch_adam(ctx->d_pn_dec, (int64_t)nd, ctx->d_pn_enc, (int64_t)ne, ctx->d_pn_grad, m, v, lr,
@@ -204,11 +222,32 @@ fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch 
   return FABRIC_OK;
 }
 
+fabric_status fabric_paper_shade_fp32(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev,
+                                      float *rgb_dev, float *comps_dev, void *stream) {
+  PN_CHECK_CTX(ctx);
+  if (!check_gbuffer(ctx, g)) return FABRIC_ERR_INVALID_ARG;
+  if (!ctx->pn_width) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network parameters set");
+  if (g->n == 0) return FABRIC_OK;
+  if (!latents_dev || !rgb_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "latents or rgb output is NULL");
+  if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
+  if (comps_dev && !is_aligned16(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  const size_t need = paper_forward_work_bytes(ctx->pn_width, g->n);
+  void *work = scratch(ctx, need);
+  if (!work) return fail(ctx, FABRIC_ERR_OOM, "forward scratch (%zu bytes)", need);
+  PN_CUDA(ctx,
+          launch_paper_forward(ctx->pn_width, ctx->pn_ablation, *g, latents_dev, ctx->d_mat, ctx->n_mat,
+                               ctx->d_pn_dec, rgb_dev, comps_dev, work, ctx->d_status,
+                               static_cast<cudaStream_t>(stream)),
+          "paper network FP32 forward");
+  return FABRIC_OK;
+}
+
 fabric_status fabric_paper_get_gradient(fabric_ctx *ctx, float *grad) {
   PN_CHECK_CTX(ctx);
   if (!ctx->pn_width || !grad) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no paper network, or grad is NULL");
   PN_CUDA(ctx, cudaDeviceSynchronize(), "get gradient");
-  const size_t n = (size_t)paper_offsets(ctx->pn_width).total + kPnEncParams;
+  const size_t n = n_dec(ctx) + kPnEncParams;
   PN_CUDA(ctx, cudaMemcpy(grad, ctx->d_pn_grad, n * sizeof(float), cudaMemcpyDeviceToHost), "gradient");
   return FABRIC_OK;
 }

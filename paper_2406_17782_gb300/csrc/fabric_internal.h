@@ -189,6 +189,7 @@ struct fabric_ctx {
   // parameters, Adam moments over [decoder | encoder], packed operands and
   // the state of the last fabric_paper_prepare
   int pn_width = 0;
+  int pn_ablation = 0;              // 0 the full structure, 1 without one-blob, 2 without spatial fusion
   float *d_pn_dec = nullptr;
   float *d_pn_enc = nullptr;
   float *d_pn_adam = nullptr;
@@ -284,9 +285,14 @@ cudaError_t launch_paper_decoder(int width, int precision, const fabric_gbuffer 
 // gradient [decoder | encoder] and the batch loss; and its encoder alone.
 size_t paper_train_work_bytes(int width, int64_t batch, int n_mat);
 int paper_train_max_materials(int width);
-cudaError_t launch_paper_train(int width, const fabric_gbuffer &q, const float *target, int loss_mode,
+cudaError_t launch_paper_train(int width, int ablation, const fabric_gbuffer &q, const float *target, int loss_mode,
                                const fabric_material *raw, int n_mat, const float *dec, const float *enc, float *grad,
                                double *loss, void *work, int *status, cudaStream_t s);
+// Its FP32 forward over a G-buffer (any ablation): components and RGB.
+size_t paper_forward_work_bytes(int width, int64_t n);
+cudaError_t launch_paper_forward(int width, int ablation, const fabric_gbuffer &g, const float *z,
+                                 const DevMaterial *mats, int n_mat, const float *dec, float *rgb, float *comps,
+                                 void *work, int *status, cudaStream_t s);
 cudaError_t launch_paper_encoder(const fabric_material *raw, int n_mat, const float *enc, float *z, cudaStream_t s);
 cudaError_t launch_error_stats(const float *a, const float *b, int64_t n, const float *w, int group, int w_stride,
                                double *out, void *work, cudaStream_t s);

@@ -48,6 +48,44 @@ __host__ __device__ constexpr PaperOffsets paper_offsets(int w) {
   return o;
 }
 
+// Ablations of the structure (Sec. 6.3): the spatial inputs unencoded
+// (frac u, frac v, t: S1 becomes [W][67]), or no spatial fusion (no S1, s1,
+// S2, s2; A1 becomes [W][93] over [z | one-blob | wi | wo.xy]).
+constexpr int kPnFull = 0, kPnNoOneBlob = 1, kPnNoFusion = 2;
+
+__host__ __device__ constexpr int paper_spatial_channels(int ablation) { return ablation == kPnNoOneBlob ? 3 : kPnBlob; }
+
+// Offsets of an ablation's parameters; the absent layers' offsets are -1.
+__host__ __device__ constexpr PaperOffsets paper_offsets_ablation(int w, int ablation) {
+  if (ablation == kPnFull) return paper_offsets(w);
+  PaperOffsets o{};
+  int at = 0;
+  if (ablation == kPnNoOneBlob) {
+    o.S1 = 0;
+    o.s1 = o.S1 + w * (kPnLatent + 3);
+    o.S2 = o.s1 + w;
+    o.s2 = o.S2 + w * w;
+    o.A1 = o.s2 + w;
+    o.a1 = o.A1 + w * (w + kPnAng);
+    at = o.a1 + w;
+  } else {
+    o.S1 = o.s1 = o.S2 = o.s2 = -1;
+    o.A1 = 0;
+    o.a1 = o.A1 + w * (kPnLatent + kPnBlob + kPnAng);
+    at = o.a1 + w;
+  }
+  o.A2 = at;
+  o.a2 = o.A2 + w * w;
+  o.A3 = o.a2 + w;
+  o.a3 = o.A3 + w * w;
+  o.A4 = o.a3 + w;
+  o.a4 = o.A4 + w * w;
+  o.A5 = o.a4 + w;
+  o.a5 = o.A5 + 4 * w;
+  o.total = o.a5 + 4;
+  return o;
+}
+
 // Encoder with a 64-wide latent (same layout as the workload's encoder).
 constexpr int kPnEncParams = 128 * 22 + 128 + 128 * 128 + 128 + kPnLatent * 128 + kPnLatent;
 

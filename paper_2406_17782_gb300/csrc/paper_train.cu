@@ -149,27 +149,64 @@ __device__ __forceinline__ void pn_blob_fp32(float u, float v, float r, float *o
   }
 }
 
-// X0[b] = [z_mat (64) | one-blob (24)], XA[b][W..W+4] = (wi, wo.xy).
-__global__ void pn_inputs_kernel(fabric_gbuffer g, const float *__restrict__ z, int n_lat, int W,
-                                 float *__restrict__ X0, float *__restrict__ XA, int *status) {
+// X0[b] = [z_mat (64) | spatial channels (24 one-blob, or 3 unencoded)]
+// with row stride ld0, and the angular inputs (wi, wo.xy) at columns
+// ang0..ang0+4 of XA (row stride lda).  Without the spatial fusion X0 is
+// the front of XA itself.
+__global__ void pn_inputs_kernel(fabric_gbuffer g, const float *__restrict__ z, int n_lat, int ablation,
+                                 float *__restrict__ X0, int ld0, float *__restrict__ XA, int lda, int ang0,
+                                 int *status) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= g.n) return;
   int m = g.material[b];
-  float *x = X0 + b * (kPnLatent + kPnBlob);
-  float *xa = XA + b * (W + kPnAng);
+  float *x = X0 + b * ld0;
+  float *xa = XA + b * lda;
+  const int ks = paper_spatial_channels(ablation);
   if (m >= n_lat) {
     atomicOr(status, kStatusBadMaterial);
-    for (int k = 0; k < kPnLatent + kPnBlob; ++k) x[k] = 0.0f;
-    for (int k = 0; k < kPnAng; ++k) xa[W + k] = 0.0f;
+    for (int k = 0; k < kPnLatent + ks; ++k) x[k] = 0.0f;
+    for (int k = 0; k < kPnAng; ++k) xa[ang0 + k] = 0.0f;
     return;
   }
   for (int k = 0; k < kPnLatent; ++k) x[k] = z[(int64_t)m * kPnLatent + k];
-  pn_blob_fp32(g.u[b], g.v[b], g.radius[b], x + kPnLatent);
-  xa[W + 0] = g.wi[3 * b];
-  xa[W + 1] = g.wi[3 * b + 1];
-  xa[W + 2] = g.wi[3 * b + 2];
-  xa[W + 3] = g.wo[3 * b];
-  xa[W + 4] = g.wo[3 * b + 1];
+  if (ablation == kPnNoOneBlob) {
+    const float u = g.u[b], v = g.v[b];
+    x[kPnLatent + 0] = u - floorf(u);
+    x[kPnLatent + 1] = v - floorf(v);
+    x[kPnLatent + 2] = (logf(fmaxf(g.radius[b], kRFloor)) - kPnLnRLo) * kPnInvLnSpan;
+  } else {
+    pn_blob_fp32(g.u[b], g.v[b], g.radius[b], x + kPnLatent);
+  }
+  xa[ang0 + 0] = g.wi[3 * b];
+  xa[ang0 + 1] = g.wi[3 * b + 1];
+  xa[ang0 + 2] = g.wi[3 * b + 2];
+  xa[ang0 + 3] = g.wo[3 * b];
+  xa[ang0 + 4] = g.wo[3 * b + 1];
+}
+
+// Components (C = max(0, y), S = max(0, expm1(y) / 100), the inverse of
+// Eq. 9) and RGB by Eq. 8 from the raw head y [n][4].
+__global__ void pn_head_kernel(const float *__restrict__ Y, const uint16_t *__restrict__ mat, int64_t n,
+                               const DevMaterial *__restrict__ mats, int n_mat, float *__restrict__ rgb,
+                               float *__restrict__ comps) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int m = mat[b];
+  float c4[4];
+  if (m >= n_mat) {
+    c4[0] = c4[1] = c4[2] = c4[3] = __int_as_float(0x7FC00000);
+  } else {
+    c4[0] = fmaxf(0.0f, Y[4 * b]);
+    c4[1] = fmaxf(0.0f, Y[4 * b + 1]);
+    c4[2] = fmaxf(0.0f, expm1f(Y[4 * b + 2]) / kSpecK);
+    c4[3] = fmaxf(0.0f, expm1f(Y[4 * b + 3]) / kSpecK);
+  }
+  if (comps) reinterpret_cast<float4 *>(comps)[b] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+  if (rgb) {
+    const DevMaterial &M = mats[m < n_mat ? m : 0];
+    for (int ch = 0; ch < 3; ++ch)
+      rgb[3 * b + ch] = M.kd[0][ch] * c4[0] + M.kd[1][ch] * c4[1] + M.ks[0][ch] * c4[2] + M.ks[1][ch] * c4[3];
+  }
 }
 
 // d loss / d y and the loss of each query (Eq. 11 or the rendered option);
@@ -226,9 +263,11 @@ __global__ void pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = col[(int64_t)(r + q) * W];   // eight loads in flight
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[smat[r + q] * W + d] += v[q];
+    for (int q = 0; q < 8; ++q)
+      if (smat[r + q] < n_mat) acc[smat[r + q] * W + d] += v[q];   // a bad index is flagged by the inputs kernel
   }
-  for (; r < rows; ++r) acc[smat[r] * W + d] += col[(int64_t)r * W];
+  for (; r < rows; ++r)
+    if (smat[r] < n_mat) acc[smat[r] * W + d] += col[(int64_t)r * W];
   float *out = part + (int64_t)blockIdx.x * n_mat * W;
   for (int m = 0; m < n_mat; ++m) out[m * W + d] = acc[m * W + d];
 }
@@ -398,29 +437,82 @@ int paper_train_max_materials(int w) { return (int)((200 * 1024) / (w * 4)); }
 size_t paper_train_work_bytes(int w, int64_t B, int n_mat) {
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
   const int64_t segs = (B + kSumRows - 1) / kSumRows;
+  const int ka_max = kPnLatent + kPnBlob + kPnAng > w + kPnAng ? kPnLatent + kPnBlob + kPnAng : w + kPnAng;
   size_t f = 0;
   f += (size_t)B * (kPnLatent + kPnBlob);         // X0
   f += (size_t)B * w;                             // H1
-  f += (size_t)B * (w + kPnAng);                  // XA
+  f += (size_t)B * ka_max;                        // XA
   f += 4 * (size_t)B * w;                         // K1..K4
   f += 2 * (size_t)B * 4;                         // Y, DY
   f += 3 * (size_t)B * w;                         // three gradient buffers
-  f += (size_t)chunks * w * (w + kPnAng + 1);     // weight-gradient partials (largest layer)
-  f += (size_t)chunks * w * (kPnLatent + kPnBlob + 1);
+  f += (size_t)chunks * w * (ka_max + 1);         // weight-gradient partials (largest layer)
   f += (size_t)n_mat * segs * w + (size_t)n_mat * w + (size_t)n_mat * kPnLatent;   // latent sums, G, dz
   f += (size_t)n_mat * (kEI + 4 * kEH + kPnLatent);                                // encoder
-  f += 64 * 8;
-  return f * 4 + ((size_t)(B + 255) / 256) * 8 + 4096;
+  f += 64 * 32;
+  return f * 4 + ((size_t)(B + 255) / 256) * 8 + 8192;
 }
+
+namespace {
+
+// Activation buffers of one pass over a batch of B queries.
+struct PnPass {
+  int w, ablation, KX0, KA;
+  bool fusion;
+  float *X0, *H1, *XA, *K1, *K2, *K3, *K4, *Y;
+};
+
+template <class Take>
+PnPass pn_pass_buffers(int w, int ablation, int64_t B, Take take) {
+  PnPass P;
+  P.w = w;
+  P.ablation = ablation;
+  P.fusion = ablation != kPnNoFusion;
+  P.KX0 = kPnLatent + paper_spatial_channels(ablation);
+  P.KA = P.fusion ? w + kPnAng : kPnLatent + kPnBlob + kPnAng;
+  P.XA = take((size_t)B * P.KA);
+  P.X0 = P.fusion ? take((size_t)B * P.KX0) : P.XA;
+  P.H1 = P.fusion ? take((size_t)B * w) : nullptr;
+  P.K1 = take((size_t)B * w);
+  P.K2 = take((size_t)B * w);
+  P.K3 = take((size_t)B * w);
+  P.K4 = take((size_t)B * w);
+  P.Y = take((size_t)B * 4);
+  return P;
+}
+
+// Inputs and the forward pass of the structure (or its ablation): the raw
+// head in P.Y.
+cudaError_t pn_forward(const PnPass &P, const fabric_gbuffer &q, const float *z, int n_mat, const float *dec,
+                       int *status, cudaStream_t s) {
+  const PaperOffsets o = paper_offsets_ablation(P.w, P.ablation);
+  const int64_t B = q.n;
+  const int w = P.w;
+  cudaError_t e;
+  const int ang0 = P.fusion ? w : kPnLatent + kPnBlob;
+  pn_inputs_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(q, z, n_mat, P.ablation, P.X0, P.fusion ? P.KX0 : P.KA,
+                                                              P.XA, P.KA, ang0, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (P.fusion) {
+    if ((e = fwd(P.X0, P.KX0, P.KX0, dec + o.S1, dec + o.s1, w, B, P.H1, w, nullptr, 0, true, s)) != cudaSuccess)
+      return e;
+    if ((e = fwd(P.H1, w, w, dec + o.S2, dec + o.s2, w, B, P.XA, P.KA, nullptr, 0, true, s)) != cudaSuccess) return e;
+  }
+  if ((e = fwd(P.XA, P.KA, P.KA, dec + o.A1, dec + o.a1, w, B, P.K1, w, nullptr, 0, true, s)) != cudaSuccess) return e;
+  if ((e = fwd(P.K1, w, w, dec + o.A2, dec + o.a2, w, B, P.K2, w, nullptr, 0, true, s)) != cudaSuccess) return e;
+  if ((e = fwd(P.K2, w, w, dec + o.A3, dec + o.a3, w, B, P.K3, w, P.K1, w, true, s)) != cudaSuccess) return e;   // skip
+  if ((e = fwd(P.K3, w, w, dec + o.A4, dec + o.a4, w, B, P.K4, w, nullptr, 0, true, s)) != cudaSuccess) return e;
+  return fwd(P.K4, w, w, dec + o.A5, dec + o.a5, 4, B, P.Y, 4, nullptr, 0, false, s);
+}
+
+}  // namespace
 
 // One step's forward, loss and backward: grad [decoder | encoder] and the
 // batch loss; raw = device copy of the training materials.
-cudaError_t launch_paper_train(int w, const fabric_gbuffer &q, const float *target, int loss_mode,
+cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, const float *target, int loss_mode,
                                const fabric_material *raw, int n_mat, const float *dec, const float *enc,
                                float *grad, double *loss, void *work, int *status, cudaStream_t s) {
-  const PaperOffsets o = paper_offsets(w);
+  const PaperOffsets o = paper_offsets_ablation(w, ablation);
   const int64_t B = q.n;
-  const int KX0 = kPnLatent + kPnBlob, KA = w + kPnAng;
   const int segs = (int)((B + kSumRows - 1) / kSumRows);
   float *p = static_cast<float *>(work);
   auto take = [&](size_t nfl) {
@@ -428,13 +520,16 @@ cudaError_t launch_paper_train(int w, const fabric_gbuffer &q, const float *targ
     p += (nfl + 63) & ~size_t(63);
     return r;
   };
-  float *X0 = take((size_t)B * KX0), *H1 = take((size_t)B * w), *XA = take((size_t)B * KA);
-  float *K1 = take((size_t)B * w), *K2 = take((size_t)B * w), *K3 = take((size_t)B * w), *K4 = take((size_t)B * w);
-  float *Y = take((size_t)B * 4), *DY = take((size_t)B * 4);
+  const PnPass P = pn_pass_buffers(w, ablation, B, take);
+  const int KX0 = P.KX0, KA = P.KA;
+  float *DY = take((size_t)B * 4);
   float *D1 = take((size_t)B * w), *D2 = take((size_t)B * w), *D3 = take((size_t)B * w);
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
-  float *part = take((size_t)chunks * w * (KX0 > KA ? KX0 + 1 : KA + 1));
-  float *msum = take((size_t)n_mat * segs * w), *G = take((size_t)n_mat * w), *dz = take((size_t)n_mat * kPnLatent);
+  float *part = take((size_t)chunks * w * ((KX0 > KA ? KX0 : KA) + 1));
+  // per-material latent sums are taken over the first layer's gradient
+  // (width W), or directly over the latent part of dXA (64) without fusion
+  const int ws = P.fusion ? w : kPnLatent;
+  float *msum = take((size_t)n_mat * segs * ws), *G = take((size_t)n_mat * ws), *dz = take((size_t)n_mat * kPnLatent);
   float *F = take((size_t)n_mat * kEI), *EH1 = take((size_t)n_mat * kEH), *EH2 = take((size_t)n_mat * kEH);
   float *DA1 = take((size_t)n_mat * kEH), *DA2 = take((size_t)n_mat * kEH), *z = take((size_t)n_mat * kPnLatent);
   double *lpart = reinterpret_cast<double *>(take((size_t)((B + 255) / 256) * 2));
@@ -445,53 +540,54 @@ cudaError_t launch_paper_train(int w, const fabric_gbuffer &q, const float *targ
     e = (x);                          \
     if (e != cudaSuccess) return e;   \
   } while (0)
-  // ---- encoder and inputs
+  // ---- encoder, inputs and forward
   pn_enc_fwd_kernel<<<n_mat, kEH, 0, s>>>(raw, enc, F, EH1, EH2, z);
   PN_TRY(cudaGetLastError());
-  pn_inputs_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(q, z, n_mat, w, X0, XA, status);
-  PN_TRY(cudaGetLastError());
-  // ---- forward
-  PN_TRY(fwd(X0, KX0, KX0, dec + o.S1, dec + o.s1, w, B, H1, w, nullptr, 0, true, s));
-  PN_TRY(fwd(H1, w, w, dec + o.S2, dec + o.s2, w, B, XA, KA, nullptr, 0, true, s));
-  PN_TRY(fwd(XA, KA, KA, dec + o.A1, dec + o.a1, w, B, K1, w, nullptr, 0, true, s));
-  PN_TRY(fwd(K1, w, w, dec + o.A2, dec + o.a2, w, B, K2, w, nullptr, 0, true, s));
-  PN_TRY(fwd(K2, w, w, dec + o.A3, dec + o.a3, w, B, K3, w, K1, w, true, s));   // + k1: the skip
-  PN_TRY(fwd(K3, w, w, dec + o.A4, dec + o.a4, w, B, K4, w, nullptr, 0, true, s));
-  PN_TRY(fwd(K4, w, w, dec + o.A5, dec + o.a5, 4, B, Y, 4, nullptr, 0, false, s));
+  PN_TRY(pn_forward(P, q, z, n_mat, dec, status, s));
   // ---- loss
   const int lblocks = (int)((B + 255) / 256);
-  pn_loss_kernel<<<lblocks, 256, 0, s>>>(Y, target, q.wi, B, loss_mode, 1.0f / (float)B, DY, lpart);
+  pn_loss_kernel<<<lblocks, 256, 0, s>>>(P.Y, target, q.wi, B, loss_mode, 1.0f / (float)B, DY, lpart);
   PN_TRY(cudaGetLastError());
   pn_loss_final_kernel<<<1, 32, 0, s>>>(lpart, lblocks, loss);
   PN_TRY(cudaGetLastError());
   // ---- backward (D1..D3 rotate as dq4, dq3, dq2, dq1, dg2, dg1)
-  PN_TRY(wgrad(DY, 4, 4, K4, w, w, B, part, gd + o.A5, gd + o.a5, s));
-  PN_TRY(bwd_in(DY, 4, 4, dec + o.A5, w, w, B, D1, w, nullptr, 0, K4, w, s));          // dq4
-  PN_TRY(wgrad(D1, w, w, K3, w, w, B, part, gd + o.A4, gd + o.a4, s));
-  PN_TRY(bwd_in(D1, w, w, dec + o.A4, w, w, B, D2, w, nullptr, 0, K3, w, s));          // dq3
-  PN_TRY(wgrad(D2, w, w, K2, w, w, B, part, gd + o.A3, gd + o.a3, s));
-  PN_TRY(bwd_in(D2, w, w, dec + o.A3, w, w, B, D3, w, nullptr, 0, K2, w, s));          // dq2
-  PN_TRY(wgrad(D3, w, w, K1, w, w, B, part, gd + o.A2, gd + o.a2, s));
-  PN_TRY(bwd_in(D3, w, w, dec + o.A2, w, w, B, D1, w, D2, w, K1, w, s));               // dq1 (+ dq3 through the skip)
-  PN_TRY(wgrad(D1, w, w, XA, KA, KA, B, part, gd + o.A1, gd + o.a1, s));
-  PN_TRY(bwd_in(D1, w, w, dec + o.A1, KA, w, B, D2, w, nullptr, 0, XA, KA, s));        // dg2
-  PN_TRY(wgrad(D2, w, w, H1, w, w, B, part, gd + o.S2, gd + o.s2, s));
-  PN_TRY(bwd_in(D2, w, w, dec + o.S2, w, w, B, D3, w, nullptr, 0, H1, w, s));          // dg1
-  PN_TRY(wgrad(D3, w, w, X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
-  // ---- latent gradient: per-material sums of dg1, times S1's latent block
+  PN_TRY(wgrad(DY, 4, 4, P.K4, w, w, B, part, gd + o.A5, gd + o.a5, s));
+  PN_TRY(bwd_in(DY, 4, 4, dec + o.A5, w, w, B, D1, w, nullptr, 0, P.K4, w, s));          // dq4
+  PN_TRY(wgrad(D1, w, w, P.K3, w, w, B, part, gd + o.A4, gd + o.a4, s));
+  PN_TRY(bwd_in(D1, w, w, dec + o.A4, w, w, B, D2, w, nullptr, 0, P.K3, w, s));          // dq3
+  PN_TRY(wgrad(D2, w, w, P.K2, w, w, B, part, gd + o.A3, gd + o.a3, s));
+  PN_TRY(bwd_in(D2, w, w, dec + o.A3, w, w, B, D3, w, nullptr, 0, P.K2, w, s));          // dq2
+  PN_TRY(wgrad(D3, w, w, P.K1, w, w, B, part, gd + o.A2, gd + o.a2, s));
+  PN_TRY(bwd_in(D3, w, w, dec + o.A2, w, w, B, D1, w, D2, w, P.K1, w, s));               // dq1 (+ dq3 through the skip)
+  PN_TRY(wgrad(D1, w, w, P.XA, KA, KA, B, part, gd + o.A1, gd + o.a1, s));
+  const float *lat_grad;   // rows whose per-material sums give dz (fusion: times S1's latent block)
+  if (P.fusion) {
+    PN_TRY(bwd_in(D1, w, w, dec + o.A1, KA, w, B, D2, w, nullptr, 0, P.XA, KA, s));      // dg2
+    PN_TRY(wgrad(D2, w, w, P.H1, w, w, B, part, gd + o.S2, gd + o.s2, s));
+    PN_TRY(bwd_in(D2, w, w, dec + o.S2, w, w, B, D3, w, nullptr, 0, P.H1, w, s));        // dg1
+    PN_TRY(wgrad(D3, w, w, P.X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
+    lat_grad = D3;
+  } else {
+    // dXA[:, :64] = dq1 A1[:, :64]: the latent columns of the angular input
+    PN_TRY(bwd_in(D1, w, w, dec + o.A1, KA, kPnLatent, B, D2, kPnLatent, nullptr, 0, nullptr, 0, s));
+    lat_grad = D2;
+  }
+  // ---- latent gradient: per-material sums in row order
   {
-    const size_t smem = (size_t)n_mat * w * sizeof(float);
+    const size_t smem = (size_t)n_mat * ws * sizeof(float);
     PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), 200 * 1024));
-    pn_material_sums_kernel<<<segs, w, smem, s>>>(q.material, B, D3, w, n_mat, msum);
+    pn_material_sums_kernel<<<segs, ws, smem, s>>>(q.material, B, lat_grad, ws, n_mat, msum);
     PN_TRY(cudaGetLastError());
-    pn_segment_total_kernel<<<(n_mat * w + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, w, G);
+    pn_segment_total_kernel<<<(n_mat * ws + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, ws, P.fusion ? G : dz);
     PN_TRY(cudaGetLastError());
-    // dz[m][k] = sum_j G[m][j] S1[j][k], k < 64
-    Epi ep{};
-    ep.mode = 1;
-    ep.out = dz;
-    ep.ld_out = kPnLatent;
-    PN_TRY((gemm<true, false, false>(G, w, 1, dec + o.S1, 1, KX0, n_mat, kPnLatent, w, w, 1, ep, s)));
+    if (P.fusion) {
+      // dz[m][k] = sum_j G[m][j] S1[j][k], k < 64
+      Epi ep{};
+      ep.mode = 1;
+      ep.out = dz;
+      ep.ld_out = kPnLatent;
+      PN_TRY((gemm<true, false, false>(G, w, 1, dec + o.S1, 1, KX0, n_mat, kPnLatent, w, w, 1, ep, s)));
+    }
   }
   // ---- encoder backward
   pn_enc_bwd_kernel<<<n_mat, kEH, 0, s>>>(enc, EH1, EH2, dz, DA1, DA2);
@@ -500,6 +596,29 @@ cudaError_t launch_paper_train(int w, const fabric_gbuffer &q, const float *targ
   PN_TRY(cudaGetLastError());
 #undef PN_TRY
   return cudaSuccess;
+}
+
+size_t paper_forward_work_bytes(int w, int64_t B) {
+  const int ka_max = kPnLatent + kPnBlob + kPnAng > w + kPnAng ? kPnLatent + kPnBlob + kPnAng : w + kPnAng;
+  return ((size_t)B * (kPnLatent + kPnBlob + ka_max + 5 * (size_t)w + 4) + 64 * 16) * 4 + 4096;
+}
+
+// FP32 forward of the structure (or an ablation) over a G-buffer, with
+// per-material latents z [n_mat][64]: components and RGB.
+cudaError_t launch_paper_forward(int w, int ablation, const fabric_gbuffer &g, const float *z,
+                                 const DevMaterial *mats, int n_mat, const float *dec, float *rgb, float *comps,
+                                 void *work, int *status, cudaStream_t s) {
+  float *p = static_cast<float *>(work);
+  auto take = [&](size_t nfl) {
+    float *r = p;
+    p += (nfl + 63) & ~size_t(63);
+    return r;
+  };
+  const PnPass P = pn_pass_buffers(w, ablation, g.n, take);
+  cudaError_t e = pn_forward(P, g, z, n_mat, dec, status, s);
+  if (e != cudaSuccess) return e;
+  pn_head_kernel<<<(unsigned)((g.n + 255) / 256), 256, 0, s>>>(P.Y, g.material, g.n, mats, n_mat, rgb, comps);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_paper_encoder(const fabric_material *raw, int n_mat, const float *enc, float *z, cudaStream_t s) {

@@ -50,6 +50,27 @@ def test_param_counts(lib):
     assert len(W.decoder_init()) == 13188 and len(W.encoder_init()) == 23584
 
 
+def test_paper_structure_param_counts(lib):
+    """The library's layout of the paper decoder and its two ablations
+    equals the oracle's (and the initialisers'), at both widths; unknown
+    widths and structures give -1."""
+    from oracle import mlp as M
+    from oracle import paper_net as PN
+    from paper_2406_17782_gb300._abi import PAPER_STRUCTURES
+    abl = {"full": PN.FULL, "no_oneblob": PN.NO_ONEBLOB, "no_fusion": PN.NO_FUSION}
+    for w in PN.WIDTHS:
+        assert lib.fabric_paper_param_count(w, 0) == lib.fabric_paper_structure_param_count(w, 0)
+        for name, a in PAPER_STRUCTURES.items():
+            n = M.n_params(PN.dec_shapes(w, abl[name]))
+            assert lib.fabric_paper_structure_param_count(w, a) == n == len(W.paper_decoder_init(w, ablation=name))
+    # S1 [64][67] (no one-blob) has 21 * 64 fewer weights; A1 [64][93] in
+    # place of S1, S2 and A1 [64][69] (no fusion)
+    assert lib.fabric_paper_structure_param_count(64, 1) == lib.fabric_paper_structure_param_count(64, 0) - 21 * 64
+    assert lib.fabric_paper_structure_param_count(64, 2) == 27076 - (64 * 88 + 64 + 64 * 64 + 64) - 64 * 69 + 64 * 93
+    assert lib.fabric_paper_structure_param_count(96, 0) == -1
+    assert lib.fabric_paper_structure_param_count(64, 3) == -1
+
+
 def test_status_strings_and_null_context(lib):
     assert lib.fabric_status_string(0) == b"FABRIC_OK"
     assert lib.fabric_status_string(6) == b"FABRIC_ERR_UNSUPPORTED"

@@ -412,17 +412,22 @@ def random_latents(n_mat: int, seed: int = 5, scale: float = 1.0, dim: int = 32)
     return (scale * rng.standard_normal((n_mat, dim))).astype(np.float32)
 
 
-def paper_decoder_layers(width: int):
-    """(out, in) of the paper decoder's seven layers: S1, S2, A1..A5."""
-    return [(width, 64 + 24), (width, width), (width, width + 5), (width, width), (width, width),
+def paper_decoder_layers(width: int, ablation: str = "full"):
+    """(out, in) of the paper decoder's layers: S1, S2, A1..A5; without the
+    one-blob encoding S1 takes 64 + 3 inputs, without the spatial fusion S1
+    and S2 are absent and A1 takes 64 + 24 + 5."""
+    if ablation == "no_fusion":
+        return [(width, 64 + 24 + 5)] + [(width, width)] * 3 + [(4, width)]
+    k0 = 64 + (3 if ablation == "no_oneblob" else 24)
+    return [(width, k0), (width, width), (width, width + 5), (width, width), (width, width),
             (width, width), (4, width)]
 
 
 PAPER_ENC_LAYERS = [(128, 22), (128, 128), (64, 128)]
 
 
-def paper_decoder_init(width: int, seed: int = 13, weight_bound: str = "he") -> np.ndarray:
-    layers = paper_decoder_layers(width)
+def paper_decoder_init(width: int, seed: int = 13, weight_bound: str = "he", ablation: str = "full") -> np.ndarray:
+    layers = paper_decoder_layers(width, ablation)
     return init_params(sum(o * i + o for o, i in layers), [i for _, i in layers], [(o * i, o) for o, i in layers],
                        seed, weight_bound)
 
