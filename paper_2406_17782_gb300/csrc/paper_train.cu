@@ -525,7 +525,9 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   float *DY = take((size_t)B * 4);
   float *D1 = take((size_t)B * w), *D2 = take((size_t)B * w), *D3 = take((size_t)B * w);
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
-  float *part = take((size_t)chunks * w * ((KX0 > KA ? KX0 : KA) + 1));
+  // weight-gradient partials of the widest layer: K = KX0 (S1), KA (A1) or W (S2, A2..A4)
+  const int k_max = KX0 > KA ? (KX0 > w ? KX0 : w) : (KA > w ? KA : w);
+  float *part = take((size_t)chunks * w * (k_max + 1));
   // per-material latent sums are taken over the first layer's gradient
   // (width W), or directly over the latent part of dXA (64) without fusion
   const int ws = P.fusion ? w : kPnLatent;
