@@ -424,9 +424,13 @@ fabric_status fabric_paper_get_params(fabric_ctx *ctx, float *decoder, float *en
  * structure (FABRIC_PAPER_FULL, what fabric_paper_set_params sets):
  *   FABRIC_PAPER_NO_ONEBLOB: the footprint's three inputs enter S1 as they
  *     are, [z (64) | frac u | frac v | t] -> S1[W][67];
- *   FABRIC_PAPER_NO_FUSION: S1 and S2 are left out and the angular decoder
- *     takes [z (64) | one-blob (24) | wi | wo.xy] -> A1[W][93].
- * Parameter layout otherwise as above, absent layers omitted.  Ablations
+ *   FABRIC_PAPER_NO_FUSION: space and angle are queried together; as the
+ *     section adds hidden layers to the angular decoder for a fair
+ *     comparison, the S1 and S2 slots hold its two added first layers,
+ *     [z (64) | one-blob (24) | wi | wo.xy] -> S1[W][93] -> S2[W][W], and
+ *     A1 becomes [W][W] over their output (same size as the full
+ *     structure).
+ * Parameter layout otherwise as above.  Ablations
  * train (fabric_paper_train_step) and shade in FP32
  * (fabric_paper_shade_fp32); the tensor-core decoder (fabric_paper_prepare,
  * fabric_paper_shade_*) refuses them with FABRIC_ERR_UNSUPPORTED.

@@ -33,8 +33,11 @@ interface with the CUDA library, each side implementing it on its own):
   A3[W][W] a3[W] A4[W][W] a4[W] A5[4][W] a5[4]
 Ablations (Sec. 6.3 varies the one-blob encoding and the spatial fusion):
 without the one-blob encoding S1 is [W][67] over [z | frac u, frac v, t];
-without the spatial fusion S1, s1, S2, s2 are absent and A1 is [W][93] over
-[z | one-blob | wi | wo.xy].
+without the spatial fusion the angular decoder gains two hidden layers in
+their place (Sec. 6.3 adds hidden layers for a fair comparison):
+H1[W][93] h1[W] H2[W][W] h2[W] over [z | one-blob | wi | wo.xy], then
+A1[W][W] a1[W] over their output and A2..a5 as above (same size as the
+full structure).
 Encoder: E1[128][22] e1[128] E2[128][128] e2[128] E3[64][128] e3[64], the
 workload's residual encoder (oracle.mlp) with a 64-wide output.
 """
@@ -60,8 +63,11 @@ WIDTHS = (64, 128)
 # Ablations of the structure (Sec. 6.3 studies the one-blob encoding and the
 # spatial fusion): FULL is the structure above; NO_ONEBLOB feeds the three
 # spatial inputs (frac u, frac v, size coordinate t) unencoded; NO_FUSION
-# drops the two spatial-fusion layers and feeds [z | one-blob | angular]
-# straight into the angular decoder.
+# queries space and angle together: the section keeps the comparison fair by
+# giving the angular decoder more hidden layers when the fusion goes, and
+# here the two fusion layers become the angular decoder's first two hidden
+# layers H1, H2 over [z | one-blob | angular], then A1 [W][W] over their
+# output (same depth and parameter count as FULL).
 FULL, NO_ONEBLOB, NO_FUSION = 0, 1, 2
 N_RAW = 3
 
@@ -74,9 +80,16 @@ def dec_shapes(w: int, ablation: int = FULL):
     tail = [("A2", (w, w)), ("a2", (w,)), ("A3", (w, w)), ("a3", (w,)), ("A4", (w, w)), ("a4", (w,)),
             ("A5", (mlp.N_OUT, w)), ("a5", (mlp.N_OUT,))]
     if ablation == NO_FUSION:
-        return [("A1", (w, LATENT + N_BLOB + N_ANG)), ("a1", (w,))] + tail
+        return [("H1", (w, LATENT + N_BLOB + N_ANG)), ("h1", (w,)), ("H2", (w, w)), ("h2", (w,)),
+                ("A1", (w, w)), ("a1", (w,))] + tail
     return [("S1", (w, LATENT + n_spatial(ablation))), ("s1", (w,)), ("S2", (w, w)), ("s2", (w,)),
             ("A1", (w, w + N_ANG)), ("a1", (w,))] + tail
+
+
+def _front(p: dict):
+    """Names of the two layers before A1: the spatial fusion (S1, S2), or
+    the angular decoder's added hidden layers without it (H1, H2)."""
+    return ("S1", "s1", "S2", "s2") if "S1" in p else ("H1", "h1", "H2", "h2")
 
 
 ENC_SHAPES = [("E1", (mlp.ENC_HIDDEN, mlp.ENC_IN)), ("e1", (mlp.ENC_HIDDEN,)),
@@ -138,17 +151,18 @@ def angular_features(wi, wo) -> np.ndarray:
 def decoder_forward(p: dict, z: np.ndarray, blob: np.ndarray, ang: np.ndarray, keep: bool = False):
     """Raw head y [n, 4] from per-point latents z [n, 64], spatial channels
     [n, 24] (or [n, 3] without the one-blob encoding) and angular inputs
-    [n, 5]; without S1 (NO_FUSION) the angular decoder takes
-    [z | spatial | angular] directly."""
-    x0 = np.concatenate([np.asarray(z, np.float64), blob], axis=1)
+    [n, 5].  With the spatial fusion the angular inputs join its output at
+    A1; without it (H1, H2 in place of S1, S2) they enter the first layer
+    with z and the spatial channels."""
+    fusion = "S1" in p
+    W1, b1, W2, b2 = _front(p)
+    z = np.asarray(z, np.float64)
+    x0 = np.concatenate([z, blob] if fusion else [z, blob, ang], axis=1)
     c = dict(x0=x0)
-    if "S1" in p:
-        c["g1"] = x0 @ p["S1"].T + p["s1"]
-        c["h1"] = lrelu(c["g1"])
-        c["g2"] = c["h1"] @ p["S2"].T + p["s2"]
-        xa = np.concatenate([lrelu(c["g2"]), ang], axis=1)
-    else:
-        xa = np.concatenate([x0, ang], axis=1)
+    c["g1"] = x0 @ p[W1].T + p[b1]
+    c["h1"] = lrelu(c["g1"])
+    c["g2"] = c["h1"] @ p[W2].T + p[b2]
+    xa = np.concatenate([lrelu(c["g2"]), ang], axis=1) if fusion else lrelu(c["g2"])
     c["xa"] = xa
     c["q1"] = xa @ p["A1"].T + p["a1"]
     c["k1"] = lrelu(c["q1"])
@@ -165,6 +179,7 @@ def decoder_forward(p: dict, z: np.ndarray, blob: np.ndarray, ang: np.ndarray, k
 def decoder_backward(p: dict, c: dict, dy: np.ndarray):
     """Gradients of sum(dy * y) w.r.t. every parameter, the latents and the
     angular inputs: (grads, dz [n, 64], dang [n, 5])."""
+    W1, b1, W2, b2 = _front(p)
     g = {}
     g["A5"] = dy.T @ c["k4"]
     g["a5"] = dy.sum(0)
@@ -181,17 +196,16 @@ def decoder_backward(p: dict, c: dict, dy: np.ndarray):
     g["A1"] = dq1.T @ c["xa"]
     g["a1"] = dq1.sum(0)
     dxa = dq1 @ p["A1"]
-    n_a = c["xa"].shape[1] - N_ANG
-    if "S1" not in p:
-        return g, dxa[:, :LATENT], dxa[:, n_a:]
-    dg2 = dxa[:, :n_a] * dlrelu(c["g2"])
-    g["S2"] = dg2.T @ c["h1"]
-    g["s2"] = dg2.sum(0)
-    dg1 = (dg2 @ p["S2"]) * dlrelu(c["g1"])
-    g["S1"] = dg1.T @ c["x0"]
-    g["s1"] = dg1.sum(0)
-    dx0 = dg1 @ p["S1"]
-    return g, dx0[:, :LATENT], dxa[:, n_a:]
+    n_h = p[W2].shape[0]
+    dg2 = dxa[:, :n_h] * dlrelu(c["g2"])
+    g[W2] = dg2.T @ c["h1"]
+    g[b2] = dg2.sum(0)
+    dg1 = (dg2 @ p[W2]) * dlrelu(c["g1"])
+    g[W1] = dg1.T @ c["x0"]
+    g[b1] = dg1.sum(0)
+    dx0 = dg1 @ p[W1]
+    dang = dxa[:, n_h:] if "S1" in p else dx0[:, -N_ANG:]
+    return g, dx0[:, :LATENT], dang
 
 
 def shade(p: dict, z_mat: np.ndarray, materials, gbuf: dict, ablation: int = FULL):

@@ -49,32 +49,29 @@ __host__ __device__ constexpr PaperOffsets paper_offsets(int w) {
 }
 
 // Ablations of the structure (Sec. 6.3): the spatial inputs unencoded
-// (frac u, frac v, t: S1 becomes [W][67]), or no spatial fusion (no S1, s1,
-// S2, s2; A1 becomes [W][93] over [z | one-blob | wi | wo.xy]).
+// (frac u, frac v, t: S1 becomes [W][67]), or no spatial fusion: the
+// angular decoder gains two hidden layers in the fusion's place (the
+// section adds hidden layers for a fair comparison), held in the S1, S2
+// slots -- [W][93] over [z | one-blob | wi | wo.xy], then [W][W] -- and A1
+// becomes [W][W] over their output (same size as the full structure).
 constexpr int kPnFull = 0, kPnNoOneBlob = 1, kPnNoFusion = 2;
 
 __host__ __device__ constexpr int paper_spatial_channels(int ablation) { return ablation == kPnNoOneBlob ? 3 : kPnBlob; }
+// Inputs of the first layer, and of A1.
+__host__ __device__ constexpr int paper_x0_inputs(int ablation) {
+  return kPnLatent + paper_spatial_channels(ablation) + (ablation == kPnNoFusion ? kPnAng : 0);
+}
+__host__ __device__ constexpr int paper_a1_inputs(int w, int ablation) { return ablation == kPnNoFusion ? w : w + kPnAng; }
 
-// Offsets of an ablation's parameters; the absent layers' offsets are -1.
 __host__ __device__ constexpr PaperOffsets paper_offsets_ablation(int w, int ablation) {
-  if (ablation == kPnFull) return paper_offsets(w);
   PaperOffsets o{};
-  int at = 0;
-  if (ablation == kPnNoOneBlob) {
-    o.S1 = 0;
-    o.s1 = o.S1 + w * (kPnLatent + 3);
-    o.S2 = o.s1 + w;
-    o.s2 = o.S2 + w * w;
-    o.A1 = o.s2 + w;
-    o.a1 = o.A1 + w * (w + kPnAng);
-    at = o.a1 + w;
-  } else {
-    o.S1 = o.s1 = o.S2 = o.s2 = -1;
-    o.A1 = 0;
-    o.a1 = o.A1 + w * (kPnLatent + kPnBlob + kPnAng);
-    at = o.a1 + w;
-  }
-  o.A2 = at;
+  o.S1 = 0;
+  o.s1 = o.S1 + w * paper_x0_inputs(ablation);
+  o.S2 = o.s1 + w;
+  o.s2 = o.S2 + w * w;
+  o.A1 = o.s2 + w;
+  o.a1 = o.A1 + w * paper_a1_inputs(w, ablation);
+  o.A2 = o.a1 + w;
   o.a2 = o.A2 + w * w;
   o.A3 = o.a2 + w;
   o.a3 = o.A3 + w * w;
@@ -85,6 +82,10 @@ __host__ __device__ constexpr PaperOffsets paper_offsets_ablation(int w, int abl
   o.total = o.a5 + 4;
   return o;
 }
+
+static_assert(paper_offsets_ablation(64, kPnFull).A5 == paper_offsets(64).A5 &&
+                  paper_offsets_ablation(128, kPnFull).total == paper_offsets(128).total,
+              "the full structure's layout");
 
 // Encoder with a 64-wide latent (same layout as the workload's encoder).
 constexpr int kPnEncParams = 128 * 22 + 128 + 128 * 128 + 128 + kPnLatent * 128 + kPnLatent;

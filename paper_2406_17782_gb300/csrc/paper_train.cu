@@ -150,17 +150,17 @@ __device__ __forceinline__ void pn_blob_fp32(float u, float v, float r, float *o
 }
 
 // X0[b] = [z_mat (64) | spatial channels (24 one-blob, or 3 unencoded)]
-// with row stride ld0, and the angular inputs (wi, wo.xy) at columns
-// ang0..ang0+4 of XA (row stride lda).  Without the spatial fusion X0 is
-// the front of XA itself.
+// (row stride ld0) and the angular inputs (wi, wo.xy) at columns
+// ang0..ang0+4 of the row of A (row stride lda): XA after the fused
+// spatial feature, or X0 itself without the fusion.
 __global__ void pn_inputs_kernel(fabric_gbuffer g, const float *__restrict__ z, int n_lat, int ablation,
-                                 float *__restrict__ X0, int ld0, float *__restrict__ XA, int lda, int ang0,
+                                 float *__restrict__ X0, int ld0, float *__restrict__ A, int lda, int ang0,
                                  int *status) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= g.n) return;
   int m = g.material[b];
   float *x = X0 + b * ld0;
-  float *xa = XA + b * lda;
+  float *xa = A + b * lda;
   const int ks = paper_spatial_channels(ablation);
   if (m >= n_lat) {
     atomicOr(status, kStatusBadMaterial);
@@ -437,15 +437,16 @@ int paper_train_max_materials(int w) { return (int)((200 * 1024) / (w * 4)); }
 size_t paper_train_work_bytes(int w, int64_t B, int n_mat) {
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
   const int64_t segs = (B + kSumRows - 1) / kSumRows;
-  const int ka_max = kPnLatent + kPnBlob + kPnAng > w + kPnAng ? kPnLatent + kPnBlob + kPnAng : w + kPnAng;
+  const int kx_max = kPnLatent + kPnBlob + kPnAng;        // widest first layer (no fusion)
+  const int k_max = kx_max > w + kPnAng ? kx_max : w + kPnAng;
   size_t f = 0;
-  f += (size_t)B * (kPnLatent + kPnBlob);         // X0
+  f += (size_t)B * kx_max;                        // X0
   f += (size_t)B * w;                             // H1
-  f += (size_t)B * ka_max;                        // XA
+  f += (size_t)B * (w + kPnAng);                  // XA
   f += 4 * (size_t)B * w;                         // K1..K4
   f += 2 * (size_t)B * 4;                         // Y, DY
   f += 3 * (size_t)B * w;                         // three gradient buffers
-  f += (size_t)chunks * w * (ka_max + 1);         // weight-gradient partials (largest layer)
+  f += (size_t)chunks * w * (k_max + 1);          // weight-gradient partials (widest layer)
   f += (size_t)n_mat * segs * w + (size_t)n_mat * w + (size_t)n_mat * kPnLatent;   // latent sums, G, dz
   f += (size_t)n_mat * (kEI + 4 * kEH + kPnLatent);                                // encoder
   f += 64 * 32;
@@ -454,10 +455,12 @@ size_t paper_train_work_bytes(int w, int64_t B, int n_mat) {
 
 namespace {
 
-// Activation buffers of one pass over a batch of B queries.
+// Activation buffers of one pass over a batch of B queries: the first
+// layer's input X0 [B][KX0], the first layer's output H1, A1's input XA
+// [B][KA] (the second layer's output, then the angular inputs with the
+// spatial fusion), K1..K4, the raw head Y.
 struct PnPass {
   int w, ablation, KX0, KA;
-  bool fusion;
   float *X0, *H1, *XA, *K1, *K2, *K3, *K4, *Y;
 };
 
@@ -466,12 +469,11 @@ PnPass pn_pass_buffers(int w, int ablation, int64_t B, Take take) {
   PnPass P;
   P.w = w;
   P.ablation = ablation;
-  P.fusion = ablation != kPnNoFusion;
-  P.KX0 = kPnLatent + paper_spatial_channels(ablation);
-  P.KA = P.fusion ? w + kPnAng : kPnLatent + kPnBlob + kPnAng;
+  P.KX0 = paper_x0_inputs(ablation);
+  P.KA = paper_a1_inputs(w, ablation);
+  P.X0 = take((size_t)B * P.KX0);
+  P.H1 = take((size_t)B * w);
   P.XA = take((size_t)B * P.KA);
-  P.X0 = P.fusion ? take((size_t)B * P.KX0) : P.XA;
-  P.H1 = P.fusion ? take((size_t)B * w) : nullptr;
   P.K1 = take((size_t)B * w);
   P.K2 = take((size_t)B * w);
   P.K3 = take((size_t)B * w);
@@ -488,15 +490,14 @@ cudaError_t pn_forward(const PnPass &P, const fabric_gbuffer &q, const float *z,
   const int64_t B = q.n;
   const int w = P.w;
   cudaError_t e;
-  const int ang0 = P.fusion ? w : kPnLatent + kPnBlob;
-  pn_inputs_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(q, z, n_mat, P.ablation, P.X0, P.fusion ? P.KX0 : P.KA,
-                                                              P.XA, P.KA, ang0, status);
+  const bool fusion = P.ablation != kPnNoFusion;
+  pn_inputs_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(
+      q, z, n_mat, P.ablation, P.X0, P.KX0, fusion ? P.XA : P.X0, fusion ? P.KA : P.KX0,
+      fusion ? w : kPnLatent + kPnBlob, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (P.fusion) {
-    if ((e = fwd(P.X0, P.KX0, P.KX0, dec + o.S1, dec + o.s1, w, B, P.H1, w, nullptr, 0, true, s)) != cudaSuccess)
-      return e;
-    if ((e = fwd(P.H1, w, w, dec + o.S2, dec + o.s2, w, B, P.XA, P.KA, nullptr, 0, true, s)) != cudaSuccess) return e;
-  }
+  if ((e = fwd(P.X0, P.KX0, P.KX0, dec + o.S1, dec + o.s1, w, B, P.H1, w, nullptr, 0, true, s)) != cudaSuccess)
+    return e;
+  if ((e = fwd(P.H1, w, w, dec + o.S2, dec + o.s2, w, B, P.XA, P.KA, nullptr, 0, true, s)) != cudaSuccess) return e;
   if ((e = fwd(P.XA, P.KA, P.KA, dec + o.A1, dec + o.a1, w, B, P.K1, w, nullptr, 0, true, s)) != cudaSuccess) return e;
   if ((e = fwd(P.K1, w, w, dec + o.A2, dec + o.a2, w, B, P.K2, w, nullptr, 0, true, s)) != cudaSuccess) return e;
   if ((e = fwd(P.K2, w, w, dec + o.A3, dec + o.a3, w, B, P.K3, w, P.K1, w, true, s)) != cudaSuccess) return e;   // skip
@@ -525,13 +526,10 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   float *DY = take((size_t)B * 4);
   float *D1 = take((size_t)B * w), *D2 = take((size_t)B * w), *D3 = take((size_t)B * w);
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
-  // weight-gradient partials of the widest layer: K = KX0 (S1), KA (A1) or W (S2, A2..A4)
+  // weight-gradient partials of the widest layer: K = KX0 (first), KA (A1) or W
   const int k_max = KX0 > KA ? (KX0 > w ? KX0 : w) : (KA > w ? KA : w);
   float *part = take((size_t)chunks * w * (k_max + 1));
-  // per-material latent sums are taken over the first layer's gradient
-  // (width W), or directly over the latent part of dXA (64) without fusion
-  const int ws = P.fusion ? w : kPnLatent;
-  float *msum = take((size_t)n_mat * segs * ws), *G = take((size_t)n_mat * ws), *dz = take((size_t)n_mat * kPnLatent);
+  float *msum = take((size_t)n_mat * segs * w), *G = take((size_t)n_mat * w), *dz = take((size_t)n_mat * kPnLatent);
   float *F = take((size_t)n_mat * kEI), *EH1 = take((size_t)n_mat * kEH), *EH2 = take((size_t)n_mat * kEH);
   float *DA1 = take((size_t)n_mat * kEH), *DA2 = take((size_t)n_mat * kEH), *z = take((size_t)n_mat * kPnLatent);
   double *lpart = reinterpret_cast<double *>(take((size_t)((B + 255) / 256) * 2));
@@ -562,34 +560,24 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   PN_TRY(wgrad(D3, w, w, P.K1, w, w, B, part, gd + o.A2, gd + o.a2, s));
   PN_TRY(bwd_in(D3, w, w, dec + o.A2, w, w, B, D1, w, D2, w, P.K1, w, s));               // dq1 (+ dq3 through the skip)
   PN_TRY(wgrad(D1, w, w, P.XA, KA, KA, B, part, gd + o.A1, gd + o.a1, s));
-  const float *lat_grad;   // rows whose per-material sums give dz (fusion: times S1's latent block)
-  if (P.fusion) {
-    PN_TRY(bwd_in(D1, w, w, dec + o.A1, KA, w, B, D2, w, nullptr, 0, P.XA, KA, s));      // dg2
-    PN_TRY(wgrad(D2, w, w, P.H1, w, w, B, part, gd + o.S2, gd + o.s2, s));
-    PN_TRY(bwd_in(D2, w, w, dec + o.S2, w, w, B, D3, w, nullptr, 0, P.H1, w, s));        // dg1
-    PN_TRY(wgrad(D3, w, w, P.X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
-    lat_grad = D3;
-  } else {
-    // dXA[:, :64] = dq1 A1[:, :64]: the latent columns of the angular input
-    PN_TRY(bwd_in(D1, w, w, dec + o.A1, KA, kPnLatent, B, D2, kPnLatent, nullptr, 0, nullptr, 0, s));
-    lat_grad = D2;
-  }
-  // ---- latent gradient: per-material sums in row order
+  PN_TRY(bwd_in(D1, w, w, dec + o.A1, KA, w, B, D2, w, nullptr, 0, P.XA, KA, s));        // dg2
+  PN_TRY(wgrad(D2, w, w, P.H1, w, w, B, part, gd + o.S2, gd + o.s2, s));
+  PN_TRY(bwd_in(D2, w, w, dec + o.S2, w, w, B, D3, w, nullptr, 0, P.H1, w, s));          // dg1
+  PN_TRY(wgrad(D3, w, w, P.X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
+  // ---- latent gradient: per-material sums of dg1 in row order, times S1's latent block
   {
-    const size_t smem = (size_t)n_mat * ws * sizeof(float);
+    const size_t smem = (size_t)n_mat * w * sizeof(float);
     PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), 200 * 1024));
-    pn_material_sums_kernel<<<segs, ws, smem, s>>>(q.material, B, lat_grad, ws, n_mat, msum);
+    pn_material_sums_kernel<<<segs, w, smem, s>>>(q.material, B, D3, w, n_mat, msum);
     PN_TRY(cudaGetLastError());
-    pn_segment_total_kernel<<<(n_mat * ws + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, ws, P.fusion ? G : dz);
+    pn_segment_total_kernel<<<(n_mat * w + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, w, G);
     PN_TRY(cudaGetLastError());
-    if (P.fusion) {
-      // dz[m][k] = sum_j G[m][j] S1[j][k], k < 64
-      Epi ep{};
-      ep.mode = 1;
-      ep.out = dz;
-      ep.ld_out = kPnLatent;
-      PN_TRY((gemm<true, false, false>(G, w, 1, dec + o.S1, 1, KX0, n_mat, kPnLatent, w, w, 1, ep, s)));
-    }
+    // dz[m][k] = sum_j G[m][j] S1[j][k], k < 64
+    Epi ep{};
+    ep.mode = 1;
+    ep.out = dz;
+    ep.ld_out = kPnLatent;
+    PN_TRY((gemm<true, false, false>(G, w, 1, dec + o.S1, 1, KX0, n_mat, kPnLatent, w, w, 1, ep, s)));
   }
   // ---- encoder backward
   pn_enc_bwd_kernel<<<n_mat, kEH, 0, s>>>(enc, EH1, EH2, dz, DA1, DA2);
@@ -601,8 +589,8 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
 }
 
 size_t paper_forward_work_bytes(int w, int64_t B) {
-  const int ka_max = kPnLatent + kPnBlob + kPnAng > w + kPnAng ? kPnLatent + kPnBlob + kPnAng : w + kPnAng;
-  return ((size_t)B * (kPnLatent + kPnBlob + ka_max + 5 * (size_t)w + 4) + 64 * 16) * 4 + 4096;
+  const int kx_max = kPnLatent + kPnBlob + kPnAng;
+  return ((size_t)B * (kx_max + (w + kPnAng) + 5 * (size_t)w + 4) + 64 * 16) * 4 + 4096;
 }
 
 // FP32 forward of the structure (or an ablation) over a G-buffer, with

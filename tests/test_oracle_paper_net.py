@@ -158,35 +158,46 @@ def test_flop_count(PN):
 
 def test_ablation_shapes_and_raw_spatial_inputs(PN):
     """Without the one-blob encoding the spatial channels are the inputs
-    themselves; without the spatial fusion the angular decoder takes
-    [z | one-blob | angular] (64 + 24 + 5 = 93 inputs)."""
+    themselves; without the spatial fusion the angular decoder's first layer
+    takes [z | one-blob | angular] (64 + 24 + 5 = 93 inputs) and the
+    decoder keeps the full structure's depth and size."""
     f = PN.spatial_features(np.float32([3.25, -0.75]), np.float32([0.5, 7.125]), np.float32([1e-4, 2.5]),
                             PN.NO_ONEBLOB)
     np.testing.assert_allclose(f, [[0.25, 0.5, 0.0], [0.25, 0.125, 1.0]], atol=1e-7)
-    shapes = dict(PN.dec_shapes(64, PN.NO_FUSION))
-    assert "S1" not in shapes and shapes["A1"] == (64, 93)
-    assert dict(PN.dec_shapes(128, PN.NO_ONEBLOB))["S1"] == (128, 67)
+    for w in PN.WIDTHS:
+        shapes = dict(PN.dec_shapes(w, PN.NO_FUSION))
+        assert "S1" not in shapes and shapes["H1"] == (w, 93) and shapes["A1"] == (w, w)
+        assert len(shapes) == len(PN.dec_shapes(w))
+        n = lambda sh: sum(int(np.prod(d)) for _, d in sh)
+        assert n(PN.dec_shapes(w, PN.NO_FUSION)) == n(PN.dec_shapes(w))
+        assert dict(PN.dec_shapes(w, PN.NO_ONEBLOB))["S1"] == (w, 67)
 
 
 def test_no_fusion_closed_form_through_the_skip(PN):
-    """No spatial fusion: A1 reads latent[2] (unit 0) and the one-blob
-    channel 3 with weight -2 (unit 1, through the leaky slope); A2 = 0, so
-    the residual block returns lrelu(a3 + k1)."""
+    """No spatial fusion: H1 reads latent[2] (unit 0), wi_z with weight -2
+    (unit 1, through the leaky slope) and one-blob channel 3 (unit 2); H2
+    and A1 pass units 0..2 on; A2 = 0, so the residual block returns
+    lrelu(a3 + k1)."""
     w = 64
     p = {k: np.zeros(s) for k, s in PN.dec_shapes(w, PN.NO_FUSION)}
-    p["A1"][0, 2] = 1.0
-    p["A1"][1, 64 + 3] = -2.0
-    p["a3"][:2] = [0.5, 0.0]
-    p["A4"][:2, :2] = np.eye(2)
-    p["A5"][0, 0] = 1.0
-    p["A5"][1, 1] = 1.0
+    p["H1"][0, 2] = 1.0
+    p["H1"][1, 64 + 24 + 2] = -2.0       # wi_z
+    p["H1"][2, 64 + 3] = 1.0             # one-blob channel 3
+    p["H2"][:3, :3] = np.eye(3)
+    p["A1"][:3, :3] = np.eye(3)
+    p["a3"][:3] = [0.5, 0.0, 0.0]
+    p["A4"][:3, :3] = np.eye(3)
+    p["A5"][:3, :3] = np.eye(3)
     z = np.zeros((1, 64))
     z[0, 2] = 0.25
     blob = np.zeros((1, 24))
     blob[0, 3] = 0.5
-    y = PN.decoder_forward(p, z, blob, np.zeros((1, 5)))
-    # k1 = (0.25, lrelu(-1) = -0.01); k3 = (0.75, lrelu(-0.01) = -1e-4); k4 = (0.75, -1e-6)
-    np.testing.assert_allclose(y, [[0.75, -1e-6, 0.0, 0.0]], rtol=0, atol=1e-15)
+    ang = np.array([[0.0, 0.0, 0.5, 0.0, 0.0]])
+    y = PN.decoder_forward(p, z, blob, ang)
+    # unit 0: 0.25 through H1, H2, A1 (k1 = 0.25), k3 = lrelu(0.5 + 0.25) = 0.75, y0 = 0.75
+    # unit 1: lrelu(-1) = -0.01 -> -1e-4 (H2) -> k1 = -1e-6 -> k3 = -1e-8 -> k4 = -1e-10 = y1
+    # unit 2: 0.5 all the way: y2 = 0.5
+    np.testing.assert_allclose(y, [[0.75, -1e-10, 0.5, 0.0]], rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("ablation", [1, 2])

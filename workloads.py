@@ -414,10 +414,10 @@ def random_latents(n_mat: int, seed: int = 5, scale: float = 1.0, dim: int = 32)
 
 def paper_decoder_layers(width: int, ablation: str = "full"):
     """(out, in) of the paper decoder's layers: S1, S2, A1..A5; without the
-    one-blob encoding S1 takes 64 + 3 inputs, without the spatial fusion S1
-    and S2 are absent and A1 takes 64 + 24 + 5."""
+    one-blob encoding S1 takes 64 + 3 inputs; without the spatial fusion the
+    first layer takes 64 + 24 + 5 and A1 the second's output alone."""
     if ablation == "no_fusion":
-        return [(width, 64 + 24 + 5)] + [(width, width)] * 3 + [(4, width)]
+        return [(width, 64 + 24 + 5)] + [(width, width)] * 5 + [(4, width)]
     k0 = 64 + (3 if ablation == "no_oneblob" else 24)
     return [(width, k0), (width, width), (width, width + 5), (width, width), (width, width),
             (width, width), (4, width)]
