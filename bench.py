@@ -31,7 +31,9 @@ Also measured in the same run and reported on the JSON line:
     error of the neural frame and of the reference at 1-256 spp with their
     times, on the 1080p frame and on the multi-scale frame (Table 2
     footprints), on the linear f_P (the headline target), tone-mapped and
-    lit; latent interpolation and the editing latency;
+    lit; the ablation of the paper's structure (without the one-blob
+    encoding, without the spatial fusion; Sec. 6.3); latent interpolation
+    and the editing latency;
   * SM clocks during the timed region, and the FP64 oracle on the host cores.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-extras | --no-quality]
@@ -232,6 +234,8 @@ def main():
     ap.add_argument("--paper-steps", type=int, default=20000,
                     help="training steps of the paper's decoder structure in the quality section")
     ap.add_argument("--paper-width", type=int, default=128, choices=[64, 128])
+    ap.add_argument("--ablation-steps", type=int, default=10000,
+                    help="training steps of each structure in the ablation of the paper's decoder (width 64)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -440,6 +444,37 @@ def _target(neural, ladder, metric):
             "speedup_at_equal_rmse": (eq["ms"] / neural["ms"]) if eq else None}
 
 
+def measure_ablation(fab, torch, W, T, tm, g_tr, target, ms_host, args):
+    """The ablation of Sec. 6.3 on the same data: the paper's decoder
+    structure at width 64, without the one-blob encoding, and without the
+    spatial fusion (its two layers moved into the angular decoder, same
+    size), each trained from the same initial seed for the same steps with
+    the rendered-space loss and evaluated in FP32 on both frames."""
+    out = {"width": 64, "steps": args.ablation_steps, "loss": "rendered", "evaluation": "FP32 forward",
+           "structures": {}}
+    for name in ("full", "no_oneblob", "no_fusion"):
+        fab.paper_set_params(64, W.paper_decoder_init(64, weight_bound="small", ablation=name),
+                             W.paper_encoder_init(weight_bound="small"), ablation=name)
+        fab.set_train_loss("rendered")
+        t0 = time.time()
+        losses = T.train(fab, tm, g_tr, target, args.ablation_steps, 65536, args.quality_lr, log_every=1000,
+                         verbose=False, paper=True)
+        torch.cuda.synchronize()
+        t_train = time.time() - t0
+        fab.set_train_loss("eq11")
+        r = T.frame_rmse(fab, gt_spp=(32, 32), ref_spps=(), paper=True, paper_fp32=True)
+        r_ms = T.frame_rmse(fab, gt_spp=(64, 64), ref_spps=(), gbuf=ms_host, paper=True, paper_fp32=True)
+        out["structures"][name] = {
+            "params": len(W.paper_decoder_init(64, ablation=name)),
+            "final_loss": losses[-1][1] if losses else None,
+            "rmse_fp": r["neural"]["rmse_fp"], "rmse_tm": r["neural"]["rmse_tm"], "rmse_lit": r["neural"]["rmse"],
+            "multiscale_rmse_fp": r_ms["neural"]["rmse_fp"], "multiscale_rmse_lit": r_ms["neural"]["rmse"],
+            "train_seconds": t_train,
+        }
+    fab.paper_set_params(args.paper_width, W.paper_decoder_init(args.paper_width), W.paper_encoder_init())
+    return out
+
+
 def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     """Train the decoder and encoder with the library's kernels on data from
     the reference kernel (once with the paper's Eq. 11 loss, once with the
@@ -559,6 +594,7 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
                        "target_lit": _target(neural_pms, ms_ladder, "rmse_lit")},
         "train_steps": args.paper_steps, "train_seconds": t_paper,
     }
+    ablation = measure_ablation(fab, torch, W, T, tm, g_tr, target, ms_host, args)
     del g_tr, target
     interp = measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream)
     best = min(("eq11", "rendered", "paper_structure"), key=lambda k: runs[k]["neural_fp16"]["rmse_fp"])
@@ -591,6 +627,7 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
         "loss_eq11": runs["eq11"],
         "loss_rendered": runs["rendered"],
         "paper_structure": runs["paper_structure"],
+        "paper_ablation": ablation,
         "training": {"queries": args.quality_queries, "data_spp": 2048, "steps": args.quality_steps,
                      "batch": 65536, "lr": args.quality_lr, "precision": args.quality_precision,
                      "data_seconds": t_data},

@@ -113,7 +113,7 @@ def _errors(fab, a, gt, g):
 
 
 def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(1, 2, 4, 8, 16), gbuf=None,
-               paper: bool = False):
+               paper: bool = False, paper_fp32: bool = False):
     """Error of the neural 1080p frame, and of the reference at lower sample
     counts, against the reference at gt_spp (see _errors for the metrics;
     the paper's results are direct-lit renders, Sec. 6, the scope's metric is
@@ -122,13 +122,16 @@ def frame_rmse(fab: Fabric, precision: str = "fp16", gt_spp=(32, 32), ref_spps=(
     deviation from the integral (half the mean squared difference of the
     two, per metric).  `gbuf`: a host G-buffer of the frame's materials
     (default: the 1080p frame); `paper`: shade with the paper's decoder
-    structure instead of the workload's network."""
+    structure instead of the workload's network (on tensor cores at
+    `precision`, or in FP32 with `paper_fp32`, which runs every ablation)."""
     mats = W.frame_materials()
     fab.set_materials(mats)
     g = GBuffer.from_numpy(W.frame_gbuffer() if gbuf is None else gbuf)
     gt, _ = fab.shade_reference(g, gt_spp[0], gt_spp[1], 0x6721)
     out = {}
-    if paper:
+    if paper and paper_fp32:
+        nrgb, _ = fab.paper_shade_fp32(g, fab.paper_encode_params(mats))
+    elif paper:
         nrgb, _ = fab.paper_shade_neural(g, fab.paper_encode_params(mats), precision)
     else:
         nrgb, _ = fab.shade_neural(g, fab.encode_params(mats), precision)
