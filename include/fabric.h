@@ -483,8 +483,8 @@ fabric_status fabric_paper_encode_params(fabric_ctx *ctx, const fabric_material 
  * by fabric_set_train_loss, the backward pass (fixed-order reductions:
  * bitwise repeatable), one Adam update of the paper network's parameters.
  * *loss_dev (device double, or NULL) receives the batch loss before the
- * update.  Batch size 1..1048576; at most 800 training materials at width
- * 64 and 400 at width 128 (FABRIC_ERR_UNSUPPORTED beyond). */
+ * update.  Batch size 1..1048576; at most 1600 training materials
+ * (FABRIC_ERR_UNSUPPORTED beyond). */
 fabric_status fabric_paper_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr, double *loss_dev,
                                       void *stream);
 

@@ -20,8 +20,8 @@
 namespace fab {
 namespace {
 
-constexpr int TM = 64, TN = 64, TR = 16;
 constexpr int kGemmThreads = 256;
+constexpr int kBK = 8;             // depth of one shared-memory stage
 constexpr int kChunkRows = 512;    // batch rows per weight-gradient partial
 
 // Epilogue of the product: forward (bias, residual, leaky ReLU), input
@@ -40,61 +40,138 @@ struct Epi {
   int64_t slab;           // partial: floats per chunk slab
 };
 
+__device__ __forceinline__ uint64_t pn_pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 pn_upk2(uint64_t r) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+  return f;
+}
+// d = a * b + c in each 32-bit lane, rounded once (the same as two fmaf)
+__device__ __forceinline__ uint64_t pn_fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // C(i, j) = sum_r A(i, r) B(j, r) for i < M, j < N, r in [r0, r1), with
 // A(i, r) = A[i a_i + r a_r] and B(j, r) = B[j b_j + r b_r].  AR / BR: the
 // operand is contiguous along r (else along i / j).  B_ONES: column j = N - 1
-// of B is the constant 1 (the bias gradient as an extra output column).
-template <bool AR, bool BR, bool B_ONES>
-__global__ void __launch_bounds__(kGemmThreads) pn_gemm_kernel(const float *__restrict__ A, int64_t a_i, int64_t a_r,
-                                                               const float *__restrict__ Bm, int64_t b_j,
-                                                               int64_t b_r, int M, int N, int64_t R,
-                                                               int64_t r_chunk, Epi e) {
-  __shared__ float As[TR][TM + 4];
-  __shared__ float Bs[TR][TN + 4];
+// of B is the constant 1 (the bias gradient as an extra output column); the
+// tiles then cover the N - 1 other columns and the first column of tiles
+// also keeps the running sums of A's rows for it.
+// A BM x BN tile per CTA of 256 threads, each thread BM/16 x BN/16 outputs
+// (rows ty*4 + {0..3} of every 64-row band, columns likewise with tx), so
+// that one 16-byte shared-memory read feeds four products, and two adjacent
+// outputs of a row share one packed FP32x2 fma; operands pass through two
+// shared-memory stages of depth 8, the next stage's global loads in
+// registers while the current one is multiplied.  Every output is a chain of
+// fmaf over r in increasing order (bitwise repeatable).
+template <int BM, int BN, bool AR, bool BR, bool B_ONES>
+__global__ void __launch_bounds__(kGemmThreads, 2) pn_gemm_kernel(const float *__restrict__ A, int64_t a_i,
+                                                                  int64_t a_r, const float *__restrict__ Bm,
+                                                                  int64_t b_j, int64_t b_r, int M, int N, int64_t R,
+                                                                  int64_t r_chunk, Epi e) {
+  constexpr int RM = BM / 16, RN = BN / 16;            // outputs per thread along i and j
+  constexpr int LA = BM * kBK / kGemmThreads, LB = BN * kBK / kGemmThreads;   // loads per thread and stage
+  __shared__ __align__(16) float As[2][kBK][BM + 4];
+  __shared__ __align__(16) float Bs[2][kBK][BN + 4];
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
-  const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
+  const int NB = B_ONES ? N - 1 : N;                   // columns that come from B
+  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
   const int64_t r_begin = (int64_t)blockIdx.z * r_chunk;
   const int64_t r_end = r_begin + r_chunk < R ? r_begin + r_chunk : R;
-  float acc[4][4] = {};
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += TR) {
+  float ra[LA], rb[LB];
+  auto fetch = [&](int64_t r0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < LA; ++q) {
       const int el = tid + kGemmThreads * q;
-      const int rr = AR ? el % TR : el / TM, ii = AR ? el / TR : el % TM;
+      const int rr = AR ? el % kBK : el / BM, ii = AR ? el / kBK : el % BM;
       const int64_t gi = i0 + ii, gr = r0 + rr;
-      As[rr][ii] = (gi < M && gr < r_end) ? A[gi * a_i + gr * a_r] : 0.0f;
-      const int rb = BR ? el % TR : el / TN, jj = BR ? el / TR : el % TN;
-      const int64_t gj = j0 + jj, gb = r0 + rb;
-      float bv = 0.0f;
-      if (gj < N && gb < r_end) bv = (B_ONES && gj == N - 1) ? 1.0f : Bm[gj * b_j + gb * b_r];
-      Bs[rb][jj] = bv;
+      ra[q] = (gi < M && gr < r_end) ? A[gi * a_i + gr * a_r] : 0.0f;
     }
-    __syncthreads();
 #pragma unroll
-    for (int r = 0; r < TR; ++r) {
-      float a[4], b[4];
+    for (int q = 0; q < LB; ++q) {
+      const int el = tid + kGemmThreads * q;
+      const int rb_ = BR ? el % kBK : el / BN, jj = BR ? el / kBK : el % BN;
+      const int64_t gj = j0 + jj, gb = r0 + rb_;
+      rb[q] = (gj < NB && gb < r_end) ? Bm[gj * b_j + gb * b_r] : 0.0f;
+    }
+  };
+  auto stash = [&](int buf) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[r][ty * 4 + q];
-        b[q] = Bs[r][tx * 4 + q];
+    for (int q = 0; q < LA; ++q) {
+      const int el = tid + kGemmThreads * q;
+      As[buf][AR ? el % kBK : el / BM][AR ? el / kBK : el % BM] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int el = tid + kGemmThreads * q;
+      Bs[buf][BR ? el % kBK : el / BN][BR ? el / kBK : el % BN] = rb[q];
+    }
+  };
+  uint64_t acc[RM][RN / 2];   // adjacent output pairs (t, t + 1) of row q
+  float rsum[B_ONES ? RM : 1];
+#pragma unroll
+  for (int q = 0; q < RM; ++q) {
+#pragma unroll
+    for (int t = 0; t < RN / 2; ++t) acc[q][t] = 0ull;
+    if (B_ONES) rsum[q] = 0.0f;
+  }
+  int buf = 0;
+  if (r_begin < r_end) {
+    fetch(r_begin);
+    stash(0);
+  }
+  __syncthreads();
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kBK) {
+    const bool more = r0 + kBK < r_end;
+    if (more) fetch(r0 + kBK);   // next stage's loads in flight during this stage's products
+#pragma unroll
+    for (int r = 0; r < kBK; ++r) {
+      float av[RM];
+      uint64_t bv[RN / 2];
+#pragma unroll
+      for (int q = 0; q < RM / 4; ++q) {
+        const float4 t = *reinterpret_cast<const float4 *>(&As[buf][r][64 * q + 4 * ty]);
+        av[4 * q] = t.x;
+        av[4 * q + 1] = t.y;
+        av[4 * q + 2] = t.z;
+        av[4 * q + 3] = t.w;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < RN / 4; ++q) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bs[buf][r][64 * q + 4 * tx]);
+        bv[2 * q] = t.x;
+        bv[2 * q + 1] = t.y;
+      }
 #pragma unroll
-        for (int s = 0; s < 4; ++s) acc[q][s] = fmaf(a[q], b[s], acc[q][s]);
+      for (int q = 0; q < RM; ++q) {
+        const uint64_t a2 = pn_pk2(av[q], av[q]);
+#pragma unroll
+        for (int t = 0; t < RN / 2; ++t) acc[q][t] = pn_fma2(a2, bv[t], acc[q][t]);
+        if (B_ONES) rsum[q] += av[q];   // = fmaf(av[q], 1, rsum[q])
+      }
     }
+    if (more) stash(buf ^ 1);   // the other stage: its last readers finished before the previous barrier
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t i = i0 + ty * 4 + q;
+  for (int q = 0; q < RM; ++q) {
+    const int64_t i = i0 + 64 * (q / 4) + 4 * ty + (q % 4);
     if (i >= M) continue;
+    if (B_ONES && blockIdx.y == 0 && tx == 0) e.out[blockIdx.z * e.slab + i * N + (N - 1)] = rsum[q];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int j = j0 + tx * 4 + s;
-      if (j >= N) continue;
-      float v = acc[q][s];
+    for (int t = 0; t < RN; ++t) {
+      const int j = j0 + 64 * (t / 4) + 4 * tx + (t % 4);
+      if (j >= NB) continue;
+      const float2 pr = pn_upk2(acc[q][t / 2]);
+      float v = (t & 1) ? pr.y : pr.x;
       if (e.mode == 0) {
         v += e.bias[j];
         if (e.res) v += e.res[i * e.ld_res + j];
@@ -118,8 +195,17 @@ __global__ void pn_reduce_chunks_kernel(const float *__restrict__ part, int chun
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = K + 1;
   if (e >= M * N) return;
+  const int64_t mn = (int64_t)M * N;
   float s = 0.0f;
-  for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * M * N + e];
+  int c = 0;
+  for (; c + 8 <= chunks; c += 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = part[(c + q) * mn + e];   // eight loads in flight, added in order
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += v[q];
+  }
+  for (; c < chunks; ++c) s += part[c * mn + e];
   const int i = e / N, j = e % N;
   if (j < K)
     out_w[i * K + j] = s;
@@ -127,61 +213,60 @@ __global__ void pn_reduce_chunks_kernel(const float *__restrict__ part, int chun
     out_b[i] = s;
 }
 
-// One-blob bins of the footprint (FP32, accurate exp): the periodic
-// Gaussians of frac u and frac v (nearest image and the one on the far
-// side) and the plain ones of the size coordinate.
-__device__ __forceinline__ void pn_blob_fp32(float u, float v, float r, float *o) {
-  const float fu = u - floorf(u), fv = v - floorf(v);
-  const float t = (logf(fmaxf(r, kRFloor)) - kPnLnRLo) * kPnInvLnSpan;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float c = (i + 0.5f) * 0.125f;
-    float d = fu - c;
-    d -= rintf(d);
-    float e = 1.0f - fabsf(d);
-    o[i] = expf(-32.0f * d * d) + expf(-32.0f * e * e);
-    d = fv - c;
-    d -= rintf(d);
-    e = 1.0f - fabsf(d);
-    o[8 + i] = expf(-32.0f * d * d) + expf(-32.0f * e * e);
-    d = t - c;
-    o[16 + i] = expf(-32.0f * d * d);
+// One-blob channel k (FP32, accurate exp) of the footprint: k < 8 the
+// periodic Gaussians of frac u (nearest image and the one on the far side),
+// 8..15 those of frac v, 16..23 the plain ones of the size coordinate.
+__device__ __forceinline__ float pn_blob_channel(float u, float v, float r, int k) {
+  const float c = ((k & 7) + 0.5f) * 0.125f;
+  if (k >= 16) {
+    const float t = (logf(fmaxf(r, kRFloor)) - kPnLnRLo) * kPnInvLnSpan;
+    const float d = t - c;
+    return expf(-32.0f * d * d);
   }
+  const float x = k < 8 ? u : v;
+  float d = (x - floorf(x)) - c;
+  d -= rintf(d);
+  const float e = 1.0f - fabsf(d);
+  return expf(-32.0f * d * d) + expf(-32.0f * e * e);
 }
 
 // X0[b] = [z_mat (64) | spatial channels (24 one-blob, or 3 unencoded)]
 // (row stride ld0) and the angular inputs (wi, wo.xy) at columns
 // ang0..ang0+4 of the row of A (row stride lda): XA after the fused
-// spatial feature, or X0 itself without the fusion.
-__global__ void pn_inputs_kernel(fabric_gbuffer g, const float *__restrict__ z, int n_lat, int ablation,
-                                 float *__restrict__ X0, int ld0, float *__restrict__ A, int lda, int ang0,
-                                 int *status) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// spatial feature, or X0 itself without the fusion.  One warp per row, so
+// that every store of a row is coalesced: lanes copy the latent in two
+// 32-float halves, lane k < 24 computes spatial channel k, lanes < 5 the
+// angular inputs.
+__global__ void __launch_bounds__(256) pn_inputs_kernel(fabric_gbuffer g, const float *__restrict__ z, int n_lat,
+                                                        int ablation, float *__restrict__ X0, int ld0,
+                                                        float *__restrict__ A, int lda, int ang0, int *status) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (b >= g.n) return;
-  int m = g.material[b];
+  const int m = g.material[b];
   float *x = X0 + b * ld0;
   float *xa = A + b * lda;
   const int ks = paper_spatial_channels(ablation);
   if (m >= n_lat) {
-    atomicOr(status, kStatusBadMaterial);
-    for (int k = 0; k < kPnLatent + ks; ++k) x[k] = 0.0f;
-    for (int k = 0; k < kPnAng; ++k) xa[ang0 + k] = 0.0f;
+    if (lane == 0) atomicOr(status, kStatusBadMaterial);
+    x[lane] = 0.0f;
+    x[32 + lane] = 0.0f;
+    if (lane < ks) x[kPnLatent + lane] = 0.0f;
+    if (lane < kPnAng) xa[ang0 + lane] = 0.0f;
     return;
   }
-  for (int k = 0; k < kPnLatent; ++k) x[k] = z[(int64_t)m * kPnLatent + k];
+  x[lane] = z[(int64_t)m * kPnLatent + lane];
+  x[32 + lane] = z[(int64_t)m * kPnLatent + 32 + lane];
+  const float u = g.u[b], v = g.v[b], r = g.radius[b];
   if (ablation == kPnNoOneBlob) {
-    const float u = g.u[b], v = g.v[b];
-    x[kPnLatent + 0] = u - floorf(u);
-    x[kPnLatent + 1] = v - floorf(v);
-    x[kPnLatent + 2] = (logf(fmaxf(g.radius[b], kRFloor)) - kPnLnRLo) * kPnInvLnSpan;
-  } else {
-    pn_blob_fp32(g.u[b], g.v[b], g.radius[b], x + kPnLatent);
+    if (lane < 3)
+      x[kPnLatent + lane] = lane == 0   ? u - floorf(u)
+                            : lane == 1 ? v - floorf(v)
+                                        : (logf(fmaxf(r, kRFloor)) - kPnLnRLo) * kPnInvLnSpan;
+  } else if (lane < kPnBlob) {
+    x[kPnLatent + lane] = pn_blob_channel(u, v, r, lane);
   }
-  xa[ang0 + 0] = g.wi[3 * b];
-  xa[ang0 + 1] = g.wi[3 * b + 1];
-  xa[ang0 + 2] = g.wi[3 * b + 2];
-  xa[ang0 + 3] = g.wo[3 * b];
-  xa[ang0 + 4] = g.wo[3 * b + 1];
+  if (lane < kPnAng) xa[ang0 + lane] = lane < 3 ? g.wi[3 * b + lane] : g.wo[3 * b + lane - 3];
 }
 
 // Components (C = max(0, y), S = max(0, expm1(y) / 100), the inverse of
@@ -232,44 +317,54 @@ __global__ void __launch_bounds__(256) pn_loss_kernel(const float *__restrict__ 
   }
 }
 
+// One warp: lane l sums the partials l, l + 32, ... in order, then a fixed
+// shuffle tree adds the lanes.
 __global__ void pn_loss_final_kernel(const double *__restrict__ part, int n, double *__restrict__ loss) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s += part[k];
-    *loss = s;
-  }
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) s += part[k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) *loss = s;
 }
 
 // Per batch segment s: the sums of the rows of D [B][W] by material, part
-// [s][m][W].  Each thread owns one column and walks the segment's rows in
-// order, adding into its column of a shared-memory table of every
-// material, so every sum runs in row order (bitwise repeatable).
+// [s][m][W].  One warp per segment and 32 columns: each lane owns one
+// column and walks the segment's rows in order, adding into its column of a
+// shared-memory table [n_mat][32], so every sum runs in row order (bitwise
+// repeatable) and several warps share an SM.
 constexpr int kSumRows = 512;   // rows per segment
 
-__global__ void pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_t n, const float *__restrict__ D,
-                                        int W, int n_mat, float *__restrict__ part) {
-  extern __shared__ float acc[];   // [n_mat][W]
+__global__ void __launch_bounds__(32) pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_t n,
+                                                              const float *__restrict__ D, int W, int n_mat,
+                                                              float *__restrict__ part) {
+  extern __shared__ float4 acc4[];   // [n_mat][32] floats
+  float *acc = reinterpret_cast<float *>(acc4);
   __shared__ uint16_t smat[kSumRows];
-  const int d = threadIdx.x;
+  const int lane = threadIdx.x;
+  const int c = blockIdx.y * 32 + lane;
+  const bool live = c < W;
   const int64_t b0 = (int64_t)blockIdx.x * kSumRows;
   const int rows = (int)(n - b0 < kSumRows ? n - b0 : kSumRows);
-  for (int e = d; e < n_mat * W; e += blockDim.x) acc[e] = 0.0f;
-  for (int r = d; r < rows; r += blockDim.x) smat[r] = mat[b0 + r];
-  __syncthreads();
-  const float *col = D + b0 * W + d;
+  for (int e = lane; e < n_mat * 8; e += 32) acc4[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int r = lane; r < rows; r += 32) smat[r] = mat[b0 + r];
+  __syncwarp();
+  const float *col = D + b0 * W + (live ? c : 0);
   int r = 0;
   for (; r + 8 <= rows; r += 8) {
     float v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = col[(int64_t)(r + q) * W];   // eight loads in flight
+    for (int q = 0; q < 8; ++q) v[q] = live ? col[(int64_t)(r + q) * W] : 0.0f;   // eight loads in flight
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      if (smat[r + q] < n_mat) acc[smat[r + q] * W + d] += v[q];   // a bad index is flagged by the inputs kernel
+      if (smat[r + q] < n_mat) acc[smat[r + q] * 32 + lane] += v[q];   // a bad index is flagged by the inputs kernel
   }
   for (; r < rows; ++r)
-    if (smat[r] < n_mat) acc[smat[r] * W + d] += col[(int64_t)r * W];
-  float *out = part + (int64_t)blockIdx.x * n_mat * W;
-  for (int m = 0; m < n_mat; ++m) out[m * W + d] = acc[m * W + d];
+    if (smat[r] < n_mat) acc[smat[r] * 32 + lane] += live ? col[(int64_t)r * W] : 0.0f;
+  __syncwarp();
+  if (!live) return;
+  float *out = part + (int64_t)blockIdx.x * n_mat * W + c;
+  for (int m = 0; m < n_mat; ++m) out[m * W] = acc[m * 32 + lane];
 }
 
 // G[m][d] = sum over segments, in segment order.
@@ -380,8 +475,20 @@ __global__ void pn_enc_grad_kernel(int n_mat, const float *__restrict__ F, const
 template <bool AR, bool BR, bool B_ONES>
 cudaError_t gemm(const float *A, int64_t a_i, int64_t a_r, const float *B, int64_t b_j, int64_t b_r, int M, int N,
                  int64_t R, int64_t r_chunk, int chunks, const Epi &e, cudaStream_t s) {
-  const dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN, chunks);
-  pn_gemm_kernel<AR, BR, B_ONES><<<grid, kGemmThreads, 0, s>>>(A, a_i, a_r, B, b_j, b_r, M, N, R, r_chunk, e);
+  // 128-wide tiles where the extent fills them, else 64 (and 64-column
+  // tiles for 129..192 columns: three instead of two mostly empty ones)
+  const int nb = B_ONES ? N - 1 : N;   // columns that come from B
+  const bool wm = M > 64, wn = nb > 64 && !(nb > 128 && nb <= 192);
+  const int bm = wm ? 128 : 64, bn = wn ? 128 : 64;
+  const dim3 grid((M + bm - 1) / bm, (nb + bn - 1) / bn, chunks);
+  if (wm && wn)
+    pn_gemm_kernel<128, 128, AR, BR, B_ONES><<<grid, kGemmThreads, 0, s>>>(A, a_i, a_r, B, b_j, b_r, M, N, R, r_chunk, e);
+  else if (wm)
+    pn_gemm_kernel<128, 64, AR, BR, B_ONES><<<grid, kGemmThreads, 0, s>>>(A, a_i, a_r, B, b_j, b_r, M, N, R, r_chunk, e);
+  else if (wn)
+    pn_gemm_kernel<64, 128, AR, BR, B_ONES><<<grid, kGemmThreads, 0, s>>>(A, a_i, a_r, B, b_j, b_r, M, N, R, r_chunk, e);
+  else
+    pn_gemm_kernel<64, 64, AR, BR, B_ONES><<<grid, kGemmThreads, 0, s>>>(A, a_i, a_r, B, b_j, b_r, M, N, R, r_chunk, e);
   return cudaGetLastError();
 }
 
@@ -431,8 +538,11 @@ cudaError_t wgrad(const float *dZ, int ldz, int N, const float *X, int ldx, int 
 }  // namespace
 
 // Largest material table whose per-material sums fit the shared memory of
-// one CTA (n_mat x W floats); the training call refuses larger tables.
-int paper_train_max_materials(int w) { return (int)((200 * 1024) / (w * 4)); }
+// one CTA (n_mat x 32 floats); the training call refuses larger tables.
+int paper_train_max_materials(int w) {
+  (void)w;   // the table holds 32 columns of every material, whatever the width
+  return (int)((200 * 1024) / (32 * 4));
+}
 
 size_t paper_train_work_bytes(int w, int64_t B, int n_mat) {
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
@@ -491,7 +601,7 @@ cudaError_t pn_forward(const PnPass &P, const fabric_gbuffer &q, const float *z,
   const int w = P.w;
   cudaError_t e;
   const bool fusion = P.ablation != kPnNoFusion;
-  pn_inputs_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(
+  pn_inputs_kernel<<<(unsigned)((B + 7) / 8), 256, 0, s>>>(
       q, z, n_mat, P.ablation, P.X0, P.KX0, fusion ? P.XA : P.X0, fusion ? P.KA : P.KX0,
       fusion ? w : kPnLatent + kPnBlob, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -566,9 +676,9 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   PN_TRY(wgrad(D3, w, w, P.X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
   // ---- latent gradient: per-material sums of dg1 in row order, times S1's latent block
   {
-    const size_t smem = (size_t)n_mat * w * sizeof(float);
+    const size_t smem = (size_t)n_mat * 32 * sizeof(float);
     PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), 200 * 1024));
-    pn_material_sums_kernel<<<segs, w, smem, s>>>(q.material, B, D3, w, n_mat, msum);
+    pn_material_sums_kernel<<<dim3(segs, (w + 31) / 32), 32, smem, s>>>(q.material, B, D3, w, n_mat, msum);
     PN_TRY(cudaGetLastError());
     pn_segment_total_kernel<<<(n_mat * w + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, w, G);
     PN_TRY(cudaGetLastError());

@@ -78,6 +78,36 @@ def test_paper_gradient_matches_oracle(fab, w, n, loss_mode):
     assert np.array_equal(d, dec) and np.array_equal(e, enc)
 
 
+def test_paper_gradient_many_materials(fab):
+    """1600 training materials (the limit: per-material latent sums in a
+    1600 x 32 shared-memory table) at width 128, against the oracle; 1601
+    are refused."""
+    w = 128
+    mats = W.training_materials(200)
+    assert len(mats) == 1600
+    g = W.training_queries(8192, len(mats), stream="paper-many")
+    target = np.abs(np.random.default_rng(23).standard_normal((8192, 4)) * 0.2).astype(np.float32)
+    dec, enc = W.paper_decoder_init(w, weight_bound="small"), W.paper_encoder_init(weight_bound="small")
+    want_loss, want = oracle_step(w, mats, g, target, dec, enc, "eq11")
+    fab.paper_set_params(w, dec, enc)
+    fab.set_train_materials(mats)
+    loss = float(fab.paper_train_step(GBuffer.from_numpy(g), torch.from_numpy(target).cuda(), 0.0).item())
+    fab.sync_status()
+    got = fab.paper_gradient()
+    nd = M.n_params(PN.dec_shapes(w))
+    print(f"paper W={w} 1600 materials: loss {loss:.7g} vs {want_loss:.7g}; grad rel-L2 decoder "
+          f"{rel_l2(got[:nd], want[:nd]):.2e}, encoder {rel_l2(got[nd:], want[nd:]):.2e}")
+    assert abs(loss - want_loss) <= 1e-5 * abs(want_loss)
+    assert rel_l2(got[:nd], want[:nd]) <= 1e-4 and rel_l2(got[nd:], want[nd:]) <= 1e-4
+    fab.set_train_materials(np.concatenate([mats, mats[:1]]))
+    try:
+        with pytest.raises(FabricError) as err:
+            fab.paper_train_step(GBuffer.from_numpy(g), torch.from_numpy(target).cuda(), 0.0)
+        assert err.value.status == 6
+    finally:
+        fab.set_train_materials(mats[:16])
+
+
 def test_paper_training_is_repeatable_and_learns(fab):
     w = 64
     mats = W.training_materials(2)
