@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kGemmThreads = 256;
 constexpr int kBK = 8;             // depth of one shared-memory stage
-constexpr int kChunkRows = 512;    // batch rows per weight-gradient partial
+constexpr int kChunkRows = 256;    // batch rows per weight-gradient partial
 
 // Epilogue of the product: forward (bias, residual, leaky ReLU), input
 // gradient (addend, leaky ReLU derivative of the layer's own output), or
@@ -188,29 +188,41 @@ __global__ void __launch_bounds__(kGemmThreads, 2) pn_gemm_kernel(const float *_
   }
 }
 
-// out_w[i][j] = sum_c part[c][i][j] for j < K, out_b[i] = sum_c part[c][i][K]
-// (chunks in order).
+// out_w[i][j] = sum_c part[c][i][j] for j < K, out_b[i] = sum_c part[c][i][K]:
+// four lanes per element, lane g summing the g-th quarter of the chunks in
+// order, the quarters then added as (q0 + q1) + (q2 + q3).
 __global__ void pn_reduce_chunks_kernel(const float *__restrict__ part, int chunks, int M, int K,
                                        float *__restrict__ out_w, float *__restrict__ out_b) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = (int)(t >> 2), g = (int)(t & 3);
   const int N = K + 1;
-  if (e >= M * N) return;
+  const bool in = e < M * N;
   const int64_t mn = (int64_t)M * N;
+  const int per = (chunks + 3) / 4;
+  const int c1 = min(chunks, (g + 1) * per);
   float s = 0.0f;
-  int c = 0;
-  for (; c + 8 <= chunks; c += 8) {
-    float v[8];
+  if (in) {
+    int c = g * per;
+    for (; c + 8 <= c1; c += 8) {
+      float v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = part[(c + q) * mn + e];   // eight loads in flight, added in order
+      for (int q = 0; q < 8; ++q) v[q] = part[(c + q) * mn + e];   // eight loads in flight, added in order
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s += v[q];
+      for (int q = 0; q < 8; ++q) s += v[q];
+    }
+    for (; c < c1; ++c) s += part[c * mn + e];
   }
-  for (; c < chunks; ++c) s += part[c * mn + e];
+  // every lane forms the same (q0 + q1) + (q2 + q3): addition commutes exactly
+  const float o1 = __shfl_xor_sync(0xffffffffu, s, 1);
+  const float p = (g & 1) ? o1 + s : s + o1;
+  const float o2 = __shfl_xor_sync(0xffffffffu, p, 2);
+  const float tot = (g & 2) ? o2 + p : p + o2;
+  if (!in || g != 0) return;
   const int i = e / N, j = e % N;
   if (j < K)
-    out_w[i * K + j] = s;
+    out_w[i * K + j] = tot;
   else
-    out_b[i] = s;
+    out_b[i] = tot;
 }
 
 // One-blob channel k (FP32, accurate exp) of the footprint: k < 8 the
@@ -329,42 +341,89 @@ __global__ void pn_loss_final_kernel(const double *__restrict__ part, int n, dou
 }
 
 // Per batch segment s: the sums of the rows of D [B][W] by material, part
-// [s][m][W].  One warp per segment and 32 columns: each lane owns one
-// column and walks the segment's rows in order, adding into its column of a
-// shared-memory table [n_mat][32], so every sum runs in row order (bitwise
-// repeatable) and several warps share an SM.
-constexpr int kSumRows = 512;   // rows per segment
+// [s][m][W].  One CTA of 256 threads per segment and 32 columns: the CTA
+// sorts the segment's (material, row) keys in shared memory (bitonic) while
+// its 512 x 32 slice of D lands in shared memory (all loads in flight
+// together), then warp 0 walks the sorted rows, each lane adding its
+// column's rows of one material in row order in a register and storing the
+// sum when the material changes (zeros for the materials the segment
+// lacks).  Every sum runs in row order (bitwise repeatable).
+constexpr int kSumRows = 512;     // rows per segment
+constexpr int kSumThreads = 256;
+constexpr int kSumLd = 33;        // shared row stride of the D slice (conflict-free column reads)
+constexpr uint32_t kNoMat = 0xFFFFu;
+constexpr size_t kSumSmem = (size_t)kSumRows * kSumLd * sizeof(float);
 
-__global__ void __launch_bounds__(32) pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_t n,
-                                                              const float *__restrict__ D, int W, int n_mat,
-                                                              float *__restrict__ part) {
-  extern __shared__ float4 acc4[];   // [n_mat][32] floats
-  float *acc = reinterpret_cast<float *>(acc4);
-  __shared__ uint16_t smat[kSumRows];
-  const int lane = threadIdx.x;
-  const int c = blockIdx.y * 32 + lane;
-  const bool live = c < W;
+__global__ void __launch_bounds__(kSumThreads) pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_t n,
+                                                                       const float *__restrict__ D, int W,
+                                                                       int n_mat, float *__restrict__ part) {
+  extern __shared__ float tile[];          // [kSumRows][kSumLd]
+  __shared__ uint32_t key[kSumRows];       // (material << 16) | row
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.y * 32;
   const int64_t b0 = (int64_t)blockIdx.x * kSumRows;
   const int rows = (int)(n - b0 < kSumRows ? n - b0 : kSumRows);
-  for (int e = lane; e < n_mat * 8; e += 32) acc4[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  for (int r = lane; r < rows; r += 32) smat[r] = mat[b0 + r];
-  __syncwarp();
-  const float *col = D + b0 * W + (live ? c : 0);
-  int r = 0;
-  for (; r + 8 <= rows; r += 8) {
-    float v[8];
+  // the slice: row r, column lane, by warp r % 8
+  for (int k0 = 0; k0 < kSumRows / 8; k0 += 16) {   // sixteen loads in flight per thread
+    float v[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = live ? col[(int64_t)(r + q) * W] : 0.0f;   // eight loads in flight
+    for (int k = 0; k < 16; ++k) {
+      const int r = warp + 8 * (k0 + k);
+      v[k] = r < rows && c0 + lane < W ? D[(b0 + r) * W + c0 + lane] : 0.0f;
+    }
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (smat[r + q] < n_mat) acc[smat[r + q] * 32 + lane] += v[q];   // a bad index is flagged by the inputs kernel
+    for (int k = 0; k < 16; ++k) tile[(warp + 8 * (k0 + k)) * kSumLd + lane] = v[k];
   }
-  for (; r < rows; ++r)
-    if (smat[r] < n_mat) acc[smat[r] * 32 + lane] += live ? col[(int64_t)r * W] : 0.0f;
-  __syncwarp();
-  if (!live) return;
-  float *out = part + (int64_t)blockIdx.x * n_mat * W + c;
-  for (int m = 0; m < n_mat; ++m) out[m * W] = acc[m * 32 + lane];
+  for (int r = tid; r < kSumRows; r += kSumThreads) {
+    uint32_t m = r < rows ? (uint32_t)mat[b0 + r] : kNoMat;
+    if (m >= (uint32_t)n_mat) m = kNoMat;   // a bad index (flagged by the inputs kernel) sorts last, unused
+    key[r] = (m << 16) | (uint32_t)r;
+  }
+  __syncthreads();
+  for (int k = 2; k <= kSumRows; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < kSumRows; i += kSumThreads) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t x = key[i], y = key[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            key[i] = y;
+            key[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (warp != 0) return;
+  const int c = c0 + lane;
+  const bool live = c < W;
+  float *out = part + (int64_t)blockIdx.x * n_mat * W + (live ? c : 0);
+  int cur = 0;   // next material whose sum is still to be stored
+  float s = 0.0f;
+  for (int i0 = 0; i0 < rows; i0 += 8) {
+    float v[8];
+    uint32_t kk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      kk[q] = i0 + q < rows ? key[i0 + q] : (kNoMat << 16);
+      v[q] = tile[(kk[q] & 0xFFFFu) * kSumLd + lane];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int m = (int)(kk[q] >> 16);
+      if (m == (int)kNoMat) break;
+      for (; cur < m; ++cur) {   // store the finished material, zeros for the absent ones
+        if (live) out[(int64_t)cur * W] = s;
+        s = 0.0f;
+      }
+      s += v[q];
+    }
+  }
+  for (; cur < n_mat; ++cur) {
+    if (live) out[(int64_t)cur * W] = s;
+    s = 0.0f;
+  }
 }
 
 // G[m][d] = sum over segments, in segment order.
@@ -531,18 +590,15 @@ cudaError_t wgrad(const float *dZ, int ldz, int N, const float *X, int ldx, int 
   cudaError_t err = gemm<false, false, true>(dZ, 1, ldz, X, 1, ldx, N, K + 1, B, kChunkRows, chunks, e, s);
   if (err != cudaSuccess) return err;
   const int tot = N * (K + 1);
-  pn_reduce_chunks_kernel<<<(tot + 255) / 256, 256, 0, s>>>(part, chunks, N, K, dW, db);
+  pn_reduce_chunks_kernel<<<(unsigned)((4 * (int64_t)tot + 255) / 256), 256, 0, s>>>(part, chunks, N, K, dW, db);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Largest material table whose per-material sums fit the shared memory of
-// one CTA (n_mat x 32 floats); the training call refuses larger tables.
-int paper_train_max_materials(int w) {
-  (void)w;   // the table holds 32 columns of every material, whatever the width
-  return (int)((200 * 1024) / (32 * 4));
-}
+// Largest training material table the step accepts, at any width (the
+// latent sums keep n_mat x W partials per 512-row segment in the scratch).
+int paper_train_max_materials(int) { return 1600; }
 
 size_t paper_train_work_bytes(int w, int64_t B, int n_mat) {
   const int64_t chunks = (B + kChunkRows - 1) / kChunkRows;
@@ -676,9 +732,9 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   PN_TRY(wgrad(D3, w, w, P.X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
   // ---- latent gradient: per-material sums of dg1 in row order, times S1's latent block
   {
-    const size_t smem = (size_t)n_mat * 32 * sizeof(float);
-    PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), 200 * 1024));
-    pn_material_sums_kernel<<<dim3(segs, (w + 31) / 32), 32, smem, s>>>(q.material, B, D3, w, n_mat, msum);
+    PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), (int)kSumSmem));
+    pn_material_sums_kernel<<<dim3(segs, (w + 31) / 32), kSumThreads, kSumSmem, s>>>(q.material, B, D3, w, n_mat,
+                                                                                       msum);
     PN_TRY(cudaGetLastError());
     pn_segment_total_kernel<<<(n_mat * w + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, w, G);
     PN_TRY(cudaGetLastError());

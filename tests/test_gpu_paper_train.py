@@ -78,6 +78,32 @@ def test_paper_gradient_matches_oracle(fab, w, n, loss_mode):
     assert np.array_equal(d, dec) and np.array_equal(e, enc)
 
 
+@pytest.mark.parametrize("w", [64, 128])
+def test_paper_gradient_full_batch(fab, w):
+    """The benchmark's step: a batch of 65 536 queries over 256 training
+    materials (every weight-gradient chunk and latent-sum segment of the
+    launch the bench times), against the oracle."""
+    mats = W.training_materials(32)
+    g = W.training_queries(65536, len(mats), stream="paper-full-batch")
+    target = np.abs(np.random.default_rng(24).standard_normal((65536, 4)) * 0.2).astype(np.float32)
+    dec, enc = W.paper_decoder_init(w, weight_bound="small"), W.paper_encoder_init(weight_bound="small")
+    want_loss, want = oracle_step(w, mats, g, target, dec, enc, "rendered")
+    fab.paper_set_params(w, dec, enc)
+    fab.set_train_materials(mats)
+    fab.set_train_loss("rendered")
+    try:
+        loss = float(fab.paper_train_step(GBuffer.from_numpy(g), torch.from_numpy(target).cuda(), 0.0).item())
+        fab.sync_status()
+        got = fab.paper_gradient()
+    finally:
+        fab.set_train_loss("eq11")
+    nd = M.n_params(PN.dec_shapes(w))
+    print(f"paper W={w} full batch: loss {loss:.7g} vs {want_loss:.7g}; grad rel-L2 decoder "
+          f"{rel_l2(got[:nd], want[:nd]):.2e}, encoder {rel_l2(got[nd:], want[nd:]):.2e}")
+    assert abs(loss - want_loss) <= 1e-5 * abs(want_loss)
+    assert rel_l2(got[:nd], want[:nd]) <= 1e-4 and rel_l2(got[nd:], want[nd:]) <= 1e-4
+
+
 def test_paper_gradient_many_materials(fab):
     """1600 training materials (the limit: per-material latent sums in a
     1600 x 32 shared-memory table) at width 128, against the oracle; 1601
