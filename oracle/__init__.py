@@ -81,6 +81,15 @@ def lib():
             L.ora_period_quadrature.restype = None
             L.ora_period_quadrature.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+            L.ora_shade_reference_vis.restype = None
+            L.ora_shade_reference_vis.argtypes = L.ora_shade_reference.argtypes + [ctypes.c_int, d,
+                                                                                  ctypes.c_void_p]
+            L.ora_height.restype = d
+            L.ora_height.argtypes = [ctypes.c_void_p, u32, u32]
+            L.ora_height_max.restype = d
+            L.ora_height_max.argtypes = [ctypes.c_void_p]
+            L.ora_visible.restype = ctypes.c_int
+            L.ora_visible.argtypes = [ctypes.c_void_p, u32, u32, ctypes.c_void_p, d, P(ctypes.c_int)]
             _lib = L
     return _lib
 
@@ -179,11 +188,14 @@ def sample_position(u, v, r, pixel, k, nx, ny, seed):
 
 
 def shade_reference(materials, gbuf: dict, spp_x: int, spp_y: int, seed: int, nthreads: int = 0,
-                    pixel_index=None):
+                    pixel_index=None, visibility: bool = False, eps: float = 1e-6):
     """Stratified footprint estimator over a G-buffer (dict of numpy arrays
     u, v, radius float32 [n]; wi, wo float32 [n,3]; material uint16 [n]).
     `pixel_index` (int64 [n]) gives each point's index in the full buffer when
-    the arrays are a subset of it.  Returns (comps [n,4], rgb [n,3]) in FP64."""
+    the arrays are a subset of it.  Returns (comps [n,4], rgb [n,3]) in FP64;
+    with `visibility` (the proposed inter-yarn visibility model) also
+    ambiguous [n] bool: points where some march came within `eps` of the
+    surface without a clear occluder."""
     rows = material_rows(materials)
     u = np.ascontiguousarray(gbuf["u"], np.float32)
     v = np.ascontiguousarray(gbuf["v"], np.float32)
@@ -195,10 +207,39 @@ def shade_reference(materials, gbuf: dict, spp_x: int, spp_y: int, seed: int, nt
     comps = np.zeros((n, 4))
     rgb = np.zeros((n, 3))
     idx = None if pixel_index is None else np.ascontiguousarray(pixel_index, np.int64)
-    lib().ora_shade_reference(_ptr(rows), len(rows), _ptr(u), _ptr(v), _ptr(r), _ptr(wi), _ptr(wo),
-                              _ptr(mat), n, spp_x, spp_y, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
-                              _ptr(comps), _ptr(rgb), int(nthreads), None if idx is None else _ptr(idx))
-    return comps, rgb
+    if not visibility:
+        lib().ora_shade_reference(_ptr(rows), len(rows), _ptr(u), _ptr(v), _ptr(r), _ptr(wi), _ptr(wo),
+                                  _ptr(mat), n, spp_x, spp_y, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                  _ptr(comps), _ptr(rgb), int(nthreads), None if idx is None else _ptr(idx))
+        return comps, rgb
+    amb = np.zeros(n, np.uint8)
+    lib().ora_shade_reference_vis(_ptr(rows), len(rows), _ptr(u), _ptr(v), _ptr(r), _ptr(wi), _ptr(wo),
+                                  _ptr(mat), n, spp_x, spp_y, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                  _ptr(comps), _ptr(rgb), int(nthreads), None if idx is None else _ptr(idx),
+                                  1, float(eps), _ptr(amb))
+    return comps, rgb, amb.astype(bool)
+
+
+def height(mat_row, pu: int, pv: int) -> float:
+    """Height of the proposed visibility model's surface at a fixed-point
+    position (repeat units)."""
+    m = np.ascontiguousarray(mat_row, np.float64)
+    return float(lib().ora_height(_ptr(m), pu & 0xFFFFFFFF, pv & 0xFFFFFFFF))
+
+
+def height_max(mat_row) -> float:
+    m = np.ascontiguousarray(mat_row, np.float64)
+    return float(lib().ora_height_max(_ptr(m)))
+
+
+def visible(mat_row, pu: int, pv: int, w, eps: float = 1e-6):
+    """(V, ambiguous) of the proposed visibility model from the surface point
+    at (pu, pv) along w."""
+    m = np.ascontiguousarray(mat_row, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    a = ctypes.c_int()
+    v = lib().ora_visible(_ptr(m), pu & 0xFFFFFFFF, pv & 0xFFFFFFFF, _ptr(w), float(eps), ctypes.byref(a))
+    return int(v), bool(a.value)
 
 
 def period_quadrature(mat_row, wi, wo, grid: int, nthreads: int = 0) -> np.ndarray:

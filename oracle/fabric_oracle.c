@@ -41,7 +41,10 @@
  *     beta cos(pi x / 2)), dh/da = tan(theta).
  *   - n_p = normalize(z - dh/dc c - dh/da a); t0 = normalize(a + tan(theta) z);
  *     t_p = cos(psi) t0 + sin(psi) (n_p x t0).
- *   - V = 1 (inter-yarn shadowing is in the missing supplementary).
+ *   - V = 1 by default (inter-yarn shadowing is in the missing
+ *     supplementary).  With visibility on, V is this build's proposed model
+ *     (see "inter-yarn visibility" below): a ray march through the height
+ *     field whose slopes the frame above uses.
  */
 #include <math.h>
 #include <stdint.h>
@@ -235,12 +238,124 @@ double ora_sggx_sigma(double alpha, const double *t, const double *w) {
   return sqrt(1.0 - (1.0 - alpha * alpha) * c * c);
 }
 
+/* ------------------------ inter-yarn visibility V ------------------------- */
+/* A proposed model of the binary visibility V(x_p, w) of Eq. 3-5 (the paper
+ * defers its own to the missing supplementary).  The surface is the height
+ * field whose slopes the frame uses, in repeat units:
+ *   top yarn body:  beta w cos(pi x / 2) + (L / N_a) (ln cos(u (1 - 2y)) - ln cos u) / (2 u)
+ *                   (the cross-section, plus the float's rise: the integral of
+ *                   tan(theta) along the float), w = (1 - g) / (2 N_c) the
+ *                   half-width of the yarn, N_c / N_a the pattern size across /
+ *                   along the yarn, u the inclination in radians;
+ *   under a gap:    beta' w' (cos(pi x' / 2) - 1), the under-yarn, level, one
+ *                   cross-section height below the top yarns' edges.
+ * V(x_p, w) = 1 when the ray from (p, H(p)) along w stays above H at every
+ * step of a march with horizontal step 1 / (16 max(R, C)) repeats, until it
+ * rises above the largest height of the material (at most 4096 steps); 0
+ * otherwise, and 0 for w below the horizon.  Step positions are integer
+ * multiples of one rounded 0.32 fixed-point increment per ray.             */
+#define ORA_V_STEPS_PER_CELL 16
+#define ORA_V_MAX_STEPS 4096
+
+static double hump(double incl, int L, int n_along, double y) {
+  if (incl == 0.0) return 0.0;
+  return (double)L / (double)n_along * (log(cos(incl * (1.0 - 2.0 * y))) - log(cos(incl))) / (2.0 * incl);
+}
+
+double ora_height(const double *m, uint32_t pu, uint32_t pv) {
+  const int pid = (int)m[M_PAT];
+  const int R = pat_rows(pid), C = pat_cols(pid);
+  const uint64_t wu = (uint64_t)pu * (uint64_t)C, wv = (uint64_t)pv * (uint64_t)R;
+  const int j = (int)(wu >> 32), i = (int)(wv >> 32);
+  const uint32_t su = (uint32_t)wu, sv = (uint32_t)wv;
+  const double au = (double)su * 0x1p-32, av = (double)sv * 0x1p-32;
+  const uint32_t G = gap_fixed(m[M_GAP]);
+  const double g = m[M_GAP];
+  const int warp_top = pat_bit(pid, i, j);
+  const uint32_t s_top = warp_top ? su : sv;
+  const int body = (s_top >= G) && (s_top <= 0xFFFFFFFFu - G);
+  if (body) {
+    const int yarn = warp_top ? 0 : 1;
+    const double s = warp_top ? au : av, t = warp_top ? av : au;
+    const int n_across = yarn == 0 ? C : R, n_along = yarn == 0 ? R : C;
+    const double w = (1.0 - g) / (2.0 * n_across);
+    const double beta = yarn == 0 ? m[M_BETA_W] : m[M_BETA_F];
+    int L, o;
+    pat_run(pid, i, j, &L, &o);
+    const double x = (2.0 * s - 1.0) / (1.0 - g);
+    return beta * w * cos(ORA_PI * x / 2.0) + hump(m[M_INCL] * (ORA_PI / 180.0), L, n_along, ((double)o + t) / L);
+  }
+  const int under = warp_top ? 1 : 0;
+  const double s2 = warp_top ? av : au;
+  double x = (2.0 * s2 - 1.0) / (1.0 - g);
+  if (x < -1.0) x = -1.0;
+  if (x > 1.0) x = 1.0;
+  const int n_across = under == 0 ? C : R;
+  const double w = (1.0 - g) / (2.0 * n_across);
+  const double beta = under == 0 ? m[M_BETA_W] : m[M_BETA_F];
+  return beta * w * (cos(ORA_PI * x / 2.0) - 1.0);
+}
+
+/* Largest height of the material: the thicker yarn's crest plus the
+ * highest float rise of the pattern (none for a negative inclination). */
+double ora_height_max(const double *m) {
+  const int pid = (int)m[M_PAT];
+  const int R = pat_rows(pid), C = pat_cols(pid);
+  const double g = m[M_GAP], incl = m[M_INCL] * (ORA_PI / 180.0);
+  const double cw = m[M_BETA_W] * (1.0 - g) / (2.0 * C), cf = m[M_BETA_F] * (1.0 - g) / (2.0 * R);
+  double rise = 0.0;
+  for (int i = 0; i < R; ++i)
+    for (int j = 0; j < C; ++j) {
+      int L, o;
+      pat_run(pid, i, j, &L, &o);
+      const double r = hump(incl, L, pat_bit(pid, i, j) ? R : C, 0.5);
+      if (r > rise) rise = r;
+    }
+  return (cw > cf ? cw : cf) + rise;
+}
+
+/* V(x_p, w) of the model above at the fixed-point position (pu, pv).  When
+ * amb is given it is set to 1 if no step lies below the surface by more than
+ * eps while some step lies within eps of it (a decision that rounding could
+ * turn), else 0.                                                            */
+int ora_visible(const double *m, uint32_t pu, uint32_t pv, const double *w, double eps, int *amb) {
+  if (amb) *amb = 0;
+  if (w[2] <= 0.0) return 0;
+  const double rho = sqrt(w[0] * w[0] + w[1] * w[1]);
+  if (rho == 0.0) return 1;
+  const int pid = (int)m[M_PAT];
+  const int R = pat_rows(pid), C = pat_cols(pid);
+  const double delta = 1.0 / (ORA_V_STEPS_PER_CELL * (R > C ? R : C));
+  const uint32_t inc_u = (uint32_t)(uint64_t)(int64_t)llrint(w[0] / rho * delta * 4294967296.0);
+  const uint32_t inc_v = (uint32_t)(uint64_t)(int64_t)llrint(w[1] / rho * delta * 4294967296.0);
+  const double dz = delta * (w[2] / rho);
+  const double h0 = ora_height(m, pu, pv);
+  const double span = (ora_height_max(m) - h0) / dz;
+  int K = span < (double)ORA_V_MAX_STEPS ? (int)floor(span) + 1 : ORA_V_MAX_STEPS;
+  if (K < 1) K = 1;
+  int vis = 1, clear = 0, near = 0;
+  uint32_t qu = pu, qv = pv;
+  for (int k = 1; k <= K; ++k) {
+    qu += inc_u;
+    qv += inc_v;
+    const double d = ora_height(m, qu, qv) - (h0 + k * dz);
+    if (d > 0.0) vis = 0;
+    if (d > eps) clear = 1;
+    if (fabs(d) <= eps) near = 1;
+  }
+  if (amb) *amb = !clear && near;
+  return vis;
+}
+
 /* Integrand of Eq. 3-5 at one point, with k_d = k_s = 1 (Eq. 7):
  * out[0..3] += numerators of (C_warp, C_weft, S_warp, S_weft); out[4] += A.
  * The Eq. 1 specular denominator 4 cos_i cos_o cancels against <wi.n_p> of
- * Eq. 3 and <wo.n_p> of Eq. 4; cosines are taken with respect to n_p.        */
-void ora_point_contrib(const double *m, uint32_t pu, uint32_t pv, const double *wi,
-                       const double *wo, double *out) {
+ * Eq. 3 and <wo.n_p> of Eq. 4; cosines are taken with respect to n_p.  With
+ * `vis`, the numerators carry V(x_p, wi) V(x_p, wo) and A carries
+ * V(x_p, wo); a visibility that cannot change the sums (wo with <wo.n_p> = 0,
+ * wi with <wi.n_p> = 0) is not marched.  *amb |= an ambiguous march.       */
+static void point_contrib(const double *m, uint32_t pu, uint32_t pv, const double *wi,
+                          const double *wo, int vis, double eps, double *out, int *amb) {
   double n_p[3], t_p[3];
   const int yarn = ora_frame(m, pu, pv, n_p, t_p);
   const double ci = fmax(0.0, dot3(wi, n_p));
@@ -267,9 +382,21 @@ void ora_point_contrib(const double *m, uint32_t pu, uint32_t pv, const double *
       s_spec = D * G / 4.0 * J;
     }
   }
-  out[yarn] += s_diff;
-  out[2 + yarn] += s_spec;
-  out[4] += co * J;
+  double vi = 1.0, vo = 1.0;
+  if (vis && co > 0.0) {
+    int a1 = 0, a2 = 0;
+    vo = ora_visible(m, pu, pv, wo, eps, &a1);
+    if (vo > 0.0 && ci > 0.0) vi = ora_visible(m, pu, pv, wi, eps, &a2);
+    if (amb) *amb |= a1 | a2;
+  }
+  out[yarn] += s_diff * vi * vo;
+  out[2 + yarn] += s_spec * vi * vo;
+  out[4] += co * J * vo;
+}
+
+void ora_point_contrib(const double *m, uint32_t pu, uint32_t pv, const double *wi,
+                       const double *wo, double *out) {
+  point_contrib(m, pu, pv, wi, wo, 0, 0.0, out, NULL);
 }
 
 /* --------------------------- sample positions ---------------------------- */
@@ -306,7 +433,8 @@ void ora_sample_position(float u, float v, float r, int64_t pixel, int k, int nx
 /* --------------------------- footprint estimator ------------------------- */
 static void shade_one(const double *mats, int n_mat, float u, float v, float r,
                       const float *wi_f, const float *wo_f, int mat, int64_t pixel,
-                      int nx, int ny, uint64_t seed, double *comps, double *rgb) {
+                      int nx, int ny, uint64_t seed, int vis, double eps, double *comps,
+                      double *rgb, uint8_t *amb) {
   double acc[5] = {0, 0, 0, 0, 0};
   if (mat < 0 || mat >= n_mat) {
     for (int k = 0; k < 4; ++k) comps[k] = NAN;
@@ -316,11 +444,13 @@ static void shade_one(const double *mats, int n_mat, float u, float v, float r,
   const double *m = mats + (size_t)mat * M_STRIDE;
   const double wi[3] = {wi_f[0], wi_f[1], wi_f[2]};
   const double wo[3] = {wo_f[0], wo_f[1], wo_f[2]};
+  int a = 0;
   for (int k = 0; k < nx * ny; ++k) {
     uint32_t pu, pv;
     ora_sample_position(u, v, r, pixel, k, nx, ny, seed, &pu, &pv);
-    ora_point_contrib(m, pu, pv, wi, wo, acc);
+    point_contrib(m, pu, pv, wi, wo, vis, eps, acc, &a);
   }
+  if (amb) *amb = (uint8_t)a;
   for (int k = 0; k < 4; ++k) comps[k] = acc[4] > 0.0 ? acc[k] / acc[4] : 0.0;
   for (int ch = 0; ch < 3; ++ch)   /* Eq. 8 */
     rgb[ch] = m[M_KD_W + ch] * comps[0] + m[M_KD_F + ch] * comps[1] +
@@ -330,18 +460,29 @@ static void shade_one(const double *mats, int n_mat, float u, float v, float r,
 /* Supersampled footprint integral for n points (structure of arrays).  The
  * sample jitter of point p is keyed by its index in the full G-buffer:
  * pixel_index[p] when given (a subset of a larger buffer), else p.          */
-void ora_shade_reference(const double *mats, int n_mat, const float *u, const float *v,
-                         const float *r, const float *wi, const float *wo,
-                         const uint16_t *mat, int64_t n, int nx, int ny, uint64_t seed,
-                         double *comps, double *rgb, int nthreads, const int64_t *pixel_index) {
+void ora_shade_reference_vis(const double *mats, int n_mat, const float *u, const float *v,
+                             const float *r, const float *wi, const float *wo,
+                             const uint16_t *mat, int64_t n, int nx, int ny, uint64_t seed,
+                             double *comps, double *rgb, int nthreads, const int64_t *pixel_index,
+                             int vis, double eps, uint8_t *ambiguous) {
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
 #endif
   for (int64_t p = 0; p < n; ++p)
     shade_one(mats, n_mat, u[p], v[p], r[p], wi + 3 * p, wo + 3 * p, (int)mat[p],
-              pixel_index ? pixel_index[p] : p, nx, ny, seed, comps + 4 * p, rgb + 3 * p);
+              pixel_index ? pixel_index[p] : p, nx, ny, seed, vis, eps, comps + 4 * p, rgb + 3 * p,
+              ambiguous ? ambiguous + p : NULL);
   (void)nthreads;
+}
+
+/* The same with V = 1. */
+void ora_shade_reference(const double *mats, int n_mat, const float *u, const float *v,
+                         const float *r, const float *wi, const float *wo,
+                         const uint16_t *mat, int64_t n, int nx, int ny, uint64_t seed,
+                         double *comps, double *rgb, int nthreads, const int64_t *pixel_index) {
+  ora_shade_reference_vis(mats, n_mat, u, v, r, wi, wo, mat, n, nx, ny, seed, comps, rgb, nthreads,
+                          pixel_index, 0, 0.0, NULL);
 }
 
 /* Components at one fixed-point position (the point evaluation f_p <wi.n_p>
