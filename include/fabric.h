@@ -214,6 +214,24 @@ fabric_status fabric_shade_reference(fabric_ctx *ctx, const fabric_gbuffer *g, i
                                      uint64_t seed, float *rgb_dev, float *comps_dev, void *stream);
 
 /*
+ * Inter-yarn visibility V(x_p, w) of Eq. 3-5 in fabric_shade_reference (and
+ * so in data generated with it): 0 (default) V = 1; 1 this library's
+ * proposed model (the paper defers its own to a supplementary that is not
+ * available).  The surface is the height field whose slopes the shading
+ * frame uses, in repeat units: on a top yarn's body beta w cos(pi x / 2) plus
+ * the float's rise (the integral of tan(theta) along the float), w the yarn's
+ * half-width (1 - g) / (2 N), N the pattern size across the yarn; under a gap
+ * the under-yarn, level, at beta' w' (cos(pi x' / 2) - 1).  V = 1 when a
+ * march from the surface point along w with horizontal steps of
+ * 1 / (16 max(rows, cols)) repeats stays above the surface until the ray
+ * rises above the material's largest height (at most 4096 steps), else 0;
+ * the numerators carry V(x_p, wi) V(x_p, wo) and A carries V(x_p, wo).
+ * Costs one or two marches per sample.  FABRIC_ERR_INVALID_ARG for values
+ * other than 0 and 1.
+ */
+fabric_status fabric_set_visibility(fabric_ctx *ctx, int on);
+
+/*
  * Neural shading (Sec. 4.4, "Rendering"): decoder over the G-buffer with the
  * per-material latents latents_dev [n_mat][32] (n_mat = size of the material
  * table), then C = max(0, y), S = max(0, expm1(y')/100) (inverse of Eq. 9)

@@ -121,6 +121,7 @@ def load(path: str | None = None):
         "fabric_paper_encode_params": (st, [vp, vp, i32, vp, vp]),
         "fabric_paper_train_step": (st, [vp, P(FabricTrainBatch), ctypes.c_float, vp, vp]),
         "fabric_paper_get_gradient": (st, [vp, vp]),
+        "fabric_set_visibility": (st, [vp, i32]),
         "fabric_paper_structure_param_count": (i64, [i32, i32]),
         "fabric_paper_set_structure": (st, [vp, i32, i32, vp, vp]),
         "fabric_paper_shade_fp32": (st, [vp, P(FabricGBuffer), vp, vp, vp, vp]),

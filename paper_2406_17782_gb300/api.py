@@ -237,6 +237,11 @@ class Fabric:
         components weighted by max(wi.z, 0))."""
         self._check(self.lib.fabric_set_train_loss(self.h, _abi.LOSS[loss]))
 
+    def set_visibility(self, on: bool):
+        """The reference's proposed inter-yarn visibility model (V of Eq. 3-5)
+        on or off (default off: V = 1)."""
+        self._check(self.lib.fabric_set_visibility(self.h, 1 if on else 0))
+
     def set_train_precision(self, precision: str = "fp32"):
         """'fp32' (SIMT kernels) or 'bf16' (tensor cores) for the decoder's
         training forward and backward."""

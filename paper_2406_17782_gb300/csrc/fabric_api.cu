@@ -1,6 +1,7 @@
 // fabric_api.cu -- the C ABI of include/fabric.h: context lifecycle, argument
 // checking, material tables, parameter storage, checkpoints and dispatch to
 // the kernels.  Host code only.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -137,6 +138,7 @@ bool build_material(const fabric_material &m, DevMaterial *d, std::string *why) 
     }
   }
   const double incl = (double)m.incl_deg * M_PI / 180.0;
+  double rise_max = 0.0;
   for (int i = 0; i < w.rows; ++i) {
     for (int j = 0; j < w.cols; ++j) {
       const bool warp = w.cells[i][j] == '1';
@@ -153,8 +155,18 @@ bool build_material(const fabric_material &m, DevMaterial *d, std::string *why) 
       // theta(t) = incl (1 - 2 (off + t) / len) = theta0 - theta1 t
       d->theta[i * kMaxPatternDim + j] =
           make_float2((float)(incl * (1.0 - 2.0 * off / len)), (float)(2.0 * incl / len));
+      // the float's rise, the integral of tan(theta) along it:
+      // (ln cos theta(t) - ln cos incl) / (theta1 N_along)
+      const int n_along = warp ? w.rows : w.cols;
+      d->rise[i * kMaxPatternDim + j] = incl != 0.0 ? (float)(len / (2.0 * incl * n_along)) : 0.0f;
+      if (incl > 0.0) rise_max = std::max(rise_max, len / (double)n_along * -std::log(std::cos(incl)) / (2.0 * incl));
     }
   }
+  d->crest[0] = (float)((double)m.beta[0] * (1.0 - (double)m.gap) / (2.0 * w.cols));
+  d->crest[1] = (float)((double)m.beta[1] * (1.0 - (double)m.gap) / (2.0 * w.rows));
+  d->lncos_incl = (float)std::log(std::cos(incl));
+  d->h_max = (float)(std::max((double)d->crest[0], (double)d->crest[1]) + rise_max);
+  d->v_delta = (float)(1.0 / (16.0 * std::max(w.rows, w.cols)));
   return true;
 }
 
@@ -330,6 +342,14 @@ fabric_status fabric_set_train_loss(fabric_ctx *ctx, fabric_loss loss) {
   if (loss != FABRIC_LOSS_EQ11 && loss != FABRIC_LOSS_RENDERED)
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "unknown loss %d", (int)loss);
   ctx->loss_mode = (int)loss;
+  return FABRIC_OK;
+}
+
+fabric_status fabric_set_visibility(fabric_ctx *ctx, int on) {
+  if (!ctx) return FABRIC_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (on != 0 && on != 1) return fail(ctx, FABRIC_ERR_INVALID_ARG, "visibility is 0 or 1 (got %d)", on);
+  ctx->visibility = on;
   return FABRIC_OK;
 }
 
@@ -528,7 +548,7 @@ fabric_status fabric_shade_reference(fabric_ctx *ctx, const fabric_gbuffer *g, i
                     : spp >= 256 ? 32 : spp >= 64 ? 16 : spp >= 16 ? 8 : spp >= 4 ? 4 : 1;
   FAB_CUDA(ctx,
            launch_reference(*g, ctx->d_mat, ctx->n_mat, spp_x, spp_y, seed, rgb_dev, comps_dev, ctx->d_status,
-                            lanes, ctx->sm_count, static_cast<cudaStream_t>(stream)),
+                            lanes, ctx->sm_count, static_cast<cudaStream_t>(stream), ctx->visibility != 0),
            "reference kernel launch");
   return FABRIC_OK;
 }

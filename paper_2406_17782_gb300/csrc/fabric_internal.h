@@ -115,6 +115,13 @@ struct alignas(16) DevMaterial {
   float kd[2][3];
   float ks[2][3];
   float2 theta[kMaxPatternDim * kMaxPatternDim];
+  // the proposed inter-yarn visibility model (height field and ray march)
+  float crest[2];                      // beta w: cross-section height of each yarn, w its half-width
+  float lncos_incl;                    // ln cos(inclination)
+  float h_max;                         // largest surface height (repeat units)
+  float v_delta;                       // horizontal march step: 1 / (16 max(rows, cols)) repeats
+  float pad1[3];
+  float rise[kMaxPatternDim * kMaxPatternDim];   // per cell 1 / (theta1 N_along), 0 without inclination
 };
 
 // One segment of a batched draw, as the kernel reads it.
@@ -175,6 +182,7 @@ struct fabric_ctx {
   int tc_warpgroups = 0;
   int tc_tile_wgs = 0;         // warpgroups per decoder tile pipeline (0 or 1: one, 2: two)
   int loss_mode = 0;           // FABRIC_LOSS_EQ11 or FABRIC_LOSS_RENDERED
+  int visibility = 0;          // the reference's proposed inter-yarn visibility model on
   int train_prec = 0;          // FABRIC_PREC_FP32 (SIMT) or FABRIC_PREC_BF16 (tensor cores)
   int ref_lanes = 0;
   // host-buffer pipeline (fabric_shade_neural_host): per-slot stream, event
@@ -218,7 +226,7 @@ void paper_release(fabric_ctx *ctx);
 // Launchers implemented in the kernel translation units.
 cudaError_t launch_reference(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, int spp_x, int spp_y,
                              uint64_t seed, float *rgb, float *comps, int *status, int lanes_per_point,
-                             int sm_count, cudaStream_t s);
+                             int sm_count, cudaStream_t s, bool visibility = false);
 cudaError_t launch_decoder_fp32(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, const float *latents,
                                 const float *dec, float *rgb, float *comps, float *y_raw, int *status,
                                 cudaStream_t s);

@@ -49,6 +49,65 @@ struct Sums {
   float c0, c1, s0, s1, a;
 };
 
+// ---- the proposed inter-yarn visibility model (V of Eq. 3-5).  The surface
+// is the height field whose slopes the frame below uses, in repeat units:
+// on a top yarn's body beta w cos(pi x / 2) plus the float's rise (the
+// integral of tan(theta) along it); under a gap the under-yarn, level, one
+// cross-section height below the top yarns' edges, beta' w' (cos(pi x'/2) - 1).
+// V(x_p, w) = 1 when a march from (p, H(p)) along w, with horizontal steps
+// of 1 / (16 max(rows, cols)) repeats, stays above H until the ray rises
+// above the material's largest height (at most 4096 steps); 0 otherwise and
+// below the horizon.  Steps are integer multiples of one 0.32 fixed-point
+// increment per ray.
+constexpr int kVisMaxSteps = 4096;
+
+__device__ __forceinline__ float surface_height(const DevMaterial *__restrict__ m, const PointMaterial &pm,
+                                                uint32_t pu, uint32_t pv) {
+  const uint32_t j = __umulhi(pu, pm.cols), su = pu * pm.cols;
+  const uint32_t i = __umulhi(pv, pm.rows), sv = pv * pm.rows;
+  const bool warp_top = (__ldg(&m->top[i]) >> j) & 1u;
+  const uint32_t s_top = warp_top ? su : sv;
+  if ((s_top >= pm.gap) && (s_top <= 0xFFFFFFFFu - pm.gap)) {
+    const float s = (float)s_top * kTwoNeg32;
+    const float x = (2.0f * s - 1.0f) * pm.inv_1mg;
+    float h = __ldg(&m->crest[warp_top ? 0 : 1]) * cosf(x * (0.5f * kPi));
+    const float rs = __ldg(&m->rise[i * kMaxPatternDim + j]);
+    if (rs != 0.0f) {
+      const float t = (float)(warp_top ? sv : su) * kTwoNeg32;
+      const float2 th = __ldg(&m->theta[i * kMaxPatternDim + j]);
+      h += rs * (logf(cosf(th.x - th.y * t)) - __ldg(&m->lncos_incl));
+    }
+    return h;
+  }
+  const float s2 = (float)(warp_top ? sv : su) * kTwoNeg32;
+  const float x = fminf(1.0f, fmaxf(-1.0f, (2.0f * s2 - 1.0f) * pm.inv_1mg));
+  return __ldg(&m->crest[warp_top ? 1 : 0]) * (cosf(x * (0.5f * kPi)) - 1.0f);
+}
+
+__device__ bool visible(const DevMaterial *__restrict__ m, const PointMaterial &pm, uint32_t pu, uint32_t pv,
+                        float3 w) {
+  if (!(w.z > 0.0f)) return false;
+  const float rho2 = w.x * w.x + w.y * w.y;
+  if (rho2 == 0.0f) return true;
+  const float rho = sqrtf(rho2);
+  const float delta = __ldg(&m->v_delta);
+  const uint32_t inc_u = (uint32_t)(unsigned long long)__float2ll_rn(w.x / rho * delta * 4294967296.0f);
+  const uint32_t inc_v = (uint32_t)(unsigned long long)__float2ll_rn(w.y / rho * delta * 4294967296.0f);
+  const float dz = delta * (w.z / rho);
+  const float h0 = surface_height(m, pm, pu, pv);
+  const float span = (__ldg(&m->h_max) - h0) / dz;
+  int K = span < (float)kVisMaxSteps ? (int)floorf(span) + 1 : kVisMaxSteps;
+  if (K < 1) K = 1;
+  uint32_t qu = pu, qv = pv;
+  for (int k = 1; k <= K; ++k) {
+    qu += inc_u;
+    qv += inc_v;
+    if (surface_height(m, pm, qu, qv) > h0 + (float)k * dz) return false;
+  }
+  return true;
+}
+
+template <bool VIS>
 __device__ __forceinline__ void shade_sample(const DevMaterial *__restrict__ m, const PointMaterial &pm,
                                              uint32_t pu, uint32_t pv, float3 wi, float3 wo, float3 h,
                                              bool h_ok, float diff_k, float diff_c, Sums &acc) {
@@ -93,8 +152,19 @@ __device__ __forceinline__ void shade_sample(const DevMaterial *__restrict__ m, 
   const float ci = fmaxf(0.0f, wi.x * n.x + wi.y * n.y + wi.z * n.z);
   const float co = fmaxf(0.0f, wo.x * n.x + wo.y * n.y + wo.z * n.z);
   const float J = 1.0f / n.z;                      // 1 / <n_s . n_p>
-  const float coJ = co * J;
-  acc.a += coJ;                                    // A of Eq. 4 (V = 1)
+  float coJ = co * J;
+  bool lit = true;                                 // V(x_p, wi) V(x_p, wo)
+  if (VIS && co > 0.0f) {
+    // V(x_p, wo) weighs A and the numerators; V(x_p, wi) only matters with <wi.n_p> > 0
+    if (!visible(m, pm, pu, pv, wo)) {
+      coJ = 0.0f;
+      lit = false;
+    } else if (ci > 0.0f) {
+      lit = visible(m, pm, pu, pv, wi);
+    }
+  }
+  acc.a += coJ;                                    // A of Eq. 4
+  if (VIS && !lit) return;
   const float diff = (diff_k * ci + diff_c) * ci * coJ;
   float spec = 0.0f;
   if (ci > 0.0f && co > 0.0f && h_ok) {
@@ -133,7 +203,7 @@ struct RefArgs {
   int *status;
 };
 
-template <int L>
+template <int L, bool VIS>
 __global__ void __launch_bounds__(256) reference_kernel(const RefArgs a) {
   const int lane_g = threadIdx.x & (L - 1);
   const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
@@ -192,7 +262,7 @@ __global__ void __launch_bounds__(256) reference_kernel(const RefArgs a) {
       }
       const uint32_t pu = cu + offset_fixed(ix, xi_x, a.two_over_nx, r);
       const uint32_t pv = cv + offset_fixed(iy, xi_y, a.two_over_ny, r);
-      shade_sample(m, pm, pu, pv, wi, wo, h, h_ok, diff_k, diff_c, acc);
+      shade_sample<VIS>(m, pm, pu, pv, wi, wo, h, h_ok, diff_k, diff_c, acc);
     }
   }
   // warp-level reduction inside each group of L lanes
@@ -234,7 +304,7 @@ __global__ void __launch_bounds__(256) reference_kernel(const RefArgs a) {
 
 cudaError_t launch_reference(const fabric_gbuffer &g, const DevMaterial *mats, int n_mat, int spp_x, int spp_y,
                              uint64_t seed, float *rgb, float *comps, int *status, int lanes_per_point,
-                             int sm_count, cudaStream_t s) {
+                             int sm_count, cudaStream_t s, bool visibility) {
   (void)sm_count;
   RefArgs a;
   a.u = g.u;
@@ -260,13 +330,24 @@ cudaError_t launch_reference(const fabric_gbuffer &g, const DevMaterial *mats, i
   const int threads = 256;
   const int64_t total = g.n * (int64_t)lanes_per_point;
   const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+  if (visibility) {
+    switch (lanes_per_point) {
+      case 1: reference_kernel<1, true><<<blocks, threads, 0, s>>>(a); break;
+      case 2: reference_kernel<2, true><<<blocks, threads, 0, s>>>(a); break;
+      case 4: reference_kernel<4, true><<<blocks, threads, 0, s>>>(a); break;
+      case 8: reference_kernel<8, true><<<blocks, threads, 0, s>>>(a); break;
+      case 16: reference_kernel<16, true><<<blocks, threads, 0, s>>>(a); break;
+      default: reference_kernel<32, true><<<blocks, threads, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   switch (lanes_per_point) {
-    case 1: reference_kernel<1><<<blocks, threads, 0, s>>>(a); break;
-    case 2: reference_kernel<2><<<blocks, threads, 0, s>>>(a); break;
-    case 4: reference_kernel<4><<<blocks, threads, 0, s>>>(a); break;
-    case 8: reference_kernel<8><<<blocks, threads, 0, s>>>(a); break;
-    case 16: reference_kernel<16><<<blocks, threads, 0, s>>>(a); break;
-    default: reference_kernel<32><<<blocks, threads, 0, s>>>(a); break;
+    case 1: reference_kernel<1, false><<<blocks, threads, 0, s>>>(a); break;
+    case 2: reference_kernel<2, false><<<blocks, threads, 0, s>>>(a); break;
+    case 4: reference_kernel<4, false><<<blocks, threads, 0, s>>>(a); break;
+    case 8: reference_kernel<8, false><<<blocks, threads, 0, s>>>(a); break;
+    case 16: reference_kernel<16, false><<<blocks, threads, 0, s>>>(a); break;
+    default: reference_kernel<32, false><<<blocks, threads, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
