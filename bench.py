@@ -746,18 +746,41 @@ def measure_extras(fab, torch, W, GBuffer, g_host, gbufs, rgbs, latents, mats, a
         fab.shade_reference(gq, 64, 32, 0xDA7A, out_rgb=rgb_q, out_comps=comps_q)
         ms_q = timed(torch, stream, lambda k: fab.shade_reference(gq, 64, 32, 0xDA7A + k, out_rgb=rgb_q,
                                                                   out_comps=comps_q), 3)
-        gen.append({"material": m_idx, "weave": int(pm[m_idx]["pattern"]), "queries": gq.n,
-                    "gpu_ms": ms_q, "host_query_build_s": host_s})
+        entry = {"material": m_idx, "weave": int(pm[m_idx]["pattern"]), "queries": gq.n,
+                 "gpu_ms": ms_q, "host_query_build_s": host_s}
+        if m_idx == 0:   # and with the proposed inter-yarn visibility model
+            fab.set_visibility(True)
+            entry["gpu_ms_with_visibility"] = timed(
+                torch, stream, lambda k: fab.shade_reference(gq, 64, 32, 0xDA7A + k, out_rgb=rgb_q,
+                                                             out_comps=comps_q), 1)
+            fab.set_visibility(False)
+        gen.append(entry)
         del gq, comps_q, rgb_q
     fab.sync_status()
     fab.set_materials(mats)
+    # the reference with the proposed inter-yarn visibility model (one or two
+    # height-field marches per sample) beside V = 1, 256 spp
+    vis = {}
+    ms_vis = GBuffer.from_numpy(W.multiscale_gbuffer())
+    for name, gb in (("frame_1080p", gbufs[0]), ("multiscale_1080p", ms_vis)):
+        for on in (False, True):
+            fab.set_visibility(on)
+            fab.shade_reference(gb, 16, 16, 5, out_rgb=rgbs[0])
+            vis[f"{name}_{'with' if on else 'without'}_visibility_ms"] = timed(
+                torch, stream, lambda k: fab.shade_reference(gb, 16, 16, 5 + k, out_rgb=rgbs[0]), 3)
+    fab.set_visibility(False)
+    fab.sync_status()
+    del ms_vis
+    out["reference_visibility"] = dict(vis, spp=256, note="proposed model (the paper's is in its supplementary): "
+                                                        "ray march through the yarn height field, off by default")
     per_mat_s = float(np.mean([r["gpu_ms"] for r in gen])) * 1e-3
     out["paper_data_generation"] = {
         "materials_timed": gen, "spp": 2048, "gpu_s_per_material": per_mat_s,
         "gpu_s_all_465_materials": per_mat_s * len(pm),
         "sample_evals_per_s": float(np.mean([r["queries"] * 2048 / (r["gpu_ms"] * 1e-3) for r in gen])),
         "paper": "about 22 min per material, 165 h for 465 materials (Sec. 5.1; hardware not stated, with "
-                 "transmission and inter-yarn shadowing-masking, which this model leaves out)",
+                 "transmission, which this model leaves out, and inter-yarn shadowing-masking, here the "
+                 "proposed visibility model: gpu_ms_with_visibility)",
         "note": "reference kernel over the paper's query set of one material, CUDA events; the host-side "
                 "construction of the query set (numpy) is reported separately"}
     # batched 4K: one persistent launch over a 3840x2160 frame with materials
