@@ -29,13 +29,13 @@ def shade(fab, g, sx, sy, seed, vis):
     return rgb.cpu().numpy(), comps.cpu().numpy()
 
 
-def check(got, want, amb, what):
+def check(got, want, amb, what, max_amb=0.02):
     err = np.abs(np.asarray(got, np.float64) - want) - (RTOL * np.abs(want) + ATOL)
     bad = (err > 0).any(axis=1)
     print(f"{what}: {int(amb.sum())} of {len(amb)} points with a near-tie march; "
           f"{int(bad.sum())} outside the bound, {int((bad & ~amb).sum())} of them elsewhere")
     assert not (bad & ~amb).any()
-    assert amb.mean() < 0.02
+    assert amb.mean() < max_amb
 
 
 @pytest.mark.parametrize("frame,stream,spp", [("frame", "vis-frame", 8), ("multiscale", "vis-ms", 8),
@@ -76,3 +76,23 @@ def test_visibility_setting_is_checked(fab):
     from paper_2406_17782_gb300._abi import check as abi_check
     with pytest.raises(FabricError):
         abi_check(fab.lib.fabric_set_visibility(fab.h, 2))
+
+
+def test_visibility_on_degenerate_inputs(fab):
+    """The degenerate-input set of the reference (zero to 5-repeat
+    footprints; grazing, horizontal, below-horizon and opposite directions;
+    uv far out and negative; beta 0 and 4, gap 0 and 0.9, inclination +-89
+    degrees, where floats rise by more than a repeat and grazing marches run
+    to the 4096-step limit) with the model on."""
+    from test_gpu_degenerate import edge_gbuffer, edge_materials
+    mats = edge_materials()
+    fab.set_materials(mats)
+    try:
+        g = edge_gbuffer(len(mats))
+        rgb, comps = shade(fab, g, 4, 4, 0xED6E, True)
+        assert np.isfinite(comps).all() and np.isfinite(rgb).all()
+        wc, wr, amb = oracle.shade_reference(mats, g, 4, 4, 0xED6E, visibility=True)
+        check(comps, wc, amb, "degenerate comps", max_amb=0.05)
+        check(rgb, wr, amb, "degenerate rgb", max_amb=0.05)
+    finally:
+        fab.set_materials(W.frame_materials())
