@@ -39,6 +39,32 @@ __device__ __forceinline__ uint32_t offset_fixed(int k, float xi, float two_over
   return (uint32_t)(unsigned long long)__float2ll_rn(__fmul_rn(t, 4294967296.0f));
 }
 
+// sin and cos for |x| <= pi/2 from their Maclaurin series up to x^11 and
+// x^12 (truncation below 6e-8 and 7e-9 there), Horner form with FMA.  The
+// frame's angles (pi x / 2 across a yarn, theta along a float) stay in that
+// range; the series keep the normal's error near one FP32 rounding, where the
+// fast intrinsics' absolute error (about 4e-7) reached 2e-4 relative in the
+// components of rays grazing the yarns.
+__device__ __forceinline__ float sin_half_pi(float x) {
+  const float x2 = x * x;
+  float p = -2.505210838544172e-08f;     // -1/11!
+  p = fmaf(p, x2, 2.7557319223985893e-06f);
+  p = fmaf(p, x2, -1.984126984126984e-04f);
+  p = fmaf(p, x2, 8.333333333333333e-03f);
+  p = fmaf(p, x2, -1.6666666666666666e-01f);
+  return fmaf(p * x2, x, x);
+}
+__device__ __forceinline__ float cos_half_pi(float x) {
+  const float x2 = x * x;
+  float p = 2.08767569878681e-09f;       // 1/12!
+  p = fmaf(p, x2, -2.755731922398589e-07f);
+  p = fmaf(p, x2, 2.48015873015873e-05f);
+  p = fmaf(p, x2, -1.388888888888889e-03f);
+  p = fmaf(p, x2, 4.1666666666666664e-02f);
+  p = fmaf(p, x2, -0.5f);
+  return fmaf(p, x2, 1.0f);
+}
+
 struct PointMaterial {
   uint32_t rows, cols, gap;
   float inv_1mg, cos_psi, sin_psi;
@@ -124,7 +150,9 @@ __device__ __forceinline__ void shade_sample(const DevMaterial *__restrict__ m, 
     const float t = (float)(warp_top ? sv : su) * kTwoNeg32;
     x = (2.0f * s - 1.0f) * pm.inv_1mg;
     const float2 th = __ldg(&m->theta[i * kMaxPatternDim + j]);
-    __sincosf(th.x - th.y * t, &st, &ct);
+    const float theta = th.x - th.y * t;
+    st = sin_half_pi(theta);
+    ct = cos_half_pi(theta);
   } else {
     // gap of the top yarn: the yarn underneath shows, level, at its edge
     yarn = warp_top ? 1 : 0;
@@ -134,7 +162,7 @@ __device__ __forceinline__ void shade_sample(const DevMaterial *__restrict__ m, 
     ct = 1.0f;
   }
   // cross-section slope of the height profile beta cos(pi x / 2)
-  const float hc = (yarn ? pm.slope[1] : pm.slope[0]) * __sinf(x * (0.5f * kPi));
+  const float hc = (yarn ? pm.slope[1] : pm.slope[0]) * sin_half_pi(x * (0.5f * kPi));
   // n_p ~ cos(theta) (z - hc c) - sin(theta) a ; t0 = cos(theta) a + sin(theta) z
   float3 nv, t0;
   if (yarn == 0) {   // warp: a = +y, c = +x
