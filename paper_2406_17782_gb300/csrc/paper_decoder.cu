@@ -221,7 +221,7 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
 // W: network width; F16: FP16 (else BF16) operands; WG tile pipelines per CTA;
 // LDR: 32-column tensor-memory loads in flight per wait in the epilogues.
 template <int W, bool F16, int WG, int LDR>
-__global__ void __launch_bounds__(kTile * WG, 1) pn_decoder_kernel(const PnArgs a) {
+__global__ void __launch_bounds__(kTile * WG, (W == 64 && WG == 2) ? 2 : 1) pn_decoder_kernel(const PnArgs a) {
   constexpr int PT = kTile;
   constexpr uint32_t COLS = pn_cols(W);
   constexpr uint32_t COL_A = W;
@@ -399,11 +399,13 @@ teardown:
   }
 }
 
-// W = 64: four pipelines of 128 columns; W = 128: two of 256.  Either way one
-// CTA takes all 512 tensor-memory columns of its SM.
+// W = 64: two pipelines of 128 columns per CTA, two CTAs per SM (four CTAs
+// of one pipeline would need four copies of the 57 KB of weights); W = 128:
+// one CTA of two pipelines of 256 columns.  Either way the SM's 512
+// tensor-memory columns are taken.
 template <int W, bool F16>
 const void *pn_kernel() {
-  if (W == 64) return reinterpret_cast<const void *>(pn_decoder_kernel<64, F16, 4, 1>);
+  if (W == 64) return reinterpret_cast<const void *>(pn_decoder_kernel<64, F16, 2, 1>);
   return reinterpret_cast<const void *>(pn_decoder_kernel<128, F16, 2, 2>);
 }
 
@@ -438,7 +440,7 @@ cudaError_t launch_paper_decoder(int w, int precision, const fabric_gbuffer &g, 
   const bool f16 = precision == FABRIC_PREC_FP16;
   const void *fn = w == 64 ? (f16 ? pn_kernel<64, true>() : pn_kernel<64, false>())
                            : (f16 ? pn_kernel<128, true>() : pn_kernel<128, false>());
-  const int wg = w == 64 ? 4 : 2;
+  const int wg = 2;
   PnArgs a = {};
   a.u = g.u;
   a.v = g.v;
@@ -453,13 +455,17 @@ cudaError_t launch_paper_decoder(int w, int precision, const fabric_gbuffer &g, 
   a.rgb = rgb;
   a.comps = comps;
   a.status = status;
-  // Shared memory: alignment slack, barriers, the blob; at least 116 KB so
-  // that no second CTA (which would wait for tensor memory) fits on an SM.
+  // Shared memory: alignment slack, barriers, the blob; padded so that no
+  // CTA beyond the ones whose tensor memory fits (it would wait for it) can
+  // share an SM: width 64 two CTAs of two 128-column pipelines (at least
+  // 80 KB each), width 128 one CTA of two 256-column pipelines (116 KB).
+  const int per_sm = w == 64 ? 2 : 1;
+  const size_t floor_smem = (size_t)(w == 64 ? 80 : 116) * 1024;
   size_t smem = 2048 + ((pn_blob(w, n_mat).total + 1023u) & ~1023u);
-  if (smem < 116 * 1024) smem = 116 * 1024;
+  if (smem < floor_smem) smem = floor_smem;
   cudaError_t e = ensure_max_dyn_smem(fn, 227 * 1024);
   if (e != cudaSuccess) return e;
-  int64_t grid = sm_count;
+  int64_t grid = (int64_t)sm_count * per_sm;
   const int64_t need = (a.n_tiles + wg - 1) / wg;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
