@@ -85,6 +85,10 @@ typedef struct {
 /*
  * G-buffer of n shading points, structure of arrays, device memory, all
  * arrays 4-byte aligned (16-byte alignment enables the vectorised paths).
+ * The same holds for every output array: a [n][4] output (comps_dev and
+ * the like) that is 16-byte aligned takes one 16-byte store per point, any
+ * other float-aligned one four 4-byte stores; FABRIC_ERR_INVALID_ARG only
+ * for an output that is not float-aligned.
  * The query of Eq. 6: footprint centre (u, v) in pattern repeats (1 uv unit =
  * one weave repeat), footprint half side `radius` in the same units (box
  * kernel k_P over [u-r, u+r] x [v-r, v+r], Eq. 3), wi and wo as [n][3] unit
@@ -351,7 +355,7 @@ fabric_status fabric_error_stats(fabric_ctx *ctx, const float *a_dev, const floa
 /* ------------------------------------------------------------------ */
 
 /* One segment of a batched draw: a G-buffer and its own outputs (device
- * memory, caller-owned; comps_dev may be NULL, else 16-byte aligned). */
+ * memory, caller-owned; comps_dev may be NULL). */
 typedef struct {
   fabric_gbuffer g;
   float *rgb_dev;     /* [g.n][3] */
@@ -380,7 +384,7 @@ void fabric_plan_destroy(fabric_plan *plan);
 /*
  * Neural shading of a G-buffer in HOST memory, with the prepared state of
  * fabric_prepare_neural for `prec`.  g_host's pointers and rgb_host [n][3]
- * (and comps_host [n][4], 16-byte aligned, or NULL) are host pointers that
+ * (and comps_host [n][4], or NULL) are host pointers that
  * must stay valid until `stream` has passed this call.  Asynchronous on
  * `stream`.
  *  - chunk_points = 0 and every buffer page-locked and mapped (as
@@ -467,7 +471,7 @@ fabric_status fabric_paper_set_structure(fabric_ctx *ctx, int width, int ablatio
 
 /* The paper network (any structure) in FP32 on CUDA cores, one thread per
  * point and layer GEMMs over the G-buffer: latents_dev [n_mat][64] for the
- * material table; rgb_dev [n][3], comps_dev [n][4] (16-byte aligned) or
+ * material table; rgb_dev [n][3], comps_dev [n][4] or
  * NULL.  Uses the context's scratch (at most (5 W + 230) * 4 bytes a point).
  * A material index beyond the table gives NaN outputs and
  * FABRIC_ERR_DEVICE at the next fabric_sync_status. */

@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
             c4[2] = fmaxf(0.0f, (__expf(y[2]) - 1.0f) * (1.0f / kSpecK));
             c4[3] = fmaxf(0.0f, (__expf(y[3]) - 1.0f) * (1.0f / kSpecK));
           }
-          if (out_comps) reinterpret_cast<float4 *>(out_comps)[p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+          if (out_comps) store_row4(out_comps, p, c4[0], c4[1], c4[2], c4[3]);
           const float4 *al = reinterpret_cast<const float4 *>(alb + (mat < 0 ? 0 : mat) * 12);
           const float4 k0 = al[0], k1 = al[1], k2 = al[2];   // kd_warp, kd_weft, ks_warp, ks_weft (RGB each)
           out_rgb[3 * p + 0] = k0.x * c4[0] + k0.w * c4[1] + k1.z * c4[2] + k2.y * c4[3];

@@ -30,6 +30,7 @@ fabric_status cuda_fail(fabric_ctx *ctx, cudaError_t e, const char *what) {
 }
 
 bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool is_aligned4(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
 void *scratch(fabric_ctx *ctx, size_t bytes) {
   if (bytes <= ctx->scratch_bytes) return ctx->scratch;
@@ -539,8 +540,8 @@ fabric_status fabric_shade_reference(fabric_ctx *ctx, const fabric_gbuffer *g, i
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "spp_x, spp_y must be in 1..4096 (got %d, %d)", spp_x, spp_y);
   if (g->n == 0) return FABRIC_OK;
   if (!rgb_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "rgb output is NULL");
-  if (comps_dev && !is_aligned16(comps_dev))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_dev && !is_aligned4(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
   const int spp = spp_x * spp_y;
   // lanes per point: a whole warp for large sample counts, fewer otherwise
@@ -585,8 +586,8 @@ fabric_status fabric_shade_neural_prepared(fabric_ctx *ctx, const fabric_gbuffer
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "no prepared state for this precision, materials and parameters");
   if (g->n == 0) return FABRIC_OK;
   if (!rgb_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "rgb output is NULL");
-  if (comps_dev && !is_aligned16(comps_dev))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_dev && !is_aligned4(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (prec == FABRIC_PREC_FP32) {
     FAB_CUDA(ctx,
@@ -611,8 +612,8 @@ fabric_status fabric_shade_neural(fabric_ctx *ctx, const fabric_gbuffer *g, cons
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
   if (g->n == 0) return FABRIC_OK;
   if (!rgb_dev || !latents_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "rgb output or latents is NULL");
-  if (comps_dev && !is_aligned16(comps_dev))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_dev && !is_aligned4(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   const fabric_status st = fabric_prepare_neural(ctx, latents_dev, prec, stream);
   if (st != FABRIC_OK) return st;
   return fabric_shade_neural_prepared(ctx, g, prec, rgb_dev, comps_dev, stream);

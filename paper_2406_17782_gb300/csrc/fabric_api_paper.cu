@@ -140,8 +140,8 @@ fabric_status fabric_paper_shade_prepared(fabric_ctx *ctx, const fabric_gbuffer 
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "no prepared paper network for this precision, materials and parameters");
   if (g->n == 0) return FABRIC_OK;
   if (!rgb_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "rgb output is NULL");
-  if (comps_dev && !is_aligned16(comps_dev))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_dev && !is_aligned4(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   PN_CUDA(ctx,
           launch_paper_decoder(ctx->pn_width, (int)prec, *g, ctx->d_pn_blob, ctx->n_mat, rgb_dev, comps_dev,
                                ctx->d_status, ctx->sm_count, static_cast<cudaStream_t>(stream)),
@@ -230,8 +230,8 @@ fabric_status fabric_paper_shade_fp32(fabric_ctx *ctx, const fabric_gbuffer *g, 
   if (g->n == 0) return FABRIC_OK;
   if (!latents_dev || !rgb_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "latents or rgb output is NULL");
   if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
-  if (comps_dev && !is_aligned16(comps_dev))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_dev && !is_aligned4(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   const size_t need = paper_forward_work_bytes(ctx->pn_width, g->n);
   void *work = scratch(ctx, need);
   if (!work) return fail(ctx, FABRIC_ERR_OOM, "forward scratch (%zu bytes)", need);

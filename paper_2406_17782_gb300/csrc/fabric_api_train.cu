@@ -146,7 +146,7 @@ fabric_status fabric_decoder_forward(fabric_ctx *ctx, const fabric_gbuffer *g, c
   if (g->n == 0) return FABRIC_OK;
   if (!latents_dev || !dec_dev || !y_dev || n_lat < 1)
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "NULL pointer or n_lat < 1");
-  if (!is_aligned16(y_dev)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "y must be 16-byte aligned");
+  if (!is_aligned4(y_dev)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "y must be float-aligned");
   FAB_CUDA(ctx, launch_decoder_raw(*g, latents_dev, n_lat, dec_dev, y_dev, ctx->d_status,
                                    static_cast<cudaStream_t>(stream)),
            "decoder forward");

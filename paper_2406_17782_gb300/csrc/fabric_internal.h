@@ -26,6 +26,22 @@ namespace fab {
 #ifdef __CUDACC__
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Row p of a [n][4] float output: one 16-byte store when the array is
+// 16-byte aligned, else four 4-byte stores (the caller's array need only be
+// float-aligned; the test is the same for every thread, so it does not
+// diverge).
+__device__ __forceinline__ void store_row4(float *out, int64_t p, float x0, float x1, float x2, float x3) {
+  if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+    reinterpret_cast<float4 *>(out)[p] = make_float4(x0, x1, x2, x3);
+  } else {
+    float *q = out + 4 * p;
+    q[0] = x0;
+    q[1] = x1;
+    q[2] = x2;
+    q[3] = x3;
+  }
+}
 #endif
 
 // Raise a kernel's dynamic shared-memory limit once per (kernel, device):
@@ -218,6 +234,7 @@ void *scratch(fabric_ctx *ctx, size_t bytes);
 bool build_material(const fabric_material &m, DevMaterial *out, std::string *why);
 bool check_gbuffer(fabric_ctx *ctx, const fabric_gbuffer *g);
 bool is_aligned16(const void *p);
+bool is_aligned4(const void *p);
 // Free the host-pipeline streams, events and staging of a context.
 void host_pipeline_release(fabric_ctx *ctx);
 // Free the paper network's parameters and buffers of a context.

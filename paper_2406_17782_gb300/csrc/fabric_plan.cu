@@ -23,8 +23,8 @@ fabric_status fabric_plan_create(fabric_ctx *ctx, const fabric_segment *segs, in
     if (!check_gbuffer(ctx, &g.g)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "segment %d: %s", s,
                                                ctx->last_error.c_str());
     if (g.g.n > 0 && !g.rgb_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "segment %d: rgb output is NULL", s);
-    if (g.comps_dev && !is_aligned16(g.comps_dev))
-      return fail(ctx, FABRIC_ERR_INVALID_ARG, "segment %d: comps output must be 16-byte aligned", s);
+    if (g.comps_dev && !is_aligned4(g.comps_dev))
+      return fail(ctx, FABRIC_ERR_INVALID_ARG, "segment %d: comps output must be float-aligned", s);
     host[s] = SegDesc{g.g.u, g.g.v, g.g.radius, g.g.wi, g.g.wo, g.g.material, g.rgb_dev, g.comps_dev, g.g.n};
     tile0[s] = tiles;
     tiles += tc_tiles(g.g.n);

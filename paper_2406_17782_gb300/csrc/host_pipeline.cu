@@ -98,8 +98,8 @@ extern "C" fabric_status fabric_shade_neural_host(fabric_ctx *ctx, const fabric_
   if (!g_host->u || !g_host->v || !g_host->radius || !g_host->wi || !g_host->wo || !g_host->material || !rgb_host)
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "a G-buffer field or the rgb output is NULL");
   if (chunk_points < 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "chunk_points < 0");
-  if (comps_host && !is_aligned16(comps_host))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_host && !is_aligned4(comps_host))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (chunk_points == 0) {

@@ -41,8 +41,8 @@ extern "C" fabric_status fabric_shade_neural_noalloc(fabric_ctx *ctx, const fabr
     return fail(ctx, FABRIC_ERR_INVALID_ARG, "the no-allocation call runs the FP16, BF16 or FP8 tensor-core decoder only");
   if (g->n == 0) return FABRIC_OK;
   if (!rgb_dev || !latents_dev) return fail(ctx, FABRIC_ERR_INVALID_ARG, "rgb output or latents is NULL");
-  if (comps_dev && !is_aligned16(comps_dev))
-    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be 16-byte aligned");
+  if (comps_dev && !is_aligned4(comps_dev))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "comps output must be float-aligned");
   if (ctx->n_mat == 0) return fail(ctx, FABRIC_ERR_INVALID_ARG, "no materials set");
   if (tc_k1(ctx->n_mat) < 0)
     return fail(ctx, FABRIC_ERR_UNSUPPORTED, "tensor-core decoder supports at most 89 materials (have %d)",

@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kTile * WG, (W == 64 && WG == 2) ? 2 : 1) pn_d
             c4[2] = fmaxf(0.0f, (__expf(y[2]) - 1.0f) * (1.0f / kSpecK));
             c4[3] = fmaxf(0.0f, (__expf(y[3]) - 1.0f) * (1.0f / kSpecK));
           }
-          if (a.comps) reinterpret_cast<float4 *>(a.comps)[p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+          if (a.comps) store_row4(a.comps, p, c4[0], c4[1], c4[2], c4[3]);
           const float4 *al = reinterpret_cast<const float4 *>(alb + (mat < 0 ? 0 : mat) * 12);
           const float4 k0 = al[0], k1 = al[1], k2 = al[2];
           a.rgb[3 * p + 0] = k0.x * c4[0] + k0.w * c4[1] + k1.z * c4[2] + k2.y * c4[3];

@@ -298,7 +298,7 @@ __global__ void pn_head_kernel(const float *__restrict__ Y, const uint16_t *__re
     c4[2] = fmaxf(0.0f, expm1f(Y[4 * b + 2]) / kSpecK);
     c4[3] = fmaxf(0.0f, expm1f(Y[4 * b + 3]) / kSpecK);
   }
-  if (comps) reinterpret_cast<float4 *>(comps)[b] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+  if (comps) store_row4(comps, b, c4[0], c4[1], c4[2], c4[3]);
   if (rgb) {
     const DevMaterial &M = mats[m < n_mat ? m : 0];
     for (int ch = 0; ch < 3; ++ch)

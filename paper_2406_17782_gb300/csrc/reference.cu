@@ -315,10 +315,7 @@ __global__ void __launch_bounds__(256) reference_kernel(const RefArgs a) {
   } else {
     c[0] = c[1] = c[2] = c[3] = 0.0f;
   }
-  if (a.comps) {
-    float4 *dst = reinterpret_cast<float4 *>(a.comps) + p;
-    *dst = make_float4(c[0], c[1], c[2], c[3]);
-  }
+  if (a.comps) store_row4(a.comps, p, c[0], c[1], c[2], c[3]);
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
     float val = c[0];

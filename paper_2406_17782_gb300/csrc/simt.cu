@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(kFwdThreads) decoder_fp32_kernel(const FwdArgs
   if (mat >= a.n_lat || (need_mat && mat >= a.n_mat)) {
     atomicOr(a.status, kStatusBadMaterial);
     const float nan = __int_as_float(0x7FC00000);
-    if (a.y_raw) reinterpret_cast<float4 *>(a.y_raw)[p] = make_float4(nan, nan, nan, nan);
-    if (a.comps) reinterpret_cast<float4 *>(a.comps)[p] = make_float4(nan, nan, nan, nan);
+    if (a.y_raw) store_row4(a.y_raw, p, nan, nan, nan, nan);
+    if (a.comps) store_row4(a.comps, p, nan, nan, nan, nan);
     if (a.rgb)
       for (int ch = 0; ch < 3; ++ch) a.rgb[3 * p + ch] = nan;
     return;
@@ -89,10 +89,10 @@ __global__ void __launch_bounds__(kFwdThreads) decoder_fp32_kernel(const FwdArgs
     for (int i = 0; i < kHidden; ++i) acc = fmaf(W[kOffW4 + k * kHidden + i], bufB[i * kFwdThreads + t], acc);
     y[k] = acc;
   }
-  if (a.y_raw) reinterpret_cast<float4 *>(a.y_raw)[p] = make_float4(y[0], y[1], y[2], y[3]);
+  if (a.y_raw) store_row4(a.y_raw, p, y[0], y[1], y[2], y[3]);
   const float c0 = fmaxf(0.0f, y[0]), c1 = fmaxf(0.0f, y[1]);
   const float s0 = fmaxf(0.0f, expm1f(y[2]) / kSpecK), s1 = fmaxf(0.0f, expm1f(y[3]) / kSpecK);
-  if (a.comps) reinterpret_cast<float4 *>(a.comps)[p] = make_float4(c0, c1, s0, s1);
+  if (a.comps) store_row4(a.comps, p, c0, c1, s0, s1);
   if (a.rgb) {
     const DevMaterial &m = a.mats[mat];
     for (int ch = 0; ch < 3; ++ch)

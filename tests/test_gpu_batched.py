@@ -116,7 +116,7 @@ def test_plan_replays_from_cuda_graph(fab, prepared):
     plan.close()
 
 
-def test_plan_refuses_stale_state_and_bad_segments(fab, prepared):
+def test_plan_refuses_stale_state_and_takes_unaligned_outputs(fab, prepared):
     mats, dec, z, lat = prepared
     segs = make_segments([1000], seed=2)
     fab.prepare_neural(lat, "fp16")
@@ -127,6 +127,19 @@ def test_plan_refuses_stale_state_and_bad_segments(fab, prepared):
     with pytest.raises(FabricError):
         plan.shade("fp16")
     plan.close()
+    # components shifted by one float (not 16-byte aligned): accepted, four
+    # 4-byte stores per point, bitwise the same values
     _, g, rgb, comps = segs[0]
-    with pytest.raises(FabricError):
-        fab.plan([(g, rgb, comps.view(-1)[1:])])  # comps shifted by one float: not 16-byte aligned
+    fab.prepare_neural(lat, "fp16")
+    p1 = fab.plan([(g, rgb, comps)])
+    p1.shade("fp16")
+    fab.sync_status()
+    want = comps.clone()
+    p1.close()
+    buf = torch.full((comps.numel() + 1,), float("nan"), dtype=torch.float32, device="cuda")
+    shifted = buf[1:].view(comps.shape)
+    p2 = fab.plan([(g, rgb, shifted)])
+    p2.shade("fp16")
+    fab.sync_status()
+    assert shifted.data_ptr() % 16 != 0 and torch.equal(shifted, want)
+    p2.close()
