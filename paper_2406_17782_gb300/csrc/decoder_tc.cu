@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kTile * H * WG, 4 / WG) decoder_tc_kernel(cons
     }
   }
 
-  ok = !wg_sync_or<PT>(wg, !ok);   // one verdict per pipeline
+  ok = !wg_sync_or<PT>(wg, !ok);   // one outcome per pipeline
 teardown:
   if (!ok) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);

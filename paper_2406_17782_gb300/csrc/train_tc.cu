@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     }
   };
   // all threads: make the stores visible, then the lead issues `issue` and
-  // everyone waits for the products.  The verdict of each wait travels with
+  // everyone waits for the products.  The outcome of each wait travels with
   // the next round's barrier (or the one after the tile loop), so a round
   // costs one CTA barrier; false: some thread's previous wait expired.
   auto round = [&](auto issue) -> bool {
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     }
     first = false;
   }
-  ok = __syncthreads_and(ok && !fail);   // one verdict for the CTA before the barriers below
+  ok = __syncthreads_and(ok && !fail);   // one outcome for the CTA before the barriers below
   // ---- this CTA's gradient partials: lane j holds row j of every dW^T;
   // the two halves take alternate 16-column chunks
   float *out = a.partial + (int64_t)blockIdx.x * a.partial_width;
