@@ -522,10 +522,8 @@ fabric_status fabric_paper_get_gradient(fabric_ctx *ctx, float *grad);
 
 /*
  * The paper has no counterpart to this call; it exists for callers that may
- * not allocate device memory while they draw: a renderer that captures its
- * frame into a CUDA graph (cudaMalloc is not allowed during stream capture),
- * or a host application that owns all device memory and forbids plug-ins to
- * allocate at draw time.
+ * not allocate device memory while they draw, such as a host application
+ * that owns all device memory and forbids plug-ins to allocate at draw time.
  *
  * Same arguments, outputs and errors as fabric_shade_neural with
  * prec = FABRIC_PREC_FP16, FABRIC_PREC_BF16 or FABRIC_PREC_FP8 (anything else
@@ -540,8 +538,8 @@ fabric_status fabric_paper_get_gradient(fabric_ctx *ctx, float *grad);
  *    (about 43 KiB) fit the array, which the library checks when it is
  *    compiled; a table that did not fit would be rejected with
  *    FABRIC_ERR_INVALID_ARG.
- *  - The first call on each device resolves the array's device address;
- *    make that first call before any stream capture.
+ *  - The first call on each device looks up the array's device address (a
+ *    host-side query that allocates nothing); later calls reuse it.
  *  - All calls share the one array and overwrite all of it that they read,
  *    so nothing needs clearing between calls, but calls that overlap on the
  *    GPU (other streams, other host threads, other contexts on the same
