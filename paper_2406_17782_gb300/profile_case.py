@@ -8,6 +8,7 @@ for profilers (ncu) and quick timing:
   python -m paper_2406_17782_gb300.profile_case batched [--precision fp16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case paper [--width 128] [--precision fp16] [--reps 3]
   python -m paper_2406_17782_gb300.profile_case paper-train [--width 128] [--batch 65536] [--reps 3]
+  python -m paper_2406_17782_gb300.profile_case reference --spp 16 --visibility
 
 The workload is the 1920 x 1080 G-buffer of eight weave materials (random-init
 networks); the training case uses a batch of queries over 256 training
@@ -47,6 +48,7 @@ def main(argv=None):
     ap.add_argument("--train-precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--elements", type=int, default=1 << 25, help="array length (error)")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--visibility", action="store_true", help="the reference with the proposed visibility model")
     args = ap.parse_args(argv)
     fab = Fabric(0)
     mats = W.frame_materials()
@@ -100,6 +102,7 @@ def main(argv=None):
         g = GBuffer.from_numpy(W.frame_gbuffer())
         rgb = torch.empty((g.n, 3), dtype=torch.float32, device=fab.device)
         if args.case == "reference":
+            fab.set_visibility(args.visibility)
             fn = lambda: fab.shade_reference(g, args.spp, args.spp, 11, out_rgb=rgb)
         else:
             fab.prepare_neural(fab.encode_params(mats), args.precision)
