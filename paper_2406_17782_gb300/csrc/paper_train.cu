@@ -344,15 +344,17 @@ __global__ void pn_loss_final_kernel(const double *__restrict__ part, int n, dou
 // [s][m][W].  One CTA of 256 threads per segment and 32 columns: the CTA
 // sorts the segment's (material, row) keys in shared memory (bitonic) while
 // its 512 x 32 slice of D lands in shared memory (all loads in flight
-// together), then warp 0 walks the sorted rows, each lane adding its
-// column's rows of one material in row order in a register and storing the
-// sum when the material changes (zeros for the materials the segment
+// together), finds each material's run in the sorted keys, and then warp w
+// takes materials w, w + 8, ...: each lane adds its column's rows of the
+// material in row order in a register (zero for a material the segment
 // lacks).  Every sum runs in row order (bitwise repeatable).
 constexpr int kSumRows = 512;     // rows per segment
 constexpr int kSumThreads = 256;
 constexpr int kSumLd = 33;        // shared row stride of the D slice (conflict-free column reads)
 constexpr uint32_t kNoMat = 0xFFFFu;
-constexpr size_t kSumSmem = (size_t)kSumRows * kSumLd * sizeof(float);
+constexpr size_t kSumTileBytes = (size_t)kSumRows * kSumLd * sizeof(float);
+// the D slice, then each material's first and end index in the sorted keys
+inline size_t sum_smem(int n_mat) { return kSumTileBytes + 2 * sizeof(int) * (size_t)n_mat; }
 
 __global__ void __launch_bounds__(kSumThreads) pn_material_sums_kernel(const uint16_t *__restrict__ mat, int64_t n,
                                                                        const float *__restrict__ D, int W,
@@ -395,34 +397,38 @@ __global__ void __launch_bounds__(kSumThreads) pn_material_sums_kernel(const uin
       __syncthreads();
     }
   }
-  if (warp != 0) return;
-  const int c = c0 + lane;
-  const bool live = c < W;
-  float *out = part + (int64_t)blockIdx.x * n_mat * W + (live ? c : 0);
-  int cur = 0;   // next material whose sum is still to be stored
-  float s = 0.0f;
-  for (int i0 = 0; i0 < rows; i0 += 8) {
-    float v[8];
-    uint32_t kk[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      kk[q] = i0 + q < rows ? key[i0 + q] : (kNoMat << 16);
-      v[q] = tile[(kk[q] & 0xFFFFu) * kSumLd + lane];
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int m = (int)(kk[q] >> 16);
-      if (m == (int)kNoMat) break;
-      for (; cur < m; ++cur) {   // store the finished material, zeros for the absent ones
-        if (live) out[(int64_t)cur * W] = s;
-        s = 0.0f;
-      }
-      s += v[q];
-    }
+  // each material's run [first, end) in the sorted keys (first = -1: absent)
+  int *first = reinterpret_cast<int *>(tile + kSumRows * kSumLd);
+  int *end = first + n_mat;
+  for (int m = tid; m < n_mat; m += kSumThreads) first[m] = -1;
+  __syncthreads();
+  for (int i = tid; i < rows; i += kSumThreads) {
+    const uint32_t m = key[i] >> 16;
+    if (m == kNoMat) continue;
+    if (i == 0 || (key[i - 1] >> 16) != m) first[m] = i;
+    if (i == rows - 1 || (key[i + 1] >> 16) != m) end[m] = i + 1;
   }
-  for (; cur < n_mat; ++cur) {
-    if (live) out[(int64_t)cur * W] = s;
-    s = 0.0f;
+  __syncthreads();
+  // warp w: materials w, w + 8, ...; lane: one column, the material's rows in row order
+  const int c = c0 + lane;
+  if (c >= W) return;
+  float *out = part + (int64_t)blockIdx.x * n_mat * W + c;
+  for (int m = warp; m < n_mat; m += kSumThreads / 32) {
+    float s = 0.0f;
+    const int i0 = first[m];
+    if (i0 >= 0) {
+      const int i1 = end[m];
+      int i = i0;
+      for (; i + 4 <= i1; i += 4) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = tile[(key[i + q] & 0xFFFFu) * kSumLd + lane];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += v[q];
+      }
+      for (; i < i1; ++i) s += tile[(key[i] & 0xFFFFu) * kSumLd + lane];
+    }
+    out[(int64_t)m * W] = s;
   }
 }
 
@@ -732,8 +738,8 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   PN_TRY(wgrad(D3, w, w, P.X0, KX0, KX0, B, part, gd + o.S1, gd + o.s1, s));
   // ---- latent gradient: per-material sums of dg1 in row order, times S1's latent block
   {
-    PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), (int)kSumSmem));
-    pn_material_sums_kernel<<<dim3(segs, (w + 31) / 32), kSumThreads, kSumSmem, s>>>(q.material, B, D3, w, n_mat,
+    PN_TRY(ensure_max_dyn_smem(reinterpret_cast<const void *>(pn_material_sums_kernel), (int)sum_smem(1600)));
+    pn_material_sums_kernel<<<dim3(segs, (w + 31) / 32), kSumThreads, sum_smem(n_mat), s>>>(q.material, B, D3, w, n_mat,
                                                                                        msum);
     PN_TRY(cudaGetLastError());
     pn_segment_total_kernel<<<(n_mat * w + 255) / 256, 256, 0, s>>>(msum, n_mat, segs, w, G);
