@@ -66,7 +66,7 @@ FLOP_PER_POINT = 2 * (39 * 64 + 64 * 64 + 64 * 64 + 64 * 4)      # 21,888 (layer
 BYTES_PER_POINT = 38 + 12                                          # G-buffer record in, RGB out
 # DRAM bytes (read + write) of one FP16 decoder launch on this frame, from an
 # ncu capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_FP16 = 78_853_376 + 6_708_992
+TRAFFIC_FP16 = 78_858_240 + 7_003_392
 WORKLOAD = "1920x1080 G-buffer, 8 weave materials (one per 240-px band), random-init decoder"
 
 
