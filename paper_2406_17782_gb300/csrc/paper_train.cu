@@ -437,8 +437,17 @@ __global__ void pn_segment_total_kernel(const float *__restrict__ part, int n_ma
                                         float *__restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_mat * W) return;
+  const int64_t stride = (int64_t)n_mat * W;
   float s = 0.0f;
-  for (int k = 0; k < segs; ++k) s += part[(int64_t)k * n_mat * W + e];
+  int k = 0;
+  for (; k + 8 <= segs; k += 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = part[(k + q) * stride + e];   // eight loads in flight, added in order
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += v[q];
+  }
+  for (; k < segs; ++k) s += part[k * stride + e];
   G[e] = s;
 }
 
@@ -451,42 +460,100 @@ static_assert(oe3 + kPnLatent == kPnEncParams, "encoder layout");
 
 __device__ __forceinline__ float elrelu(float x) { return x > 0.0f ? x : kPnSlope * x; }
 
-// One material per CTA of 128 threads: features, h1, h2 (post-activation)
-// and z; h1, h2 and the features are kept for the backward pass.
-__global__ void __launch_bounds__(kEH) pn_enc_fwd_kernel(const fabric_material *__restrict__ raw,
+// Four materials per CTA of 128 threads: features, h1, h2 (post-activation)
+// and z; h1, h2 and the features are kept for the backward pass.  Thread j
+// loads row j of a layer's weights into registers once (all loads in flight
+// together) and applies it to the four materials; every output is a chain
+// of fmaf over its inputs in order, from the bias.
+constexpr int kEncG = 4;
+
+__global__ void __launch_bounds__(kEH) pn_enc_fwd_kernel(const fabric_material *__restrict__ raw, int n_mat,
                                                          const float *__restrict__ enc, float *__restrict__ F,
                                                          float *__restrict__ H1, float *__restrict__ H2,
                                                          float *__restrict__ z) {
-  __shared__ float f[kEI], h1[kEH], h2[kEH];
-  const int m = blockIdx.x, j = threadIdx.x;
-  if (j < kEI) {
-    const fabric_material &M = raw[m];
-    float v;
-    if (j < kPatternSlots)
-      v = M.pattern_id == j ? 1.0f : 0.0f;
-    else {
-      const int q = j - kPatternSlots;
-      v = q == 0 ? M.twist_deg / 30.0f : q == 1 ? M.incl_deg / 45.0f : q == 2 ? M.alpha[0] : q == 3 ? M.beta[0]
-        : q == 4 ? M.alpha[1] : M.beta[1];
+  __shared__ float f[kEncG][kEI];
+  __shared__ float h1[kEncG][kEH], h2[kEncG][kEH];
+  const int m0 = blockIdx.x * kEncG, j = threadIdx.x;
+  const int nm = min(kEncG, n_mat - m0);
+  for (int e = j; e < kEncG * kEI; e += kEH) {
+    const int g = e / kEI, i = e % kEI;
+    float v = 0.0f;
+    if (g < nm) {
+      const fabric_material &M = raw[m0 + g];
+      if (i < kPatternSlots) {
+        v = M.pattern_id == i ? 1.0f : 0.0f;
+      } else {
+        const int q = i - kPatternSlots;
+        v = q == 0 ? M.twist_deg / 30.0f : q == 1 ? M.incl_deg / 45.0f : q == 2 ? M.alpha[0] : q == 3 ? M.beta[0]
+          : q == 4 ? M.alpha[1] : M.beta[1];
+      }
+      if (F) F[(int64_t)(m0 + g) * kEI + i] = v;
     }
-    f[j] = v;
-    if (F) F[m * kEI + j] = v;
+    f[g][i] = v;
   }
   __syncthreads();
-  float a = enc[oe1 + j];
-  for (int i = 0; i < kEI; ++i) a = fmaf(enc[oE1 + j * kEI + i], f[i], a);
-  h1[j] = elrelu(a);
+  float a[kEncG];
+  {
+    float c[kEI];
+#pragma unroll
+    for (int i = 0; i < kEI; ++i) c[i] = enc[oE1 + j * kEI + i];
+    const float b = enc[oe1 + j];
+#pragma unroll
+    for (int g = 0; g < kEncG; ++g) {
+      a[g] = b;
+#pragma unroll
+      for (int i = 0; i < kEI; ++i) a[g] = fmaf(c[i], f[g][i], a[g]);
+      h1[g][j] = elrelu(a[g]);
+    }
+  }
   __syncthreads();
-  a = enc[oe2 + j] + h1[j];   // skip before the last activation
-  for (int i = 0; i < kEH; ++i) a = fmaf(enc[oE2 + j * kEH + i], h1[i], a);
-  h2[j] = elrelu(a);
-  if (H1) H1[m * kEH + j] = h1[j];
-  if (H2) H2[m * kEH + j] = h2[j];
+  {
+    float c[kEH];
+    const float4 *w4 = reinterpret_cast<const float4 *>(enc + oE2 + j * kEH);
+#pragma unroll
+    for (int i4 = 0; i4 < kEH / 4; ++i4) {
+      const float4 t = w4[i4];
+      c[4 * i4] = t.x;
+      c[4 * i4 + 1] = t.y;
+      c[4 * i4 + 2] = t.z;
+      c[4 * i4 + 3] = t.w;
+    }
+    const float b = enc[oe2 + j];
+#pragma unroll
+    for (int g = 0; g < kEncG; ++g) {
+      a[g] = b + h1[g][j];   // skip before the last activation
+#pragma unroll
+      for (int i = 0; i < kEH; ++i) a[g] = fmaf(c[i], h1[g][i], a[g]);
+      h2[g][j] = elrelu(a[g]);
+      if (g < nm) {
+        if (H1) H1[(int64_t)(m0 + g) * kEH + j] = h1[g][j];
+        if (H2) H2[(int64_t)(m0 + g) * kEH + j] = h2[g][j];
+      }
+    }
+  }
   __syncthreads();
-  if (j < kPnLatent) {
-    a = enc[oe3 + j];
-    for (int i = 0; i < kEH; ++i) a = fmaf(enc[oE3 + j * kEH + i], h2[i], a);
-    z[m * kPnLatent + j] = a;
+  // z: thread j takes output k = j % 64 of materials g = j / 64 and g + 2
+  {
+    const int k = j % kPnLatent, g0 = j / kPnLatent;
+    float c[kEH];
+    const float4 *w4 = reinterpret_cast<const float4 *>(enc + oE3 + k * kEH);
+#pragma unroll
+    for (int i4 = 0; i4 < kEH / 4; ++i4) {
+      const float4 t = w4[i4];
+      c[4 * i4] = t.x;
+      c[4 * i4 + 1] = t.y;
+      c[4 * i4 + 2] = t.z;
+      c[4 * i4 + 3] = t.w;
+    }
+    const float b = enc[oe3 + k];
+#pragma unroll
+    for (int gg = 0; gg < kEncG / 2; ++gg) {
+      const int g = g0 + 2 * gg;
+      float acc = b;
+#pragma unroll
+      for (int i = 0; i < kEH; ++i) acc = fmaf(c[i], h2[g][i], acc);
+      if (g < nm) z[(int64_t)(m0 + g) * kPnLatent + k] = acc;
+    }
   }
 }
 
@@ -509,32 +576,73 @@ __global__ void __launch_bounds__(kEH) pn_enc_bwd_kernel(const float *__restrict
   DA1[m * kEH + j] = g * (H1[m * kEH + j] > 0.0f ? 1.0f : kPnSlope);
 }
 
-// One thread per encoder parameter: sums over materials in order.
-__global__ void pn_enc_grad_kernel(int n_mat, const float *__restrict__ F, const float *__restrict__ H1,
-                                   const float *__restrict__ H2, const float *__restrict__ dz,
-                                   const float *__restrict__ DA1, const float *__restrict__ DA2,
-                                   float *__restrict__ genc) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= kPnEncParams) return;
-  const float *dv;
-  const float *xv = nullptr;
-  int ldd, ldx = 0, o, i = -1;
-  if (p < oe1) {
-    o = p / kEI; i = p % kEI; dv = DA1; ldd = kEH; xv = F; ldx = kEI;
-  } else if (p < oE2) {
-    o = p - oe1; dv = DA1; ldd = kEH;
-  } else if (p < oe2) {
-    o = (p - oE2) / kEH; i = (p - oE2) % kEH; dv = DA2; ldd = kEH; xv = H1; ldx = kEH;
-  } else if (p < oE3) {
-    o = p - oe2; dv = DA2; ldd = kEH;
-  } else if (p < oe3) {
-    o = (p - oE3) / kEH; i = (p - oE3) % kEH; dv = dz; ldd = kPnLatent; xv = H2; ldx = kEH;
-  } else {
-    o = p - oe3; dv = dz; ldd = kPnLatent;
+// Encoder parameter gradients as sums over materials of outer products,
+// G[o][i] = sum_m L[m][o] R[m][i] (R = 1 for a bias): E1 (da1, features),
+// e1, E2 (da2, h1), e2, E3 (dz, h2), e3.  A CTA of 256 threads takes a
+// 32 x 32 tile of one block, stages 64 materials' slices of L and R in
+// shared memory at a time, and thread (w, c) keeps outputs 4w..4w+3 of
+// column c, each a chain of fmaf over the materials in order.
+constexpr int kEncGradChunk = 64;
+
+__host__ __device__ constexpr int pn_tiles(int rows, int cols) { return ((rows + 31) / 32) * ((cols + 31) / 32); }
+constexpr int kPnEncGradTiles = pn_tiles(kEH, kEI) + pn_tiles(kEH, 1) + pn_tiles(kEH, kEH) + pn_tiles(kEH, 1) +
+                                pn_tiles(kPnLatent, kEH) + pn_tiles(kPnLatent, 1);
+
+__global__ void __launch_bounds__(256) pn_enc_grad_kernel(int n_mat, const float *__restrict__ F,
+                                                          const float *__restrict__ H1, const float *__restrict__ H2,
+                                                          const float *__restrict__ dz,
+                                                          const float *__restrict__ DA1,
+                                                          const float *__restrict__ DA2, float *__restrict__ genc) {
+  __shared__ __align__(16) float sl[kEncGradChunk][32];
+  __shared__ float sr[kEncGradChunk][32];
+  // which block, and which 32 x 32 tile of it
+  const float *L = DA1, *R = F;
+  int ldl = kEH, ldr = kEI, rows = kEH, cols = kEI, out = oE1;
+  int t = blockIdx.x;
+  const int t0 = pn_tiles(kEH, kEI), t1 = t0 + pn_tiles(kEH, 1), t2 = t1 + pn_tiles(kEH, kEH),
+            t3 = t2 + pn_tiles(kEH, 1), t4 = t3 + pn_tiles(kPnLatent, kEH);
+  if (t >= t4) {
+    L = dz; ldl = kPnLatent; R = nullptr; rows = kPnLatent; cols = 1; out = oe3; t -= t4;
+  } else if (t >= t3) {
+    L = dz; ldl = kPnLatent; R = H2; ldr = kEH; rows = kPnLatent; cols = kEH; out = oE3; t -= t3;
+  } else if (t >= t2) {
+    L = DA2; R = nullptr; cols = 1; out = oe2; t -= t2;
+  } else if (t >= t1) {
+    L = DA2; R = H1; ldr = kEH; cols = kEH; out = oE2; t -= t1;
+  } else if (t >= t0) {
+    R = nullptr; cols = 1; out = oe1; t -= t0;
   }
-  float s = 0.0f;
-  for (int m = 0; m < n_mat; ++m) s = fmaf(dv[m * ldd + o], xv ? xv[m * ldx + i] : 1.0f, s);
-  genc[p] = s;
+  const int ct = (cols + 31) / 32;
+  const int r0 = (t / ct) * 32, c0 = (t % ct) * 32;
+  const int tid = threadIdx.x, c = tid & 31, w = tid >> 5;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int m0 = 0; m0 < n_mat; m0 += kEncGradChunk) {
+    const int mc = min(kEncGradChunk, n_mat - m0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kEncGradChunk * 32 / 256; ++q) {
+      const int e = tid + 256 * q, mm = e >> 5, k = e & 31;
+      const bool in = mm < mc;
+      sl[mm][k] = in && r0 + k < rows ? L[(int64_t)(m0 + mm) * ldl + r0 + k] : 0.0f;
+      sr[mm][k] = !in ? 0.0f : !R ? 1.0f : (c0 + k < cols ? R[(int64_t)(m0 + mm) * ldr + c0 + k] : 0.0f);
+    }
+    __syncthreads();
+    for (int mm = 0; mm < mc; ++mm) {
+      const float4 a = reinterpret_cast<const float4 *>(sl[mm])[w];
+      const float x = sr[mm][c];
+      acc[0] = fmaf(a.x, x, acc[0]);
+      acc[1] = fmaf(a.y, x, acc[1]);
+      acc[2] = fmaf(a.z, x, acc[2]);
+      acc[3] = fmaf(a.w, x, acc[3]);
+    }
+  }
+  if (c0 + c < cols) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = r0 + 4 * w + k;
+      if (r < rows) genc[out + r * cols + c0 + c] = acc[k];
+    }
+  }
 }
 
 template <bool AR, bool BR, bool B_ONES>
@@ -713,7 +821,7 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
     if (e != cudaSuccess) return e;   \
   } while (0)
   // ---- encoder, inputs and forward
-  pn_enc_fwd_kernel<<<n_mat, kEH, 0, s>>>(raw, enc, F, EH1, EH2, z);
+  pn_enc_fwd_kernel<<<(n_mat + kEncG - 1) / kEncG, kEH, 0, s>>>(raw, n_mat, enc, F, EH1, EH2, z);
   PN_TRY(cudaGetLastError());
   PN_TRY(pn_forward(P, q, z, n_mat, dec, status, s));
   // ---- loss
@@ -754,7 +862,7 @@ cudaError_t launch_paper_train(int w, int ablation, const fabric_gbuffer &q, con
   // ---- encoder backward
   pn_enc_bwd_kernel<<<n_mat, kEH, 0, s>>>(enc, EH1, EH2, dz, DA1, DA2);
   PN_TRY(cudaGetLastError());
-  pn_enc_grad_kernel<<<(kPnEncParams + 255) / 256, 256, 0, s>>>(n_mat, F, EH1, EH2, dz, DA1, DA2, ge);
+  pn_enc_grad_kernel<<<kPnEncGradTiles, 256, 0, s>>>(n_mat, F, EH1, EH2, dz, DA1, DA2, ge);
   PN_TRY(cudaGetLastError());
 #undef PN_TRY
   return cudaSuccess;
@@ -784,7 +892,7 @@ cudaError_t launch_paper_forward(int w, int ablation, const fabric_gbuffer &g, c
 }
 
 cudaError_t launch_paper_encoder(const fabric_material *raw, int n_mat, const float *enc, float *z, cudaStream_t s) {
-  pn_enc_fwd_kernel<<<n_mat, kEH, 0, s>>>(raw, enc, nullptr, nullptr, nullptr, z);
+  pn_enc_fwd_kernel<<<(n_mat + kEncG - 1) / kEncG, kEH, 0, s>>>(raw, n_mat, enc, nullptr, nullptr, nullptr, z);
   return cudaGetLastError();
 }
 
