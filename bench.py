@@ -234,6 +234,10 @@ def main():
     ap.add_argument("--paper-steps", type=int, default=20000,
                     help="training steps of the paper's decoder structure in the quality section")
     ap.add_argument("--paper-width", type=int, default=128, choices=[64, 128])
+    ap.add_argument("--visibility-queries", type=int, default=1 << 23,
+                    help="training queries generated with the proposed visibility model in the quality section")
+    ap.add_argument("--visibility-steps", type=int, default=60000,
+                    help="training steps of the 3x64 decoder on the data with the visibility model")
     ap.add_argument("--ablation-steps", type=int, default=10000,
                     help="training steps of each structure in the ablation of the paper's decoder (width 64)")
     args = ap.parse_args()
@@ -475,6 +479,80 @@ def measure_ablation(fab, torch, W, T, tm, g_tr, target, ms_host, args):
     return out
 
 
+def measure_visibility_quality(fab, torch, W, GBuffer, T, tm, gbufs, rgbs, ms_host, args, stream):
+    """The proposed inter-yarn visibility model end to end: training data,
+    ground truth and reference ladder all with V on; the 3x64 decoder (BF16
+    kernels) and the paper's structure at width 128 (FP32 kernels), both
+    trained on that data with the rendered-space loss, against the reference
+    at 1-256 spp, on the 1080p and multi-scale frames."""
+    fab.set_visibility(True)
+    try:
+        t0 = time.time()
+        g_tr, target = T.generate_dataset(fab, tm, args.visibility_queries, (64, 32), frame_share=0.5)
+        torch.cuda.synchronize()
+        t_data = time.time() - t0
+        fab.set_train_loss("rendered")
+        # the 3x64 decoder
+        fab.set_params(W.decoder_init(weight_bound="small"), W.encoder_init(weight_bound="small"))
+        fab.set_train_precision("bf16")
+        t0 = time.time()
+        T.train(fab, tm, g_tr, target, args.visibility_steps, 65536, args.quality_lr, log_every=1000, verbose=False)
+        torch.cuda.synchronize()
+        t_train = time.time() - t0
+        fab.set_train_precision("fp32")
+        # the paper's structure
+        pw = args.paper_width
+        fab.paper_set_params(pw, W.paper_decoder_init(pw, weight_bound="small"),
+                             W.paper_encoder_init(weight_bound="small"))
+        t0 = time.time()
+        T.train(fab, tm, g_tr, target, args.paper_steps, 65536, args.quality_lr, log_every=1000, verbose=False,
+                paper=True)
+        torch.cuda.synchronize()
+        t_paper = time.time() - t0
+        fab.set_train_loss("eq11")
+        del g_tr, target
+        out = {"model": "proposed inter-yarn visibility (ray march through the yarn height field)",
+               "training": {"queries": args.visibility_queries, "data_spp": 2048, "loss": "rendered",
+                            "data_seconds": t_data,
+                            "decoder_3x64": {"steps": args.visibility_steps, "precision": "bf16",
+                                             "train_seconds": t_train},
+                            "paper_structure": {"width": pw, "steps": args.paper_steps, "precision": "fp32",
+                                                "train_seconds": t_paper}}}
+        mats = W.frame_materials()
+        fab.set_materials(mats)
+        copies = len(gbufs)
+        fab.prepare_neural(fab.encode_params(mats), "fp16")
+        ms_n = timed(torch, stream, lambda k: fab.shade_neural_prepared(gbufs[k % copies], "fp16",
+                                                                       out_rgb=rgbs[k % copies]), 50)
+        fab.paper_prepare(fab.paper_encode_params(mats), "fp16")
+        ms_p = timed(torch, stream, lambda k: fab.paper_shade_prepared(gbufs[k % copies], "fp16",
+                                                                      out_rgb=rgbs[k % copies]), 20)
+        ms_dev = GBuffer.from_numpy(ms_host)
+        for name, gb_host, gb_dev, gt in (("frame_1080p", None, gbufs[0], (32, 32)),
+                                           ("multiscale_1080p", ms_host, ms_dev, (64, 64))):
+            rm = T.frame_rmse(fab, "fp16", gt_spp=gt, ref_spps=(1, 2, 4, 8, 16), gbuf=gb_host)
+            rp = T.frame_rmse(fab, "fp16", gt_spp=gt, ref_spps=(), gbuf=gb_host, paper=True)
+            ladder = []
+            for sp in (1, 2, 4, 8, 16):
+                fab.shade_reference(gb_dev, sp, sp, 5, out_rgb=rgbs[0])
+                ms_r = timed(torch, stream, lambda k: fab.shade_reference(gb_dev, sp, sp, 5 + k, out_rgb=rgbs[0]), 3)
+                ladder.append(_ladder_entry(sp, rm[f"reference_{sp * sp}spp"], ms_r))
+            entry = {"reference": ladder,
+                     "ground_truth": {"spp": gt[0] * gt[1], "gt_noise_fp": rm["gt_noise_fp"],
+                                      "gt_noise_lit": rm["gt_noise"]}}
+            for net, r, ms in (("decoder_3x64", rm, ms_n), ("paper_structure", rp, ms_p)):
+                neural = {k: r["neural"][k] for k in ("rmse_fp", "rel_l2_fp", "rmse_tm")}
+                neural.update(rmse_lit=r["neural"]["rmse"], ms=ms)
+                entry[net] = {"neural_fp16": neural, "target_fp": _target(neural, ladder, "rmse_fp"),
+                              "target_lit": _target(neural, ladder, "rmse_lit")}
+            out[name] = entry
+        del ms_dev
+        fab.sync_status()
+        return out
+    finally:
+        fab.set_visibility(False)
+
+
 def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     """Train the decoder and encoder with the library's kernels on data from
     the reference kernel (once with the paper's Eq. 11 loss, once with the
@@ -596,6 +674,7 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
     }
     ablation = measure_ablation(fab, torch, W, T, tm, g_tr, target, ms_host, args)
     del g_tr, target
+    visibility = measure_visibility_quality(fab, torch, W, GBuffer, T, tm, gbufs, rgbs, ms_host, args, stream)
     interp = measure_interpolation(fab, torch, W, GBuffer, gbufs, rgbs, stream)
     best = min(("eq11", "rendered", "paper_structure"), key=lambda k: runs[k]["neural_fp16"]["rmse_fp"])
     return {
@@ -628,6 +707,7 @@ def measure_quality(fab, torch, W, GBuffer, gbufs, rgbs, args, stream):
         "loss_rendered": runs["rendered"],
         "paper_structure": runs["paper_structure"],
         "paper_ablation": ablation,
+        "with_visibility_model": visibility,
         "training": {"queries": args.quality_queries, "data_spp": 2048, "steps": args.quality_steps,
                      "batch": 65536, "lr": args.quality_lr, "precision": args.quality_precision,
                      "data_seconds": t_data},
