@@ -56,10 +56,13 @@ __device__ __forceinline__ void query_features(const fabric_gbuffer &g, int64_t 
 }
 
 // d loss / d y_k for output k of one query (scaled by inv_batch); adds the
-// query's loss term to *loss.  y: raw head; tg: target component; wz: the
-// query's <wi . n_s> (rendered-space loss only).
-__device__ __forceinline__ float loss_grad(int k, float y, float tg, float wz, int mode, float inv_batch,
-                                           double *loss) {
+// query's loss term to *loss in the accumulator's type T.  y: raw head; tg:
+// target component; wz: the query's <wi . n_s> (rendered-space loss only).
+// T = double adds every term in FP64; T = float lets a caller sum a query's
+// four terms in FP32 and only the per-query totals in FP64 (FP64 arithmetic
+// issues at a small fraction of the FP32 rate).
+template <typename T>
+__device__ __forceinline__ float loss_grad(int k, float y, float tg, float wz, int mode, float inv_batch, T *loss) {
   if (mode == FABRIC_LOSS_RENDERED) {
     // ((c_hat - c) max(<wi.n_s>, 0))^2, c_hat = y (C) or (exp(min(y, 12)) - 1) / k (S)
     const float w = fmaxf(wz, 0.0f);
@@ -72,13 +75,13 @@ __device__ __forceinline__ float loss_grad(int k, float y, float tg, float wz, i
       dc = y < kYClamp ? expf(ys) * (1.0f / kSpecK) : 0.0f;
     }
     const float diff = (c - tg) * w;
-    *loss += (double)diff * (double)diff * (double)inv_batch;
+    *loss += (T)diff * (T)diff * (T)inv_batch;
     return 2.0f * diff * w * dc * inv_batch;
   }
   const float tt = k < 2 ? tg : logf(kSpecK * tg + 1.0f);   // g(x) = ln(k x + 1), Eq. 9
   const float lam = k < 2 ? kLambdaC : kLambdaS;
   const float diff = y - tt;
-  *loss += (double)lam * (double)diff * (double)diff * (double)inv_batch;
+  *loss += (T)lam * (T)diff * (T)diff * (T)inv_batch;
   return 2.0f * lam * diff * inv_batch;
 }
 

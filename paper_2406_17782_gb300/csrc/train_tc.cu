@@ -1,6 +1,7 @@
 // train_tc.cu -- the decoder's training forward and backward on the tensor
 // cores (tcgen05, BF16 operands, FP32 accumulation), one 128-query tile per
-// step of a persistent loop; one CTA of one warpgroup per SM.
+// step of a persistent loop; one CTA of two warpgroups per SM, two threads
+// per query row (warps w and w + 4 share lane quadrant w).
 //
 // Per tile, with one query per thread and tile row:
 //   forward   x = [z | q | 1] (K = 80) -> h1 -> h2 -> h3 -> y (N = 16, 4 used):
@@ -15,6 +16,10 @@
 //             all of the CTA's tiles in tensor memory; the bias gradients
 //             come out as the row of the constant-one input.
 //   latent    dz rows = da_1 W1[:, :32] (FP32, for the per-material sums).
+// Thread 0 issues the products an epilogue reads and thread 128 the weight-
+// gradient products, which nothing reads until the tile loop ends: each dW
+// chain is waited for only before the shared-memory operand it reads is
+// rewritten (the da operands alternate between two buffers for this).
 // At the end each CTA writes its gradient partials; the fixed-order
 // reduction over CTAs, the encoder backward and Adam are shared with the FP32
 // path.  Tensor-memory columns: D [0, 64), A [64, 104), dW1^T [128, 192),
@@ -56,11 +61,16 @@ constexpr uint32_t kSmXT = (kBlob + 1023) / 1024 * 1024;   // x^T: 128 inputs x 
 constexpr uint32_t kSmH1T = kSmXT + 128 * 128 * 2;
 constexpr uint32_t kSmH2T = kSmH1T + 128 * 128 * 2;
 constexpr uint32_t kSmH3T = kSmH2T + 128 * 128 * 2;
-constexpr uint32_t kSmDaT = kSmH3T + 128 * 128 * 2;        // da: 64 outputs x 128 queries
-constexpr uint32_t kSmTotal = kSmDaT + 64 * 128 * 2;
+constexpr uint32_t kSmDaA = kSmH3T + 128 * 128 * 2;        // da: 64 outputs x 128 queries, two buffers
+constexpr uint32_t kSmDaB = kSmDaA + 64 * 128 * 2;          // (layers alternate between them)
+constexpr uint32_t kSmTotal = kSmDaB + 64 * 128 * 2;
 constexpr size_t kDynSmem = 1024 /* align */ + 1024 /* header */ + kSmTotal;
 
 constexpr uint32_t kColD = 0, kColA = 64, kColW1 = 128, kColW2 = 192, kColW3 = 256, kColW4 = 320;
+
+// Thread 0 issues the products the epilogues read; thread 128 (the first
+// thread of half 1) issues the weight-gradient products.
+constexpr int kDwIssuer = 128;
 
 // Instruction-descriptor bits: A and B read MN-major (transposed).
 constexpr uint32_t kTransA = 1u << 15, kTransB = 1u << 16;
@@ -81,6 +91,21 @@ __host__ __device__ constexpr uint32_t mn_offset(int j, int r, int width) {
 // BF16 pairs, into an MN-major operand of the given width.
 __device__ __forceinline__ void st_row8(uint8_t *base, int j0, int r, int width, const uint32_t *w4) {
   *reinterpret_cast<uint4 *>(base + mn_offset(j0, r, width)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+}
+
+// Global loads that stay where they are written: volatile asm keeps the
+// compiler from moving them to their first use, so that they are in flight
+// during the work in between.
+__device__ __forceinline__ float ld_pinned(const float *p) {
+  float v;
+  asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ int ld_pinned_u16(const uint16_t *p) {
+  unsigned short v;
+  asm volatile("ld.global.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return (int)v;
 }
 
 __device__ __forceinline__ void put(uint8_t *base, uint32_t off, float v) {
@@ -147,12 +172,14 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bar_w = reinterpret_cast<uint64_t *>(smem);
-  uint64_t *bar_mma = bar_w + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_w + 2);
-  __shared__ double loss_red[kRows];
+  uint64_t *bar_mma = bar_w + 1;     // thread 0's products
+  uint64_t *bar_dw = bar_w + 2;      // [3]: dW4, dW3 and dW1 (each once per tile)
+  uint64_t *bar_drain = bar_w + 5;   // both issuers' products, after a failed wait
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_w + 6);
+  __shared__ double loss_red[4];
   uint8_t *sm = smem + 1024;
   uint8_t *wts = sm + kSmWts, *xT = sm + kSmXT, *h1T = sm + kSmH1T, *h2T = sm + kSmH2T, *h3T = sm + kSmH3T;
-  uint8_t *daT = sm + kSmDaT;
+  uint8_t *daA = sm + kSmDaA, *daB = sm + kSmDaB;
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int hf = warp >> 2;                      // which half of every epilogue's columns
@@ -162,11 +189,13 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   if (lead) {
     tc::mbar_init(bar_w, 1);
     tc::mbar_init(bar_mma, 1);
+    for (int k = 0; k < 3; ++k) tc::mbar_init(bar_dw + k, 1);
+    tc::mbar_init(bar_drain, 2);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
   // unused rows of the gradient operands stay zero
-  for (uint32_t e = tid; e < (kSmDaT + 64 * 128 * 2 - kSmXT) / 16; e += kThreads)
+  for (uint32_t e = tid; e < (kSmTotal - kSmXT) / 16; e += kThreads)
     reinterpret_cast<uint4 *>(xT)[e] = make_uint4(0u, 0u, 0u, 0u);
   tc::fence_proxy_async_smem();
   sync_all();
@@ -177,10 +206,12 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     tc::mbar_arrive_expect_tx(bar_w, kBlob);
     tc::bulk_g2s(wts, a.blob, kBlob, bar_w);
   }
-  bool ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
+  bool ok = true;   // the weights' wait comes after the first tile's input loads are issued
   const uint32_t s_w = tc::smem_addr(wts), s_xT = tc::smem_addr(xT), s_h1T = tc::smem_addr(h1T);
-  const uint32_t s_h2T = tc::smem_addr(h2T), s_h3T = tc::smem_addr(h3T), s_daT = tc::smem_addr(daT);
-  uint32_t phase = 0;
+  const uint32_t s_h2T = tc::smem_addr(h2T), s_h3T = tc::smem_addr(h3T);
+  const uint32_t s_daA = tc::smem_addr(daA), s_daB = tc::smem_addr(daB);
+  uint32_t phase = 0;    // bar_mma's
+  uint32_t dw_par = 0;   // this tile's phase of the bar_dw barriers
   double loss_acc = 0.0;
   const int64_t n_tiles = (a.g.n + kRows - 1) / kRows;
   bool first = true;
@@ -194,19 +225,24 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   };
   // dW^T (M = 128 input rows, N outputs) += act^T (shared) by da (shared),
   // K = 128 queries, both operands MN-major: K = 16 spans two 8-query groups
-  auto mma_dw = [&](uint32_t d_col, uint32_t actT, int N, bool acc) {
+  auto mma_dw = [&](uint32_t d_col, uint32_t actT, uint32_t da, int N, bool acc) {
     const uint32_t kg_a = 128u * 16u, kg_b = (uint32_t)N * 16u;   // bytes per 8-query group
     for (int kk = 0; kk < kRows / 16; ++kk) {
       const uint64_t ad = mn_desc(actT + kk * 2u * kg_a, kg_a);
-      const uint64_t bd = mn_desc(s_daT + kk * 2u * kg_b, kg_b);
+      const uint64_t bd = mn_desc(da + kk * 2u * kg_b, kg_b);
       tc::mma_bf16(tmem + d_col, ad, bd, tc::idesc_bf16(128, N) | kTransA | kTransB, (acc || kk > 0) ? 1u : 0u);
     }
   };
-  // all threads: make the stores visible, then the lead issues `issue` and
-  // everyone waits for the products.  The outcome of each wait travels with
-  // the next round's barrier (or the one after the tile loop), so a round
-  // costs one CTA barrier; false: some thread's previous wait expired.
-  auto round = [&](auto issue) -> bool {
+  // All threads make their stores visible and meet.  Then thread 0 issues
+  // `issue` (the products the epilogue reads) and commits it to bar_mma, and
+  // thread 128 issues `issue_dw` (weight-gradient products, read only after
+  // the tile loop) and commits it to dw_bar where one is given; a dW chain
+  // is waited for only before the shared-memory operands it reads are
+  // overwritten.  Every thread then runs `overlap` (half 1's share of the
+  // next tile's inputs) and waits for bar_mma.  The outcome of each wait
+  // travels with the next round's barrier (or the one after the tile loop),
+  // so a round costs one CTA barrier; false: some thread's wait expired.
+  auto round = [&](auto issue, auto issue_dw, uint64_t *dw_bar, auto overlap) -> bool {
     tc::tmem_st_wait();
     tc::fence_proxy_async_smem();
     tc::tc_fence_before();
@@ -215,12 +251,18 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       tc::tc_fence_after();
       issue();
       tc::mma_commit(bar_mma);
+    } else if (tid == kDwIssuer) {
+      tc::tc_fence_after();
+      issue_dw();
+      if (dw_bar != nullptr) tc::mma_commit(dw_bar);
     }
+    overlap();
     ok = tc::mbar_wait(bar_mma, phase, kWaitCycles);   // spin: one CTA per SM, nothing else to run
     phase ^= 1u;
     tc::tc_fence_after();
     return true;
   };
+  auto none = [] {};
   // 32 activations of this half (columns c0 .. c0 + 31 of a 64-wide layer)
   // into the next A operand (16 columns) and the MN-major copy
   auto put_half = [&](const float *v, uint8_t *mn, int width, int c0) {
@@ -232,36 +274,114 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     for (int q = 0; q < 4; ++q) st_row8(mn, c0 + 8 * q, r, width, w + 4 * q);
   };
 
-  // A tile's global inputs, loaded one tile ahead (during the previous
-  // tile's backward pass): half 0 the latent row, the targets and <wi.n_s>,
-  // half 1 the G-buffer record; both the material id.
-  int in_mat = -1;
-  float in_v[kLatent], in_tg[4], in_wz = 0.0f;
-  auto load_inputs = [&](int64_t t) {
+  // A tile's global inputs are loaded ahead, so that no wait for them falls
+  // on the tile's critical path.  When a tile starts, every thread issues the
+  // load of the next tile's material id, and half 1 those of its G-buffer
+  // record.  Half 1 encodes the record while the forward rounds' products
+  // run (the octaves of u, of v, then the rest), when it has nothing else to
+  // do; half 0 issues the latent row, target and <wi.n_s> loads after the
+  // loss, in flight during the backward pass.
+  int nxt_raw = -1;       // the next tile's raw material id
+  int nxt_mat = -1;       // resolved: -1 for no query or a material out of range
+  float in_v[kLatent];    // half 0: the latent row; half 1: the G-buffer record (9 used)
+  uint32_t in_x[24];      // half 1: inputs 32..79 as BF16 pairs
+  float in_tg[4], in_wz = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kLatent; ++i) in_v[i] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 24; ++k) in_x[k] = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) in_tg[k] = 0.0f;
+  auto load_early = [&](int64_t t) {
     const int64_t q = t * kRows + r;
-    in_mat = t < n_tiles && q < a.g.n ? (int)a.g.material[q] : -1;
-    if (in_mat >= a.n_lat) {
-      if (hf == 0) atomicOr(a.status, kStatusBadMaterial);
-      in_mat = -1;
-    }
-    if (hf == 0) {
+    nxt_raw = -1;
+    if (t < n_tiles && q < a.g.n) {
+      nxt_raw = ld_pinned_u16(a.g.material + q);
+      if (hf == 1) {
+        in_v[0] = ld_pinned(a.g.u + q);
+        in_v[1] = ld_pinned(a.g.v + q);
+        in_v[2] = ld_pinned(a.g.radius + q);
 #pragma unroll
-      for (int i = 0; i < kLatent; ++i) in_v[i] = in_mat >= 0 ? a.latents[(int64_t)in_mat * kLatent + i] : 0.0f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) in_tg[k] = in_mat >= 0 ? a.target[4 * q + k] : 0.0f;
-      in_wz = in_mat >= 0 ? a.g.wi[3 * q + 2] : 0.0f;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) in_v[i] = 0.0f;
-      if (in_mat >= 0) load_record(a.g, q, in_v);
+        for (int i = 0; i < 3; ++i) {
+          in_v[3 + i] = ld_pinned(a.g.wi + 3 * q + i);
+          in_v[6 + i] = ld_pinned(a.g.wo + 3 * q + i);
+        }
+      }
     }
   };
-  load_inputs(blockIdx.x);
+  auto resolve = [&]() {
+    nxt_mat = nxt_raw;
+    if (nxt_mat >= a.n_lat) {
+      if (hf == 0) atomicOr(a.status, kStatusBadMaterial);
+      nxt_mat = -1;
+    }
+  };
+  // half 1, step s of encoding the next tile's record into [q | 1 | 0]:
+  // 1 the octaves of u, 2 those of v, 3 log r, the directions, the constant
+  // one and the padding, and all zeros where there is no query
+  auto encode_step = [&](int s) {
+    if (hf != 1) return;
+    if (s == 1 || s == 2) {
+      float f[16];
+      octaves_accurate(in_v[s - 1], f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) in_x[8 * (s - 1) + k] = tc::pack_bf16(f[2 * k], f[2 * k + 1]);
+    } else if (s == 3) {
+      resolve();
+      static_assert(kDecIn - kLatent - 32 == 7, "inputs 32..79: 32 octave values, log r, 6 directions, one");
+      float x[16];
+      x[0] = (logf(fmaxf(in_v[2], kRFloor)) - kLogRC0) * kLogRInvC1;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) x[1 + i] = in_v[3 + i];
+      x[7] = 1.0f;
+#pragma unroll
+      for (int i = 8; i < 16; ++i) x[i] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) in_x[16 + k] = tc::pack_bf16(x[2 * k], x[2 * k + 1]);
+      if (nxt_mat < 0) {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) in_x[k] = 0u;
+      }
+    }
+  };
+  auto load_late = [&](int64_t t) {   // half 0: latent row, targets, <wi.n_s>
+    const int64_t q = t * kRows + r;
+    const int m = nxt_mat;
+    if (m >= 0) {
+#pragma unroll
+      for (int i = 0; i < kLatent; ++i) in_v[i] = ld_pinned(a.latents + (int64_t)m * kLatent + i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) in_tg[k] = ld_pinned(a.target + 4 * q + k);
+      in_wz = ld_pinned(a.g.wi + 3 * q + 2);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kLatent; ++i) in_v[i] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) in_tg[k] = 0.0f;
+      in_wz = 0.0f;
+    }
+  };
+  load_early(blockIdx.x);
+  resolve();
+  if (hf == 1) {
+    encode_step(1);
+    encode_step(2);
+    encode_step(3);
+  } else {
+    load_late(blockIdx.x);
+  }
+  ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
 
   bool fail = false;   // CTA-uniform: a round found an expired wait
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // the previous tile's dW1 (and with it every earlier dW chain) has read
+    // x^T, h^T and the da buffers before they are rewritten
+    if (!first) {
+      ok = tc::mbar_wait(bar_dw + 2, dw_par ^ 1u, kWaitCycles) && ok;
+      tc::tc_fence_after();
+    }
     const int64_t p = tile * kRows + r;
-    const int mat = in_mat;
+    const int mat = nxt_mat;
     const bool valid = mat >= 0;
     float tg[4] = {in_tg[0], in_tg[1], in_tg[2], in_tg[3]};
     const float wz = in_wz;
@@ -271,29 +391,24 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     if (hf == 0) {
       put_half(in_v, xT, 128, 0);
     } else {
-      float x[48];
+      tc::tmem_st16(t_a + 16, in_x);
 #pragma unroll
-      for (int i = 0; i < 48; ++i) x[i] = 0.0f;
-      if (valid) {
-        query_features_of(in_v, x);
-        x[kDecIn - kLatent] = 1.0f;
-      }
-      put_half(x, xT, 128, 32);
-      uint32_t w[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) w[k] = tc::pack_bf16(x[32 + 2 * k], x[32 + 2 * k + 1]);
-      tc::tmem_st8(t_a + 32, w);
-      st_row8(xT, 64, r, 128, w);
-      st_row8(xT, 72, r, 128, w + 4);
+      for (int q = 0; q < 4; ++q) st_row8(xT, 32 + 8 * q, r, 128, in_x + 4 * q);
+      tc::tmem_st8(t_a + 32, in_x + 16);
+      st_row8(xT, 64, r, 128, in_x + 16);
+      st_row8(xT, 72, r, 128, in_x + 20);
     }
+    load_early(tile + gridDim.x);
     // ---- forward: three hidden layers (ReLU masks of this half's columns
-    // in registers) and the head
+    // in registers) and the head; half 1 encodes the next tile's record
+    // during the products of layers 2, 3 and the head
     uint32_t mask[3];
     const uint32_t wf[3] = {s_w + kW1f, s_w + kW2f, s_w + kW3f};
     uint8_t *const hT[3] = {h1T, h2T, h3T};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      if (!round([&] { mma_ts(kColD, wf[l], l == 0 ? kK1 : kKH, 64); })) { fail = true; break; }
+      if (!round([&] { mma_ts(kColD, wf[l], l == 0 ? kK1 : kKH, 64); }, none, nullptr,
+                 [&] { encode_step(l); })) { fail = true; break; }
       float acc[32];
       tc::tmem_ld32(t_d + 32 * hf, acc);
       tc::tmem_ld_wait();
@@ -313,48 +428,57 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       }
     }
     if (fail) break;
-    if (!round([&] { mma_ts(kColD, s_w + kW4f, kKH, 16); })) { fail = true; break; }
-    // ---- loss and the head's gradient da4 (A operand, K = 16, and da4)
+    if (!round([&] { mma_ts(kColD, s_w + kW4f, kKH, 16); }, none, nullptr, [&] { encode_step(3); })) {
+      fail = true;
+      break;
+    }
+    // ---- loss and the head's gradient da4 (A operand, K = 16, and da4 in buffer A)
     if (hf == 0) {
+      resolve();
       float y[4];
       tc::tmem_ld4(t_d, y);
       tc::tmem_ld_wait();
       float d4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (valid) {
+        float lq = 0.0f;   // the query's four loss terms in FP32, their total in FP64
 #pragma unroll
-        for (int k = 0; k < 4; ++k) d4[k] = loss_grad(k, y[k], tg[k], wz, a.loss_mode, a.inv_batch, &loss_acc);
+        for (int k = 0; k < 4; ++k) d4[k] = loss_grad(k, y[k], tg[k], wz, a.loss_mode, a.inv_batch, &lq);
+        loss_acc += (double)lq;
       }
       uint32_t w[8] = {tc::pack_bf16(d4[0], d4[1]), tc::pack_bf16(d4[2], d4[3]), 0u, 0u, 0u, 0u, 0u, 0u};
       tc::tmem_st8(t_a, w);
-      st_row8(daT, 0, r, 16, w);
-      st_row8(daT, 8, r, 16, w + 4);
+      st_row8(daA, 0, r, 16, w);
+      st_row8(daA, 8, r, 16, w + 4);
+      load_late(tile + gridDim.x);   // in flight during the backward pass
     }
-    load_inputs(tile + gridDim.x);   // the next tile's, in flight during the backward pass
-    // ---- backward: dh_{l} = da_{l+1} W_{l+1}; dW_{l+1}^T += h_l^T da_{l+1}
+    // ---- backward: dh_{l} = da_{l+1} W_{l+1}; dW_{l+1}^T += h_l^T da_{l+1}.
+    // The da of the head, of layer 3, 2 and 1 go to buffers A, B, A, B; an
+    // epilogue that rewrites a buffer first waits for the dW chain that read it.
     const uint32_t wt[3] = {s_w + kW2t, s_w + kW3t, s_w + kW4t};   // transposed W2, W3, W4
     const uint32_t hTa[3] = {s_h1T, s_h2T, s_h3T};
     const uint32_t cdw[3] = {kColW2, kColW3, kColW4};
+    const uint32_t da_in[3] = {s_daA, s_daB, s_daA};    // by l: the da this round's dW chain reads
+    uint8_t *const da_out[3] = {daB, daA, daB};         // by l: where its epilogue writes
+    uint64_t *const dw_commit[3] = {nullptr, bar_dw + 1, bar_dw + 0};
+    uint64_t *const dw_before[3] = {bar_dw + 1, bar_dw + 0, nullptr};
 #pragma unroll
     for (int l = 2; l >= 0; --l) {
       // layer l+2 (1-based) produced h_{l+1}: dh_{l+1} = da W_{l+2}, dW_{l+2}^T += h_{l+1}^T da
       const int Kin = l == 2 ? 16 : 64, Nw = l == 2 ? 16 : 64;
-      if (!round([&] {
-            mma_ts(kColD, wt[l], Kin, 64);
-            mma_dw(cdw[l], hTa[l], Nw, !first);
-          })) { fail = true; break; }
+      if (!round([&] { mma_ts(kColD, wt[l], Kin, 64); }, [&] { mma_dw(cdw[l], hTa[l], da_in[l], Nw, !first); },
+                 dw_commit[l], none)) { fail = true; break; }
       float acc[32];
       tc::tmem_ld32(t_d + 32 * hf, acc);
       tc::tmem_ld_wait();
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = (mask[l] >> j) & 1u ? acc[j] : 0.0f;
-      put_half(acc, daT, 64, 32 * hf);
+      if (dw_before[l] != nullptr) ok = tc::mbar_wait(dw_before[l], dw_par, kWaitCycles) && ok;
+      put_half(acc, da_out[l], 64, 32 * hf);
     }
     if (fail) break;
     // ---- dz rows = da1 W1[:, :32] (16 columns per half); dW1^T += x^T da1
-    if (!round([&] {
-          mma_ts(kColD, s_w + kW1t, 64, 32);
-          mma_dw(kColW1, s_xT, 64, !first);
-        })) { fail = true; break; }
+    if (!round([&] { mma_ts(kColD, s_w + kW1t, 64, 32); }, [&] { mma_dw(kColW1, s_xT, s_daB, 64, !first); },
+               bar_dw + 2, none)) { fail = true; break; }
     {
       float dz[16];
       tc::tmem_ld16(t_d + 16 * hf, dz);
@@ -366,28 +490,44 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       }
     }
     first = false;
+    dw_par ^= 1u;
+  }
+  // every dW chain has finished before the accumulators are read
+  if (!first && !fail) {
+    ok = tc::mbar_wait(bar_dw + 2, dw_par ^ 1u, kWaitCycles) && ok;
+    tc::tc_fence_after();
   }
   ok = __syncthreads_and(ok && !fail);   // one outcome for the CTA before the barriers below
   // ---- this CTA's gradient partials: lane j holds row j of every dW^T;
-  // the two halves take alternate 16-column chunks
+  // the two halves take alternate 16-column chunks, all loaded before one wait
   float *out = a.partial + (int64_t)blockIdx.x * a.partial_width;
   if (ok) {
     const int j = r;
     const uint32_t t_row = tmem + lane;
+    float v[4][32];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int N = l == 3 ? 16 : 64;
+      const uint32_t col = l == 0 ? kColW1 : l == 1 ? kColW2 : l == 2 ? kColW3 : kColW4;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (16 * hf + 32 * h < N) tc::tmem_ld16(t_row + col + 16 * hf + 32 * h, v[l] + 16 * h);
+    }
+    tc::tmem_ld_wait();
+#pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int N = l == 3 ? 16 : 64, in = l == 0 ? kDecIn : kHidden, nout = l == 3 ? kOut : kHidden;
       const int offW = l == 0 ? kOffW1 : l == 1 ? kOffW2 : l == 2 ? kOffW3 : kOffW4;
       const int offB = l == 0 ? kOffB1 : l == 1 ? kOffB2 : l == 2 ? kOffB3 : kOffB4;
-      const uint32_t col = l == 0 ? kColW1 : l == 1 ? kColW2 : l == 2 ? kColW3 : kColW4;
-      for (int c = 16 * hf; c < N; c += 32) {
-        float v[16];
-        tc::tmem_ld16(t_row + col + c, v);
-        tc::tmem_ld_wait();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 16 * hf + 32 * h;
+        if (c >= N) continue;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int o = c + e;
           if (o >= nout) continue;
-          const float g = first ? 0.0f : v[e];   // a CTA without tiles contributes zeros
+          const float g = first ? 0.0f : v[l][16 * h + e];   // a CTA without tiles contributes zeros
           if (j < in) out[offW + o * in + j] = g;
           else if (j == in) out[offB + o] = g;
         }
@@ -411,17 +551,34 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       int nt = 0;   // tiles in this group
       while (nt < group && t0 + (int64_t)nt * gridDim.x < n_tiles) ++nt;
       __syncthreads();
-      for (int e = tid; e < nt * kRows * (kLatent / 4); e += kThreads) {
-        const int t = e / (kRows * (kLatent / 4)), rest = e % (kRows * (kLatent / 4));
-        const int64_t row = (t0 + (int64_t)t * gridDim.x) * kRows + rest / (kLatent / 4);
-        reinterpret_cast<float4 *>(stage)[e] =
-            row < a.g.n ? reinterpret_cast<const float4 *>(a.dlat_rows)[row * (kLatent / 4) + rest % (kLatent / 4)]
-                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      // eight loads in flight per thread before their stores
+      const int n4 = nt * kRows * (kLatent / 4);
+      for (int e0 = tid; e0 < n4; e0 += 8 * kThreads) {
+        float4 v4[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kThreads;
+          const int t = e / (kRows * (kLatent / 4)), rest = e % (kRows * (kLatent / 4));
+          const int64_t row = (t0 + (int64_t)t * gridDim.x) * kRows + rest / (kLatent / 4);
+          v4[u] = e < n4 && row < a.g.n
+                      ? reinterpret_cast<const float4 *>(a.dlat_rows)[row * (kLatent / 4) + rest % (kLatent / 4)]
+                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u * kThreads < n4) reinterpret_cast<float4 *>(stage)[e0 + u * kThreads] = v4[u];
       }
-      for (int e = tid; e < nt * kRows; e += kThreads) {
-        const int64_t row = (t0 + (int64_t)(e / kRows) * gridDim.x) * kRows + e % kRows;
-        const int m = row < a.g.n ? (int)a.g.material[row] : -1;
-        ids[e] = m < a.n_lat ? m : -1;
+      for (int e0 = tid; e0 < nt * kRows; e0 += 4 * kThreads) {
+        int m4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * kThreads;
+          const int64_t row = (t0 + (int64_t)(e / kRows) * gridDim.x) * kRows + e % kRows;
+          m4[u] = e < nt * kRows && row < a.g.n ? (int)a.g.material[row] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (e0 + u * kThreads < nt * kRows) ids[e0 + u * kThreads] = m4[u] < a.n_lat ? m4[u] : -1;
       }
       __syncthreads();
       for (int t = 0; t < nt; ++t) {
@@ -442,17 +599,22 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     __syncthreads();
     for (int e = tid; e < a.n_lat * kLatent; e += kThreads) out[kDecParams + e] = first ? 0.0f : acc[e];
   }
-  if (hf == 0) loss_red[r] = loss_acc;
+  // the loss: a fixed shuffle tree in each of half 0's warps, then their four sums in order
+  if (hf == 0) {
+    double l = loss_acc;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, d);
+    if ((tid & 31) == 0) loss_red[warp] = l;
+  }
   __syncthreads();
   if (tid == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kRows; ++k) s += loss_red[k];
-    a.loss_partial[blockIdx.x] = s;
+    a.loss_partial[blockIdx.x] = (loss_red[0] + loss_red[1]) + (loss_red[2] + loss_red[3]);
     if (!ok) atomicOr(a.status, kStatusTimeout);
   }
-  if (!ok) {
+  if (!ok) {   // after an expired wait: let the weights' copy and both issuers' products finish
     tc::mbar_wait(bar_w, 0, kWaitCycles);
-    tc::mbar_wait(bar_mma, phase ^ 1u, kWaitCycles);
+    if (lead || tid == kDwIssuer) tc::mma_commit(bar_drain);
+    tc::mbar_wait(bar_drain, 0, kWaitCycles);
   }
   tc::tc_fence_before();
   __syncthreads();
