@@ -436,54 +436,58 @@ __device__ __forceinline__ void material_features(const fabric_material &m, floa
 // inputs in order, as for a single material).
 constexpr int kEncGroup = 4;
 
-// dot of weight row w (LEN floats, 16-byte aligned when V) with the group's
-// vectors x[g][0..LEN), one accumulator per material, inputs in order.  The
-// whole row is loaded into registers first, so that its loads are in flight
-// together rather than one dependent round trip per few elements.
-template <bool V, int LEN, int LD>
-__device__ __forceinline__ void enc_dot(const float *__restrict__ w, const float (*x)[LD], float *acc) {
-  float c[LEN];
+// The encoder kernels stage the weights they read in shared memory with
+// asynchronous copies issued at once, so that all of them are one round trip
+// rather than one dependent round trip per few elements.  Rows read by one
+// thread each (thread j: row j) are padded so that a warp's reads fall into
+// distinct banks: E1 rows of kEncIn floats at a stride of kE1Ld (odd),
+// E2 and E3 rows of 128 floats at a stride of 132 (read as float4: eight
+// lanes of a quarter-warp cover the 32 banks).
+constexpr int kE1Ld = kEncIn | 1;
+constexpr int kERowLd = kEncHidden + 4;
+constexpr size_t kEncFwdSmem = (size_t)(kEncHidden * kE1Ld + kEncHidden * kERowLd + kLatent * kERowLd) * 4;
+constexpr size_t kEncBwdSmem = (size_t)(kEncHidden * kEncHidden + kLatent * kEncHidden) * 4;
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// rows x cols floats at src (row stride cols) into dst (row stride ld), by
+// all threads of the CTA; 16-byte copies when V (src, cols and ld multiples
+// of four floats, src 16-byte aligned), else 4-byte ones
+template <bool V>
+__device__ __forceinline__ void stage_rows(float *dst, int ld, const float *src, int rows, int cols) {
   if (V) {
-    const float4 *w4 = reinterpret_cast<const float4 *>(w);
-#pragma unroll
-    for (int i4 = 0; i4 < LEN / 4; ++i4) {
-      const float4 t = w4[i4];
-      c[4 * i4] = t.x;
-      c[4 * i4 + 1] = t.y;
-      c[4 * i4 + 2] = t.z;
-      c[4 * i4 + 3] = t.w;
-    }
+    const int c4 = cols / 4;
+    for (int e = threadIdx.x; e < rows * c4; e += blockDim.x)
+      cp_async16(dst + (e / c4) * ld + 4 * (e % c4), src + (e / c4) * cols + 4 * (e % c4));
   } else {
-#pragma unroll
-    for (int i = 0; i < LEN; ++i) c[i] = w[i];
-  }
-#pragma unroll
-  for (int i = 0; i < LEN; ++i) {
-#pragma unroll
-    for (int g = 0; g < kEncGroup; ++g) acc[g] = fmaf(c[i], x[g][i], acc[g]);
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x)
+      cp_async4(dst + (e / cols) * ld + e % cols, src + e);
   }
 }
 
-// Same for one vector x[0..kEncHidden).
-template <bool V>
-__device__ __forceinline__ void enc_dot1(const float *__restrict__ w, const float *x, float *acc) {
-  float c[kEncHidden];
-  if (V) {
-    const float4 *w4 = reinterpret_cast<const float4 *>(w);
+// dot of a shared-memory weight row w (LEN floats; 16-byte aligned) with the
+// group's vectors x[g][0..LEN), one accumulator per material, inputs in order
+template <int LEN, int LD>
+__device__ __forceinline__ void enc_dot_s(const float *w, const float (*x)[LD], float *acc) {
+#pragma unroll 8
+  for (int i4 = 0; i4 < LEN / 4; ++i4) {
+    const float4 c = reinterpret_cast<const float4 *>(w)[i4];
 #pragma unroll
-    for (int i4 = 0; i4 < kEncHidden / 4; ++i4) {
-      const float4 t = w4[i4];
-      c[4 * i4] = t.x;
-      c[4 * i4 + 1] = t.y;
-      c[4 * i4 + 2] = t.z;
-      c[4 * i4 + 3] = t.w;
+    for (int g = 0; g < kEncGroup; ++g) {
+      acc[g] = fmaf(c.x, x[g][4 * i4], acc[g]);
+      acc[g] = fmaf(c.y, x[g][4 * i4 + 1], acc[g]);
+      acc[g] = fmaf(c.z, x[g][4 * i4 + 2], acc[g]);
+      acc[g] = fmaf(c.w, x[g][4 * i4 + 3], acc[g]);
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kEncHidden; ++i) c[i] = w[i];
   }
-#pragma unroll
-  for (int i = 0; i < kEncHidden; ++i) acc[0] = fmaf(c[i], x[i], acc[0]);
 }
 
 template <bool V>
@@ -494,6 +498,14 @@ __global__ void __launch_bounds__(kEncHidden) encoder_fwd_kernel(const float *__
                                                                  float *__restrict__ z, float *__restrict__ acts) {
   grid_dependency_wait();
   grid_dependents_launch();
+  extern __shared__ __align__(16) float enc_smem[];
+  float *e1 = enc_smem;                             // [128][kE1Ld]
+  float *e2 = e1 + kEncHidden * kE1Ld;              // [128][kERowLd]
+  float *e3 = e2 + kEncHidden * kERowLd;            // [32][kERowLd]
+  static_assert((kEncHidden * kE1Ld) % 4 == 0, "E2 rows 16-byte aligned in shared memory");
+  stage_rows<false>(e1, kE1Ld, enc + kOffE1, kEncHidden, kEncIn);
+  stage_rows<V>(e2, kERowLd, enc + kOffE2, kEncHidden, kEncHidden);
+  stage_rows<V>(e3, kERowLd, enc + kOffE3, kLatent, kEncHidden);
   __shared__ float f[kEncGroup][kEncIn];
   __shared__ __align__(16) float h1[kEncGroup][kEncHidden];
   __shared__ __align__(16) float h2[kEncGroup][kEncHidden];
@@ -520,19 +532,24 @@ __global__ void __launch_bounds__(kEncHidden) encoder_fwd_kernel(const float *__
       f[g][i] = g < nm ? feats[(int64_t)(m0 + g) * kEncIn + i] : 0.0f;
     }
   }
+  const float b1 = enc[kOffEb1 + j], b2 = enc[kOffEb2 + j], b3 = enc[kOffEb3 + j % kLatent];
+  cp_async_wait_all();
   __syncthreads();
   float a1[kEncGroup], a2[kEncGroup];
-  const float b1 = enc[kOffEb1 + j];
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) a1[g] = b1;
-  enc_dot<false, kEncIn, kEncIn>(enc + kOffE1 + j * kEncIn, f, a1);   // rows of 22 floats: 8-byte aligned at best
+#pragma unroll
+  for (int i = 0; i < kEncIn; ++i) {
+    const float c = e1[j * kE1Ld + i];
+#pragma unroll
+    for (int g = 0; g < kEncGroup; ++g) a1[g] = fmaf(c, f[g][i], a1[g]);
+  }
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) h1[g][j] = lrelu(a1[g]);
   __syncthreads();
-  const float b2 = enc[kOffEb2 + j];
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) a2[g] = b2 + h1[g][j];   // skip connection before the last activation
-  enc_dot<V, kEncHidden, kEncHidden>(enc + kOffE2 + j * kEncHidden, h1, a2);
+  enc_dot_s<kEncHidden, kEncHidden>(e2 + j * kERowLd, h1, a2);
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) {
     h2[g][j] = lrelu(a2[g]);
@@ -545,29 +562,39 @@ __global__ void __launch_bounds__(kEncHidden) encoder_fwd_kernel(const float *__
   // layer 3: thread j computes latent output k = j % 32 of material j / 32
   static_assert(kEncGroup * kLatent == kEncHidden, "one layer-3 output per thread");
   const int k = j % kLatent, g = j / kLatent;
-  float acc[1] = {enc[kOffEb3 + k]};
-  enc_dot1<V>(enc + kOffE3 + k * kEncHidden, h2[g], acc);
-  if (g < nm) z[(int64_t)(m0 + g) * kLatent + k] = acc[0];
+  float acc = b3;
+  const float *w3 = e3 + k * kERowLd;
+#pragma unroll 8
+  for (int i4 = 0; i4 < kEncHidden / 4; ++i4) {
+    const float4 c = reinterpret_cast<const float4 *>(w3)[i4];
+    acc = fmaf(c.x, h2[g][4 * i4], acc);
+    acc = fmaf(c.y, h2[g][4 * i4 + 1], acc);
+    acc = fmaf(c.z, h2[g][4 * i4 + 2], acc);
+    acc = fmaf(c.w, h2[g][4 * i4 + 3], acc);
+  }
+  if (g < nm) z[(int64_t)(m0 + g) * kLatent + k] = acc;
 }
 
 // Per material: back-propagated pre-activation gradients da1, da2 and the
 // activations h1, h2 into work [n][4][128]; kEncGroup materials per CTA.
+template <bool V>
 __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float *__restrict__ enc, int n,
                                                                      const float *__restrict__ acts,
                                                                      const float *__restrict__ dz,
                                                                      float *__restrict__ work) {
   grid_dependency_wait();
   grid_dependents_launch();
+  // E2 and E3 staged as they are (thread j reads their column j: a warp's
+  // reads are consecutive words)
+  extern __shared__ __align__(16) float enc_smem[];
+  float *e2 = enc_smem;                          // [128][128]
+  float *e3 = e2 + kEncHidden * kEncHidden;      // [32][128]
+  stage_rows<V>(e2, kEncHidden, enc + kOffE2, kEncHidden, kEncHidden);
+  stage_rows<V>(e3, kEncHidden, enc + kOffE3, kLatent, kEncHidden);
   __shared__ float sdz[kEncGroup][kLatent], da2s[kEncGroup][kEncHidden];
   const int m0 = blockIdx.x * kEncGroup, j = threadIdx.x;
   const int nm = min(kEncGroup, n - m0);
-  // every global load of the kernel first, so that they are in flight
-  // together: columns j of E3 and E2, the activations and dz
-  float w3[kLatent], w2[kEncHidden], a1[kEncGroup], a2[kEncGroup];
-#pragma unroll
-  for (int k = 0; k < kLatent; ++k) w3[k] = enc[kOffE3 + k * kEncHidden + j];
-#pragma unroll
-  for (int o = 0; o < kEncHidden; ++o) w2[o] = enc[kOffE2 + o * kEncHidden + j];
+  float a1[kEncGroup], a2[kEncGroup];
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) {
     const int64_t m = g < nm ? m0 + g : m0;
@@ -578,14 +605,16 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
     const int k = j % kLatent, g = j / kLatent;
     sdz[g][k] = g < nm ? dz[(int64_t)(m0 + g) * kLatent + k] : 0.0f;
   }
+  cp_async_wait_all();
   __syncthreads();
   float dh2[kEncGroup], dh1[kEncGroup];
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) dh2[g] = 0.0f;
-#pragma unroll
+#pragma unroll 8
   for (int k = 0; k < kLatent; ++k) {
+    const float w3 = e3[k * kEncHidden + j];
 #pragma unroll
-    for (int g = 0; g < kEncGroup; ++g) dh2[g] = fmaf(w3[k], sdz[g][k], dh2[g]);
+    for (int g = 0; g < kEncGroup; ++g) dh2[g] = fmaf(w3, sdz[g][k], dh2[g]);
   }
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) {
@@ -594,10 +623,11 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
     dh1[g] = da2;   // through the skip
   }
   __syncthreads();
-#pragma unroll
+#pragma unroll 8
   for (int o = 0; o < kEncHidden; ++o) {
+    const float w2 = e2[o * kEncHidden + j];
 #pragma unroll
-    for (int g = 0; g < kEncGroup; ++g) dh1[g] = fmaf(w2[o], da2s[g][o], dh1[g]);
+    for (int g = 0; g < kEncGroup; ++g) dh1[g] = fmaf(w2, da2s[g][o], dh1[g]);
   }
 #pragma unroll
   for (int g = 0; g < kEncGroup; ++g) {
@@ -612,10 +642,11 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
 
 // Encoder parameter gradients: every block is a sum over materials of outer
 // products, out[r][c] = sum_m L[m][r] R[m][c] (R = 1 for the biases).  A CTA
-// takes a 32 x 32 block of one of them: it stages 64 materials' rows of L
+// takes a 32 x 32 block of one of them with two groups of 256 threads: group
+// q sums over the q-th half of the materials, staging 64 materials' rows of L
 // and R at a time in shared memory (all of a chunk's loads in flight
-// together), and thread (w, c) accumulates rows 4w..4w+3 of column c over the
-// materials in order.
+// together), thread (w, c) accumulating rows 4w..4w+3 of column c over its
+// materials in order; the block is then (first half) + (second half).
 constexpr int kGradChunk = 64;
 
 struct GradBlock {
@@ -646,14 +677,16 @@ constexpr int kGradTiles = grad_tiles(kEncHidden, kEncIn) + grad_tiles(kEncHidde
                            grad_tiles(kEncHidden, kEncHidden) + grad_tiles(kEncHidden, 1) +
                            grad_tiles(kLatent, kEncHidden) + grad_tiles(kLatent, 1);
 
-__global__ void __launch_bounds__(256) encoder_grad_kernel(const float *__restrict__ feats, int n,
-                                                           const float *__restrict__ dz,
-                                                           const float *__restrict__ work,
-                                                           float *__restrict__ denc) {
+constexpr int kGradThreads = 512;
+
+__global__ void __launch_bounds__(kGradThreads) encoder_grad_kernel(const float *__restrict__ feats, int n,
+                                                                    const float *__restrict__ dz,
+                                                                    const float *__restrict__ work,
+                                                                    float *__restrict__ denc) {
   grid_dependency_wait();
   grid_dependents_launch();
-  __shared__ __align__(16) float sl[kGradChunk][32];
-  __shared__ float sr[kGradChunk][32];
+  __shared__ __align__(16) float sl[2][kGradChunk][32];
+  __shared__ float sr[2][kGradChunk][32];
   // which block, and which 32 x 32 tile of it
   int t = blockIdx.x, b = 0;
   while (t >= grad_tiles(kGradBlocks[b].rows, kGradBlocks[b].cols)) {
@@ -666,35 +699,46 @@ __global__ void __launch_bounds__(256) encoder_grad_kernel(const float *__restri
   int ldl, ldr;
   const float *L = grad_src(B.l_src, work, feats, dz, ldl);
   const float *R = grad_src(B.r_src, work, feats, dz, ldr);
-  const int tid = threadIdx.x, c = tid & 31, w = tid >> 5;
+  const int q = threadIdx.x >> 8, tid = threadIdx.x & 255, c = tid & 31, w = tid >> 5;
+  const int half = (n + 1) / 2, m_begin = q == 0 ? 0 : half, m_end = q == 0 ? half : n;
+  const int rounds = (half + kGradChunk - 1) / kGradChunk;   // the same for both groups (CTA barriers)
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  for (int m0 = 0; m0 < n; m0 += kGradChunk) {
-    const int mc = min(kGradChunk, n - m0);
+  for (int k0 = 0; k0 < rounds; ++k0) {
+    const int m0 = m_begin + k0 * kGradChunk;
+    const int mc = max(0, min(kGradChunk, m_end - m0));
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kGradChunk * 32 / 256; ++q) {
-      const int e = tid + 256 * q, mm = e >> 5, k = e & 31;
+    for (int u = 0; u < kGradChunk * 32 / 256; ++u) {
+      const int e = tid + 256 * u, mm = e >> 5, k = e & 31;
       const bool in = mm < mc;
-      sl[mm][k] = in && r0 + k < B.rows ? L[(int64_t)(m0 + mm) * ldl + B.l_off + r0 + k] : 0.0f;
-      sr[mm][k] = !in ? 0.0f
-                      : B.r_off < 0 ? 1.0f
-                                    : (c0 + k < B.cols ? R[(int64_t)(m0 + mm) * ldr + B.r_off + c0 + k] : 0.0f);
+      sl[q][mm][k] = in && r0 + k < B.rows ? L[(int64_t)(m0 + mm) * ldl + B.l_off + r0 + k] : 0.0f;
+      sr[q][mm][k] = !in ? 0.0f
+                         : B.r_off < 0 ? 1.0f
+                                       : (c0 + k < B.cols ? R[(int64_t)(m0 + mm) * ldr + B.r_off + c0 + k] : 0.0f);
     }
     __syncthreads();
     for (int mm = 0; mm < mc; ++mm) {
-      const float4 a = reinterpret_cast<const float4 *>(sl[mm])[w];
-      const float x = sr[mm][c];
+      const float4 a = reinterpret_cast<const float4 *>(sl[q][mm])[w];
+      const float x = sr[q][mm][c];
       acc[0] = fmaf(a.x, x, acc[0]);
       acc[1] = fmaf(a.y, x, acc[1]);
       acc[2] = fmaf(a.z, x, acc[2]);
       acc[3] = fmaf(a.w, x, acc[3]);
     }
   }
-  if (c0 + c < B.cols) {
+  // the second half's sums through shared memory, added to the first half's
+  __syncthreads();
+  float(*part)[32] = sl[1];   // [32 rows][32 columns]: rows 4w..4w+3 of column c
+  if (q == 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[4 * w + k][c] = acc[k];
+  }
+  __syncthreads();
+  if (q == 0 && c0 + c < B.cols) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int r = r0 + 4 * w + k;
-      if (r < B.rows) denc[B.out + r * B.cols + c0 + c] = acc[k];
+      if (r < B.rows) denc[B.out + r * B.cols + c0 + c] = acc[k] + part[4 * w + k][c];
     }
   }
 }
@@ -1223,26 +1267,32 @@ cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const
 }
 
 namespace {
-void encoder_fwd(const float *feats, const fabric_material *raw, float *feats_out, int n, const float *enc, float *z,
-                 float *acts, cudaStream_t s) {
+cudaError_t encoder_fwd(const float *feats, const fabric_material *raw, float *feats_out, int n, const float *enc,
+                        float *z, float *acts, cudaStream_t s) {
   const int grid = (n + kEncGroup - 1) / kEncGroup;
-  if ((reinterpret_cast<uintptr_t>(enc) & 15) == 0)
-    launch_dependent(encoder_fwd_kernel<true>, grid, kEncHidden, 0, s, feats, raw, feats_out, n, enc, z, acts);
+  const bool v = (reinterpret_cast<uintptr_t>(enc) & 15) == 0;
+  const void *k = v ? reinterpret_cast<const void *>(encoder_fwd_kernel<true>)
+                    : reinterpret_cast<const void *>(encoder_fwd_kernel<false>);
+  const cudaError_t e = ensure_max_dyn_smem(k, (int)kEncFwdSmem);
+  if (e != cudaSuccess) return e;
+  if (v)
+    launch_dependent(encoder_fwd_kernel<true>, grid, kEncHidden, kEncFwdSmem, s, feats, raw, feats_out, n, enc, z,
+                     acts);
   else
-    launch_dependent(encoder_fwd_kernel<false>, grid, kEncHidden, 0, s, feats, raw, feats_out, n, enc, z, acts);
+    launch_dependent(encoder_fwd_kernel<false>, grid, kEncHidden, kEncFwdSmem, s, feats, raw, feats_out, n, enc, z,
+                     acts);
+  return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_encoder_feats(const float *feats, int n, const float *enc, float *z, float *acts,
                                  cudaStream_t s) {
-  encoder_fwd(feats, nullptr, nullptr, n, enc, z, acts, s);
-  return cudaGetLastError();
+  return encoder_fwd(feats, nullptr, nullptr, n, enc, z, acts, s);
 }
 
 cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *feats_out, float *z,
                                float *acts, cudaStream_t s) {
-  encoder_fwd(nullptr, raw, feats_out, n, enc, z, acts, s);
-  return cudaGetLastError();
+  return encoder_fwd(nullptr, raw, feats_out, n, enc, z, acts, s);
 }
 
 size_t encoder_backward_work_floats(int n) { return (size_t)n * 2 * kEncHidden + (size_t)n * 4 * kEncHidden; }
@@ -1254,11 +1304,23 @@ cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc,
   float *vec = work + (size_t)n * 2 * kEncHidden;
   if (!acts_in) {
     // recompute the forward pass to obtain the pre-activations (z discarded into vec)
-    encoder_fwd(feats, nullptr, nullptr, n, enc, vec, acts, s);
+    const cudaError_t e = encoder_fwd(feats, nullptr, nullptr, n, enc, vec, acts, s);
+    if (e != cudaSuccess) return e;
     acts_in = acts;
   }
-  launch_dependent(encoder_bwd_vec_kernel, (n + kEncGroup - 1) / kEncGroup, kEncHidden, 0, s, enc, n, acts_in, dz, vec);
-  launch_dependent(encoder_grad_kernel, kGradTiles, 256, 0, s, feats, n, dz, vec, denc);
+  const bool v = (reinterpret_cast<uintptr_t>(enc) & 15) == 0;
+  const void *k = v ? reinterpret_cast<const void *>(encoder_bwd_vec_kernel<true>)
+                    : reinterpret_cast<const void *>(encoder_bwd_vec_kernel<false>);
+  {
+    const cudaError_t e = ensure_max_dyn_smem(k, (int)kEncBwdSmem);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = (n + kEncGroup - 1) / kEncGroup;
+  if (v)
+    launch_dependent(encoder_bwd_vec_kernel<true>, grid, kEncHidden, kEncBwdSmem, s, enc, n, acts_in, dz, vec);
+  else
+    launch_dependent(encoder_bwd_vec_kernel<false>, grid, kEncHidden, kEncBwdSmem, s, enc, n, acts_in, dz, vec);
+  launch_dependent(encoder_grad_kernel, kGradTiles, kGradThreads, 0, s, feats, n, dz, vec, denc);
   return cudaGetLastError();
 }
 
