@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kBwdThreads) decoder_bwd_kernel(const BwdArgs 
 // then the range sums are added in range order: a fixed order, so the
 // result does not change from run to run.
 constexpr int kSumSegs = 8;
+constexpr int kSumBatch = 24;   // one batch for up to 192 partials
 
 __device__ void reduce_loss_warp(const double *__restrict__ part, int n, double *__restrict__ out);
 
@@ -314,15 +315,15 @@ __global__ void __launch_bounds__(32 * kSumSegs) reduce_partials_kernel(const fl
   const int c0 = min(n_part, seg * per), c1 = min(n_part, c0 + per);
   float s = 0.0f;
   if (j < width) {
-    int c = c0;
-    for (; c + 4 <= c1; c += 4) {
-      float t[4];
+    // kSumBatch loads in flight, then their sum in order
+    for (int c = c0; c < c1; c += kSumBatch) {
+      float t[kSumBatch];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) t[q] = partial[(int64_t)(c + q) * stride + j];
+      for (int q = 0; q < kSumBatch; ++q) t[q] = c + q < c1 ? partial[(int64_t)(c + q) * stride + j] : 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s += t[q];
+      for (int q = 0; q < kSumBatch; ++q)
+        if (c + q < c1) s += t[q];
     }
-    for (; c < c1; ++c) s += partial[(int64_t)c * stride + j];
   }
   seg_sum[seg][lane] = s;
   __syncthreads();

@@ -167,7 +167,9 @@ __device__ __forceinline__ void sync_all() {
 }
 
 __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs a) {
-  grid_dependency_wait();
+  // The set-up and the first tile's G-buffer reads (inputs of the step, which
+  // the step's first kernel waited for) overlap the kernels before this one;
+  // the wait for them comes before the weights and latents they write.
   grid_dependents_launch();
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -202,11 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   const uint32_t tmem = *tmem_slot;
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;   // this warp's lane quadrant
   const uint32_t t_d = tmem + lane + kColD, t_a = tmem + lane + kColA;
-  if (lead) {
-    tc::mbar_arrive_expect_tx(bar_w, kBlob);
-    tc::bulk_g2s(wts, a.blob, kBlob, bar_w);
-  }
-  bool ok = true;   // the weights' wait comes after the first tile's input loads are issued
+  bool ok = true;
   const uint32_t s_w = tc::smem_addr(wts), s_xT = tc::smem_addr(xT), s_h1T = tc::smem_addr(h1T);
   const uint32_t s_h2T = tc::smem_addr(h2T), s_h3T = tc::smem_addr(h3T);
   const uint32_t s_daA = tc::smem_addr(daA), s_daB = tc::smem_addr(daB);
@@ -367,9 +365,13 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     encode_step(1);
     encode_step(2);
     encode_step(3);
-  } else {
-    load_late(blockIdx.x);
   }
+  grid_dependency_wait();
+  if (lead) {
+    tc::mbar_arrive_expect_tx(bar_w, kBlob);
+    tc::bulk_g2s(wts, a.blob, kBlob, bar_w);
+  }
+  if (hf == 0) load_late(blockIdx.x);
   ok = tc::mbar_wait_sleep(bar_w, 0, kWaitCycles);
 
   bool fail = false;   // CTA-uniform: a round found an expired wait
