@@ -67,6 +67,11 @@ constexpr uint32_t kSmTotal = kSmDaB + 64 * 128 * 2;
 constexpr size_t kDynSmem = 1024 /* align */ + 1024 /* header */ + kSmTotal;
 
 constexpr uint32_t kColD = 0, kColA = 64, kColW1 = 128, kColW2 = 192, kColW3 = 256, kColW4 = 320;
+// The latent-gradient rows of up to kDzTiles tiles stay in tensor memory,
+// 32 columns per tile from kColDz, for the per-material sums at the end.
+constexpr uint32_t kColDz = 336;
+constexpr int kDzTiles = 5;
+static_assert(kColDz + 32 * kDzTiles <= 512, "latent-gradient rows inside the allocation");
 
 // Thread 0 issues the products the epilogues read; thread 128 (the first
 // thread of half 1) issues the weight-gradient products.
@@ -213,6 +218,14 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   double loss_acc = 0.0;
   const int64_t n_tiles = (a.g.n + kRows - 1) / kRows;
   bool first = true;
+  // With the per-material latent sums folded into the partials, a CTA of at
+  // most kDzTiles tiles (all staged at once at the end) keeps its rows in
+  // tensor memory; otherwise they go to a.dlat_rows.
+  const int my_tiles = n_tiles > blockIdx.x ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  const int sum_group = (int)max((int64_t)0, ((int64_t)kSmTotal - (int64_t)a.n_lat * kLatent * 4) /
+                                                 (int64_t)(kRows * (kLatent * 4 + 4)));   // tiles staged at once
+  const bool dz_tmem = a.partial_width > kDecParams && my_tiles <= kDzTiles && my_tiles <= sum_group;
+  int ti = 0;   // tiles done
 
   // one MMA chain (K/16 steps) of A in tensor memory by B in shared memory
   auto mma_ts = [&](uint32_t d_col, uint32_t b_addr, int K, int N) {
@@ -479,9 +492,10 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     }
     if (fail) break;
     // ---- dz rows = da1 W1[:, :32] (16 columns per half); dW1^T += x^T da1
-    if (!round([&] { mma_ts(kColD, s_w + kW1t, 64, 32); }, [&] { mma_dw(kColW1, s_xT, s_daB, 64, !first); },
+    const uint32_t dz_col = dz_tmem ? kColDz + 32u * (uint32_t)ti : kColD;
+    if (!round([&] { mma_ts(dz_col, s_w + kW1t, 64, 32); }, [&] { mma_dw(kColW1, s_xT, s_daB, 64, !first); },
                bar_dw + 2, none)) { fail = true; break; }
-    {
+    if (!dz_tmem) {
       float dz[16];
       tc::tmem_ld16(t_d + 16 * hf, dz);
       tc::tmem_ld_wait();
@@ -493,6 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     }
     first = false;
     dw_par ^= 1u;
+    ++ti;
   }
   // every dW chain has finished before the accumulators are read
   if (!first && !fail) {
@@ -544,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   if (ok && a.partial_width > kDecParams) {
     float *acc = reinterpret_cast<float *>(sm);                   // [n_lat][32]
     float *stage = acc + (size_t)a.n_lat * kLatent;                // [group][128][32]
-    const int group = (int)((kSmTotal - (size_t)a.n_lat * kLatent * 4) / (kRows * (kLatent * 4 + 4)));
+    const int group = sum_group;
     int *ids = reinterpret_cast<int *>(stage + (size_t)group * kRows * kLatent);   // [group][128]
     const int lane32 = tid & 31;
     __syncthreads();
@@ -553,8 +568,24 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       int nt = 0;   // tiles in this group
       while (nt < group && t0 + (int64_t)nt * gridDim.x < n_tiles) ++nt;
       __syncthreads();
-      // eight loads in flight per thread before their stores
-      const int n4 = nt * kRows * (kLatent / 4);
+      // the rows: from tensor memory (every tile of the CTA in this one
+      // group), or from a.dlat_rows with eight loads in flight per thread
+      // before their stores
+      const int n4 = dz_tmem ? 0 : nt * kRows * (kLatent / 4);
+      if (dz_tmem) {
+        tc::tc_fence_after();
+        for (int t = 0; t < nt; ++t) {
+          float v[16];
+          tc::tmem_ld16(tmem + lane + kColDz + 32u * (uint32_t)t + 16u * (uint32_t)hf, v);
+          tc::tmem_ld_wait();
+          const bool in = (t0 + (int64_t)t * gridDim.x) * kRows + r < a.g.n;
+          float4 *dst = reinterpret_cast<float4 *>(stage + ((size_t)t * kRows + r) * kLatent + 16 * hf);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            dst[i] = in ? make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3])
+                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+      }
       for (int e0 = tid; e0 < n4; e0 += 8 * kThreads) {
         float4 v4[8];
 #pragma unroll

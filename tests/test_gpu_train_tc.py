@@ -103,6 +103,24 @@ def test_tensor_core_gradient_many_materials(fab, tmp_path):
     assert rel_l2(g_bf[:ND], want[:ND]) <= TOL_DEC_BF16 and rel_l2(g_bf[ND:], want[ND:]) <= TOL_ENC_BF16
 
 
+@pytest.mark.parametrize("n", [65536, 6 * 152 * 128 + 77])
+def test_tensor_core_gradient_large_batch(fab, tmp_path, n):
+    """Batches whose CTAs take up to five tiles (the latent-gradient rows
+    stay in tensor memory until the per-material sums) and more than five
+    (the rows go through global memory): both match the oracle."""
+    mats = W.training_materials(2)
+    g = W.training_queries(n, len(mats), stream=f"tc-grad-large-{n}")
+    target = np.abs(np.random.default_rng(12).standard_normal((n, 4)) * 0.2).astype(np.float32)
+    gd, tt = GBuffer.from_numpy(g), torch.from_numpy(target).cuda()
+    dec, enc = W.decoder_init(weight_bound="small"), W.encoder_init(weight_bound="small")
+    want_loss, want = oracle_gradient(mats, g, target, dec, enc, "eq11")
+    loss_bf, g_bf = one_step_gradient(fab, tmp_path, "bf16", "eq11", mats, gd, tt, dec, enc)
+    print(f"n={n}: loss bf16 {loss_bf:.6g} fp64 {want_loss:.6g}; grad rel-L2 decoder "
+          f"{rel_l2(g_bf[:ND], want[:ND]):.2e}, encoder {rel_l2(g_bf[ND:], want[ND:]):.2e}")
+    assert abs(loss_bf - want_loss) <= 2e-2 * abs(want_loss)
+    assert rel_l2(g_bf[:ND], want[:ND]) <= TOL_DEC_BF16 and rel_l2(g_bf[ND:], want[ND:]) <= TOL_ENC_BF16
+
+
 def test_tensor_core_training_is_repeatable_and_learns(fab):
     mats = W.training_materials(2)
     g = W.training_queries(8192, len(mats), stream="tc-learn")
