@@ -327,17 +327,25 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       nxt_mat = -1;
     }
   };
-  // half 1, step s of encoding the next tile's record into [q | 1 | 0]:
-  // 1 the octaves of u, 2 those of v, 3 log r, the directions, the constant
-  // one and the padding, and all zeros where there is no query
+  // half 1, step s of encoding the next tile's record into [q | 1 | 0], in
+  // pieces that fit the waits they fill: 1 and 2 the octaves 0-3 and 4-7 of
+  // u, 3 and 4 those of v, and with 4 also log r, the directions, the
+  // constant one and the padding, and all zeros where there is no query.
+  // Each octave is the one octaves_accurate() computes.
+  auto octave = [&](float x, int k) -> uint32_t {
+    const float f0 = x - floorf(x);
+    const float sc = f0 * (float)(1 << k);
+    const float fk = sc - floorf(sc);
+    float sn, cs;
+    sincospif(2.0f * fk, &sn, &cs);
+    return tc::pack_bf16(sn, cs);
+  };
   auto encode_step = [&](int s) {
-    if (hf != 1) return;
-    if (s == 1 || s == 2) {
-      float f[16];
-      octaves_accurate(in_v[s - 1], f);
+    if (hf != 1 || s < 1) return;
+    const int c = (s - 1) >> 1, k0 = 4 * ((s - 1) & 1);   // coordinate (u, v) and first octave
 #pragma unroll
-      for (int k = 0; k < 8; ++k) in_x[8 * (s - 1) + k] = tc::pack_bf16(f[2 * k], f[2 * k + 1]);
-    } else if (s == 3) {
+    for (int k = 0; k < 4; ++k) in_x[8 * c + k0 + k] = octave(in_v[c], k0 + k);
+    if (s == 4) {
       resolve();
       static_assert(kDecIn - kLatent - 32 == 7, "inputs 32..79: 32 octave values, log r, 6 directions, one");
       float x[16];
@@ -375,9 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   load_early(blockIdx.x);
   resolve();
   if (hf == 1) {
-    encode_step(1);
-    encode_step(2);
-    encode_step(3);
+    for (int k = 1; k <= 4; ++k) encode_step(k);
   }
   grid_dependency_wait();
   if (lead) {
@@ -416,7 +422,8 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
     load_early(tile + gridDim.x);
     // ---- forward: three hidden layers (ReLU masks of this half's columns
     // in registers) and the head; half 1 encodes the next tile's record
-    // during the products of layers 2, 3 and the head
+    // during the products of layers 2, 3 and the head, and while half 0
+    // evaluates the loss
     uint32_t mask[3];
     const uint32_t wf[3] = {s_w + kW1f, s_w + kW2f, s_w + kW3f};
     uint8_t *const hT[3] = {h1T, h2T, h3T};
@@ -465,6 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       st_row8(daA, 0, r, 16, w);
       st_row8(daA, 8, r, 16, w + 4);
       load_late(tile + gridDim.x);   // in flight during the backward pass
+    } else {
+      encode_step(4);
     }
     // ---- backward: dh_{l} = da_{l+1} W_{l+1}; dW_{l+1}^T += h_l^T da_{l+1}.
     // The da of the head, of layer 3, 2 and 1 go to buffers A, B, A, B; an
