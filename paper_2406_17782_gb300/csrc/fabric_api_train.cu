@@ -111,6 +111,7 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   void *tc_blob = c.take<uint8_t>(train_tc_blob_bytes());
   double *loss = loss_dev ? loss_dev : loss_tmp;
   FAB_CUDA(ctx, launch_encoder_raw(ctx->d_train_raw, M, ctx->d_enc, feats, z, acts, s), "encoder forward");
+  const float *dec_partial = nullptr;   // tensor-core path: the decoder's per-CTA gradient partials
   if (tc) {
     Carve w{dwork};
     float *partial = w.take<float>((size_t)tc_grid * tc_width);
@@ -120,22 +121,45 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
              launch_train_tc(q, z, M, ctx->d_dec, batch->target, ctx->loss_mode, tc_blob, partial, loss_part, rows,
                              ctx->sm_count, ctx->d_status, s),
              "tensor-core decoder forward/backward");
-    FAB_CUDA(ctx, launch_decoder_grad_finish(q, M, partial, tc_grid, tc_width, loss_part, rows, grad, loss, dz, s),
-             "gradient sums");
+    // the decoder's gradient sums and Adam update run beside the encoder's
+    // gradients (DecAdamArgs below)
+    FAB_CUDA(ctx, launch_decoder_grad_finish(q, M, partial, tc_grid, tc_width, loss_part, rows, nullptr, loss, dz, s),
+             "latent-gradient and loss sums");
+    dec_partial = partial;
   } else {
     FAB_CUDA(ctx,
              launch_decoder_backward(q, z, M, ctx->d_dec, nullptr, batch->target, ctx->loss_mode, grad, dz, loss,
                                      dwork, ctx->sm_count, ctx->d_status, s),
              "decoder forward/backward");
   }
-  FAB_CUDA(ctx, launch_encoder_backward(feats, M, ctx->d_enc, acts, dz, grad + kDecParams, ework, s),
-           "encoder backward");
   ctx->adam_step += 1;
   ctx->version += 1;
   const size_t np = (size_t)kDecParams + kEncParams;
   float *m = ctx->d_adam, *v = ctx->d_adam + np;
-  FAB_CUDA(ctx, launch_adam(ctx->d_dec, kDecParams, ctx->d_enc, kEncParams, grad, m, v, lr, ctx->adam_step, s),
-           "adam");
+  DecAdamArgs da{};
+  if (dec_partial) {
+    da.partial = dec_partial;
+    da.n_part = tc_grid;
+    da.stride = tc_width;
+    da.n = kDecParams;
+    da.p = ctx->d_dec;
+    da.m = m;
+    da.v = v;
+    da.lr = lr;
+    adam_bias(ctx->adam_step, &da.bc1, &da.bc2);
+  }
+  FAB_CUDA(ctx,
+           launch_encoder_backward(feats, M, ctx->d_enc, acts, dz, grad + kDecParams, ework, s,
+                                   dec_partial ? &da : nullptr),
+           "encoder backward");
+  if (dec_partial)
+    FAB_CUDA(ctx,
+             launch_adam(ctx->d_enc, kEncParams, nullptr, 0, grad + kDecParams, m + kDecParams, v + kDecParams, lr,
+                         ctx->adam_step, s),
+             "adam");
+  else
+    FAB_CUDA(ctx, launch_adam(ctx->d_dec, kDecParams, ctx->d_enc, kEncParams, grad, m, v, lr, ctx->adam_step, s),
+             "adam");
   return FABRIC_OK;
 }
 

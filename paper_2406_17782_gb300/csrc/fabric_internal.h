@@ -264,8 +264,21 @@ cudaError_t launch_selftest_mma(const float *a, const float *b, int n, int k, in
 cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *enc, float *z, cudaStream_t s);
 cudaError_t launch_encoder_feats(const float *feats, int n, const float *enc, float *z, float *acts,
                                  cudaStream_t s);
+// The decoder's gradient summed from per-CTA partials and its Adam update,
+// run by extra blocks of the encoder-gradient launch, beside that work
+// instead of before it.  The sums are the ones launch_decoder_grad_finish
+// forms, in the same order.
+struct DecAdamArgs {
+  const float *partial;   // [n_part][stride]; the decoder's n columns first
+  int n_part, stride, n;
+  float *p, *m, *v;       // the decoder's parameters and their Adam moments
+  float lr, bc1, bc2;
+};
 cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc, const float *acts,
-                                    const float *dz, float *denc, float *work, cudaStream_t s);
+                                    const float *dz, float *denc, float *work, cudaStream_t s,
+                                    const DecAdamArgs *dec_adam = nullptr);
+// Adam's bias corrections 1 - beta^t for step t.
+void adam_bias(int64_t step, float *bc1, float *bc2);
 size_t encoder_backward_work_floats(int n);
 // Encoder forward with the input features computed from the material
 // records (and written to feats_out, when not null, for the backward pass).
@@ -278,10 +291,10 @@ cudaError_t launch_decoder_backward(const fabric_gbuffer &g, const float *latent
                                     double *loss, void *work, int sm_count, int *status, cudaStream_t s);
 size_t decoder_backward_work_bytes(int64_t n, int sm_count);
 // The fixed-order sums after a backward pass that wrote per-CTA partials
-// ([grid][width] floats): parameter gradients, the loss, and the
-// per-material latent gradients (from the partials' columns past
-// kDecParams when width > kDecParams, else from the per-row latent
-// gradients `rows`).
+// ([grid][width] floats): parameter gradients (left to a DecAdamArgs launch
+// when ddec is null), the loss, and the per-material latent gradients (from
+// the partials' columns past kDecParams when width > kDecParams, else from
+// the per-row latent gradients `rows`).
 cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const float *partial, int grid, int width,
                                       const double *loss_part, const float *rows, float *ddec, double *loss,
                                       float *dlat, cudaStream_t s);

@@ -650,6 +650,46 @@ __global__ void __launch_bounds__(kEncHidden) encoder_bwd_vec_kernel(const float
 // materials in order; the block is then (first half) + (second half).
 constexpr int kGradChunk = 64;
 
+// Adam (Kingma and Ba 2015) with bias correction, one parameter.
+__device__ __forceinline__ void adam_update(float *p, float *m, float *v, float g, float lr, float bc1, float bc2) {
+  const float mi = 0.9f * *m + 0.1f * g;
+  const float vi = 0.999f * *v + 0.001f * g * g;
+  *m = mi;
+  *v = vi;
+  *p -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+}
+
+// Block cb of the decoder's gradient: columns 32 cb .. 32 cb + 31 summed over
+// the partials exactly as reduce_partials_kernel sums them (kSumSegs
+// segments of partials in order, then the segments in order), then Adam.
+// Run by threads 0..255 of the block.
+__device__ void dec_reduce_adam(const DecAdamArgs &d, int cb) {
+  __shared__ float seg_sum[kSumSegs][32];
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int j = cb * 32 + lane;
+  const int per = (d.n_part + kSumSegs - 1) / kSumSegs;
+  const int c0 = min(d.n_part, seg * per), c1 = min(d.n_part, c0 + per);
+  float s = 0.0f;
+  if (j < d.n) {
+    for (int c = c0; c < c1; c += kSumBatch) {
+      float t[kSumBatch];
+#pragma unroll
+      for (int q = 0; q < kSumBatch; ++q) t[q] = c + q < c1 ? d.partial[(int64_t)(c + q) * d.stride + j] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < kSumBatch; ++q)
+        if (c + q < c1) s += t[q];
+    }
+  }
+  seg_sum[seg][lane] = s;
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kSumSegs) : "memory");
+  if (seg == 0 && j < d.n) {
+    float tot = seg_sum[0][lane];
+#pragma unroll
+    for (int k = 1; k < kSumSegs; ++k) tot += seg_sum[k][lane];
+    adam_update(d.p + j, d.m + j, d.v + j, tot, d.lr, d.bc1, d.bc2);
+  }
+}
+
 struct GradBlock {
   int l_off, r_off;        // column offsets of L and R in their per-material rows (r_off < 0: R = 1)
   int l_src, r_src;        // 0: work rows (512 floats), 1: feats rows (kEncIn), 2: dz rows (kLatent)
@@ -683,9 +723,13 @@ constexpr int kGradThreads = 512;
 __global__ void __launch_bounds__(kGradThreads) encoder_grad_kernel(const float *__restrict__ feats, int n,
                                                                     const float *__restrict__ dz,
                                                                     const float *__restrict__ work,
-                                                                    float *__restrict__ denc) {
+                                                                    float *__restrict__ denc, const DecAdamArgs dec) {
   grid_dependency_wait();
   grid_dependents_launch();
+  if (blockIdx.x >= kGradTiles) {   // the decoder's gradient sums and Adam update
+    if (threadIdx.x < 32 * kSumSegs) dec_reduce_adam(dec, blockIdx.x - kGradTiles);
+    return;
+  }
   __shared__ __align__(16) float sl[2][kGradChunk][32];
   __shared__ float sr[2][kGradChunk][32];
   // which block, and which 32 x 32 tile of it
@@ -757,12 +801,7 @@ __global__ void adam_kernel(float *__restrict__ p0, int64_t n0, float *__restric
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n0 + n1) return;
   float *p = i < n0 ? p0 + i : p1 + (i - n0);
-  const float gi = g[i];
-  const float mi = 0.9f * m[i] + 0.1f * gi;
-  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  *p -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+  adam_update(p, m + i, v + i, g[i], lr, bc1, bc2);
 }
 
 // ---------------------------------------------------------------------------
@@ -1260,9 +1299,17 @@ cudaError_t launch_decoder_grad_finish(const fabric_gbuffer &g, int n_lat, const
   // width > kDecParams: the per-CTA partials already hold the per-material
   // latent-gradient sums after the decoder's columns
   const bool folded = width > kDecParams;
-  const int cols = dlat ? width : kDecParams;
-  launch_dependent(reduce_partials_kernel, (cols + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s, partial, grid,
-                   width, cols, kDecParams, ddec, dlat, loss_part, loss);
+  if (ddec) {
+    const int cols = dlat ? width : kDecParams;
+    launch_dependent(reduce_partials_kernel, (cols + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s, partial, grid,
+                     width, cols, kDecParams, ddec, dlat, loss_part, loss);
+  } else {   // only the latent columns (folded) and the loss
+    const int cols = dlat && folded ? width - kDecParams : 0;
+    if (cols > 0 || loss)
+      launch_dependent(reduce_partials_kernel, (cols + 31) / 32 + (loss ? 1 : 0), 32 * kSumSegs, 0, s,
+                       partial + kDecParams, grid, width, cols, 0, static_cast<float *>(nullptr), dlat, loss_part,
+                       loss);
+  }
   if (dlat && !folded) latent_sums(g, n_lat, rows, dlat, s);
   return cudaGetLastError();
 }
@@ -1299,7 +1346,8 @@ cudaError_t launch_encoder_raw(const fabric_material *raw, int n, const float *e
 size_t encoder_backward_work_floats(int n) { return (size_t)n * 2 * kEncHidden + (size_t)n * 4 * kEncHidden; }
 
 cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc, const float *acts_in,
-                                    const float *dz, float *denc, float *work, cudaStream_t s) {
+                                    const float *dz, float *denc, float *work, cudaStream_t s,
+                                    const DecAdamArgs *dec_adam) {
   // work: [n][2][128] activations (recomputed when acts_in is null) | [n][4][128]
   float *acts = work;
   float *vec = work + (size_t)n * 2 * kEncHidden;
@@ -1321,14 +1369,25 @@ cudaError_t launch_encoder_backward(const float *feats, int n, const float *enc,
     launch_dependent(encoder_bwd_vec_kernel<true>, grid, kEncHidden, kEncBwdSmem, s, enc, n, acts_in, dz, vec);
   else
     launch_dependent(encoder_bwd_vec_kernel<false>, grid, kEncHidden, kEncBwdSmem, s, enc, n, acts_in, dz, vec);
-  launch_dependent(encoder_grad_kernel, kGradTiles, kGradThreads, 0, s, feats, n, dz, vec, denc);
+  DecAdamArgs d{};
+  int extra = 0;
+  if (dec_adam) {
+    d = *dec_adam;
+    extra = (d.n + 31) / 32;
+  }
+  launch_dependent(encoder_grad_kernel, kGradTiles + extra, kGradThreads, 0, s, feats, n, dz, vec, denc, d);
   return cudaGetLastError();
+}
+
+void adam_bias(int64_t step, float *bc1, float *bc2) {
+  *bc1 = (float)(1.0 - std::pow(0.9, (double)step));
+  *bc2 = (float)(1.0 - std::pow(0.999, (double)step));
 }
 
 cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const float *grad, float *m, float *v, float lr,
                         int64_t step, cudaStream_t s) {
-  const float bc1 = (float)(1.0 - std::pow(0.9, (double)step));
-  const float bc2 = (float)(1.0 - std::pow(0.999, (double)step));
+  float bc1, bc2;
+  adam_bias(step, &bc1, &bc2);
   launch_dependent(adam_kernel, (unsigned)((n0 + n1 + 255) / 256), 256, 0, s, p0, n0, p1, n1, grad, m, v, lr, bc1, bc2);
   return cudaGetLastError();
 }
