@@ -291,6 +291,24 @@ fabric_status fabric_set_train_materials(fabric_ctx *ctx, const fabric_material 
 fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch, float lr,
                                 double *loss_dev, void *stream);
 
+/*
+ * n_steps training steps of fabric_train_step over one dataset, without a
+ * host round trip between them: step k (k = 0 .. n_steps - 1) takes the
+ * `batch` queries and targets starting at point (k mod (n / batch)) * batch
+ * of data (n = data->queries.n, so an epoch is n / batch steps over
+ * consecutive slices; shuffle the dataset between calls), with learning rate
+ *   lr(t) = lr1 + (lr0 - lr1) (1 + cos(pi t / total_steps)) / 2,
+ * t = first_step + k, evaluated in double and rounded to float (a cosine
+ * decay over total_steps steps).  loss_dev (device doubles, optional) gets
+ * step k's loss at loss_dev[k].  The results are bitwise those of the same
+ * single steps.  batch 1..min(n, 1048576); n_steps >= 0; total_steps >= 1;
+ * first_step >= 0; else FABRIC_ERR_INVALID_ARG.  Errors of a step end the
+ * call with that step's status (the steps before it are applied).
+ */
+fabric_status fabric_train_steps(fabric_ctx *ctx, const fabric_train_batch *data, int64_t batch, int n_steps,
+                                 int64_t first_step, int64_t total_steps, double lr0, double lr1,
+                                 double *loss_dev, void *stream);
+
 /* Training loss of fabric_train_step (default FABRIC_LOSS_EQ11):
  *   FABRIC_LOSS_EQ11      the paper's Eq. 11, as above;
  *   FABRIC_LOSS_RENDERED  this library's option: (1/B) sum over queries and

@@ -98,6 +98,8 @@ def load(path: str | None = None):
         "fabric_prepare_neural": (st, [vp, vp, st, vp]),
         "fabric_shade_neural_prepared": (st, [vp, P(FabricGBuffer), st, vp, vp, vp]),
         "fabric_train_step": (st, [vp, P(FabricTrainBatch), ctypes.c_float, vp, vp]),
+        "fabric_train_steps": (st, [vp, P(FabricTrainBatch), i64, i32, i64, i64, ctypes.c_double, ctypes.c_double,
+                                    vp, vp]),
         "fabric_decoder_forward": (st, [vp, P(FabricGBuffer), vp, i32, vp, vp, vp]),
         "fabric_decoder_backward": (st, [vp, P(FabricGBuffer), vp, i32, vp, vp, vp, vp, vp]),
         "fabric_encoder_forward": (st, [vp, vp, i32, vp, vp, vp]),

@@ -254,6 +254,21 @@ class Fabric:
                                                _stream_handle(stream)))
         return loss
 
+    def train_steps(self, data: GBuffer, target: torch.Tensor, batch: int, n_steps: int, first_step: int,
+                    total_steps: int, lr0: float, lr1: float, loss_out=None, stream=None):
+        """n_steps steps of train_step over consecutive batch-sized slices of
+        data (wrapping after n // batch steps), with the cosine learning
+        rate lr1 + (lr0 - lr1) (1 + cos(pi t / total_steps)) / 2 at step
+        t = first_step + k, in one call (fabric_train_steps).  loss_out:
+        optional float64 device tensor of at least n_steps entries."""
+        if loss_out is not None:
+            assert loss_out.dtype == torch.float64 and loss_out.is_contiguous() and loss_out.numel() >= n_steps
+        tb = FabricTrainBatch(data.struct(), target.contiguous().data_ptr())
+        self._check(self.lib.fabric_train_steps(self.h, ctypes.byref(tb), int(batch), int(n_steps), int(first_step),
+                                                int(total_steps), float(lr0), float(lr1),
+                                                _ptr(loss_out) if loss_out is not None else None,
+                                                _stream_handle(stream)))
+
     def error_stats(self, a: torch.Tensor, b: torch.Tensor, weights: torch.Tensor = None, group: int = 1,
                     weight_stride: int = 1, out=None, stream=None) -> torch.Tensor:
         """[sum (w(a-b))^2, sum (w b)^2, max |w(a-b)|] in FP64 on the device;

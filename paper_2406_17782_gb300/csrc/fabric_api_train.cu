@@ -1,5 +1,7 @@
 // fabric_api_train.cu -- C ABI entry points of the encoder, the training step
 // and the autograd building blocks (include/fabric.h).  Host code only.
+#include <cmath>
+
 #include "fabric_internal.h"
 
 using namespace fab;
@@ -160,6 +162,37 @@ fabric_status fabric_train_step(fabric_ctx *ctx, const fabric_train_batch *batch
   else
     FAB_CUDA(ctx, launch_adam(ctx->d_dec, kDecParams, ctx->d_enc, kEncParams, grad, m, v, lr, ctx->adam_step, s),
              "adam");
+  return FABRIC_OK;
+}
+
+fabric_status fabric_train_steps(fabric_ctx *ctx, const fabric_train_batch *data, int64_t batch, int n_steps,
+                                 int64_t first_step, int64_t total_steps, double lr0, double lr1, double *loss_dev,
+                                 void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!data) return fail(ctx, FABRIC_ERR_INVALID_ARG, "dataset is NULL");
+  const fabric_gbuffer &g = data->queries;
+  if (batch < 1 || batch > g.n || batch > (1 << 20))
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "batch must be 1..min(n, 1048576)");
+  if (n_steps < 0 || total_steps < 1 || first_step < 0)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "n_steps >= 0, total_steps >= 1 and first_step >= 0 required");
+  const int64_t per_epoch = g.n / batch;
+  for (int k = 0; k < n_steps; ++k) {
+    const int64_t off = (k % per_epoch) * batch;
+    fabric_train_batch b;
+    b.queries = g;
+    b.queries.u = g.u ? g.u + off : nullptr;
+    b.queries.v = g.v ? g.v + off : nullptr;
+    b.queries.radius = g.radius ? g.radius + off : nullptr;
+    b.queries.wi = g.wi ? g.wi + 3 * off : nullptr;
+    b.queries.wo = g.wo ? g.wo + 3 * off : nullptr;
+    b.queries.material = g.material ? g.material + off : nullptr;
+    b.queries.n = batch;
+    b.target = data->target ? data->target + 4 * off : nullptr;
+    const double t = (double)(first_step + k);
+    const float lr = (float)(lr1 + 0.5 * (lr0 - lr1) * (1.0 + std::cos(3.141592653589793 * t / (double)total_steps)));
+    const fabric_status st = fabric_train_step(ctx, &b, lr, loss_dev ? loss_dev + k : nullptr, stream);
+    if (st != FABRIC_OK) return st;
+  }
   return FABRIC_OK;
 }
 

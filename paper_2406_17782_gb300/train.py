@@ -77,10 +77,31 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
     gen = torch.Generator(device=fab.device)
     gen.manual_seed(seed)
     per_epoch = g.n // batch
+    if per_epoch < 1:
+        raise ValueError(f"the dataset ({g.n} points) is smaller than one batch ({batch})")
     losses = []
-    loss_buf = torch.empty(log_every, dtype=torch.float64, device=fab.device)
     t0 = time.time()
     gs, ts = shuffled(g, target, gen)
+    if not paper:
+        # one native call per epoch (fabric_train_steps: the same steps,
+        # learning rates and results as the per-step loop below)
+        all_loss = torch.empty(max(1, steps), dtype=torch.float64, device=fab.device)
+        step = 0
+        while step < steps:
+            if step > 0:
+                gs, ts = shuffled(g, target, gen)
+            n = min(per_epoch, steps - step)
+            fab.train_steps(gs, ts, batch, n, step, max(1, steps), lr0, lr1, loss_out=all_loss[step:step + n])
+            for m in range((step // log_every + 1) * log_every, step + n + 1, log_every):
+                mean = float(all_loss[m - log_every:m].mean().item())
+                losses.append((m, mean))
+                if verbose:
+                    lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * (m - 1) / max(1, steps)))
+                    print(f"step {m:7d}  loss {mean:.5f}  lr {lr:.2e}  {time.time() - t0:6.1f}s", flush=True)
+            step += n
+        fab.sync_status()
+        return losses
+    loss_buf = torch.empty(log_every, dtype=torch.float64, device=fab.device)
     for step in range(steps):
         k = step % per_epoch
         if k == 0 and step > 0:

@@ -205,3 +205,41 @@ def test_checkpoint_resume_is_bitwise(fab, tmp_path):
     assert e.value.status == 5
     with pytest.raises(FabricError):
         fab.checkpoint_load(str(tmp_path / "missing.bin"))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_train_steps_equal_single_steps(fab, prec):
+    """fabric_train_steps (one native call for several steps over consecutive
+    slices of a dataset, with the cosine learning rate) against the same
+    steps one train_step call at a time: bitwise the same losses and
+    parameters, across an epoch's wrap-around and from a nonzero first step.
+    Arguments out of range are refused."""
+    import math
+    mats = W.training_materials(2)
+    n, bsz, n_steps, first, total, lr0, lr1 = 3000, 1000, 7, 5, 40, 3e-3, 1e-5
+    g = batch(n, len(mats), stream="steps")
+    target = np.abs(np.random.default_rng(13).standard_normal((n, 4)) * 0.2).astype(np.float32)
+    gd, tt = GBuffer.from_numpy(g), torch.from_numpy(target).cuda()
+    fab.set_train_materials(mats)
+    fab.set_train_precision(prec)
+    try:
+        fab.set_params(W.decoder_init(), W.encoder_init())
+        loss_a = torch.empty(n_steps, dtype=torch.float64, device="cuda")
+        fab.train_steps(gd, tt, bsz, n_steps, first, total, lr0, lr1, loss_out=loss_a)
+        a = fab.get_params()
+        fab.set_params(W.decoder_init(), W.encoder_init())
+        loss_b = []
+        for k in range(n_steps):
+            sl = slice((k % (n // bsz)) * bsz, (k % (n // bsz) + 1) * bsz)
+            bg = GBuffer(*(getattr(gd, f)[sl] for f in ("u", "v", "radius", "wi", "wo", "material")))
+            lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * (first + k) / total))
+            loss_b.append(float(fab.train_step(bg, tt[sl], lr).item()))
+        b = fab.get_params()
+        fab.sync_status()
+    finally:
+        fab.set_train_precision("fp32")
+    assert loss_a.cpu().tolist() == loss_b
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for bad in [(0, 1, 0, 1), (n + 1, 1, 0, 1), (bsz, -1, 0, 1), (bsz, 1, 0, 0), (bsz, 1, -1, 1)]:
+        with pytest.raises(FabricError):
+            fab.train_steps(gd, tt, bad[0], bad[1], bad[2], bad[3], lr0, lr1)
