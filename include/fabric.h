@@ -309,6 +309,31 @@ fabric_status fabric_train_steps(fabric_ctx *ctx, const fabric_train_batch *data
                                  int64_t first_step, int64_t total_steps, double lr0, double lr1,
                                  double *loss_dev, void *stream);
 
+/* Output arrays of fabric_shuffle_dataset: device memory of the caller, the
+ * layout of fabric_train_batch (wi, wo [n][3], target [n][4]), not
+ * overlapping the input. */
+typedef struct {
+  float *u;
+  float *v;
+  float *radius;
+  float *wi;
+  float *wo;
+  uint16_t *material;
+  float *target;   /* NULL when the input has no targets */
+} fabric_dataset_out;
+
+/*
+ * A shuffled copy of a training dataset in one pass on the device (the data
+ * loader between epochs): dst[p] = src[pi(p)] for every field, p < n, where
+ * pi is the pseudo-random permutation of [0, n) that `seed` selects: a
+ * four-round Feistel network on [0, 4^k), 4^k >= n, whose round function is
+ * the SplitMix64 finaliser of (seed, round, half), walked along its cycles
+ * until it lands in [0, n).  pi depends only on n and seed.  n 1..2^31;
+ * FABRIC_ERR_INVALID_ARG for NULL or misaligned arrays.  Asynchronous.
+ */
+fabric_status fabric_shuffle_dataset(fabric_ctx *ctx, const fabric_train_batch *src, const fabric_dataset_out *dst,
+                                     uint64_t seed, void *stream);
+
 /* Training loss of fabric_train_step (default FABRIC_LOSS_EQ11):
  *   FABRIC_LOSS_EQ11      the paper's Eq. 11, as above;
  *   FABRIC_LOSS_RENDERED  this library's option: (1/B) sum over queries and

@@ -39,6 +39,10 @@ class FabricTrainBatch(ctypes.Structure):
     _fields_ = [("queries", FabricGBuffer), ("target", ctypes.c_void_p)]
 
 
+class FabricDatasetOut(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("u", "v", "radius", "wi", "wo", "material", "target")]
+
+
 class FabricSegment(ctypes.Structure):
     _fields_ = [("g", FabricGBuffer), ("rgb_dev", ctypes.c_void_p), ("comps_dev", ctypes.c_void_p)]
 
@@ -98,6 +102,7 @@ def load(path: str | None = None):
         "fabric_prepare_neural": (st, [vp, vp, st, vp]),
         "fabric_shade_neural_prepared": (st, [vp, P(FabricGBuffer), st, vp, vp, vp]),
         "fabric_train_step": (st, [vp, P(FabricTrainBatch), ctypes.c_float, vp, vp]),
+        "fabric_shuffle_dataset": (st, [vp, P(FabricTrainBatch), P(FabricDatasetOut), u64, vp]),
         "fabric_train_steps": (st, [vp, P(FabricTrainBatch), i64, i32, i64, i64, ctypes.c_double, ctypes.c_double,
                                     vp, vp]),
         "fabric_decoder_forward": (st, [vp, P(FabricGBuffer), vp, i32, vp, vp, vp]),

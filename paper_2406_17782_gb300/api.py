@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import PAPER_STRUCTURES, FabricGBuffer, FabricMaterial, FabricTrainBatch, check
+from ._abi import PAPER_STRUCTURES, FabricDatasetOut, FabricGBuffer, FabricMaterial, FabricTrainBatch, check
 
 LATENT = 32
 
@@ -268,6 +268,24 @@ class Fabric:
                                                 int(total_steps), float(lr0), float(lr1),
                                                 _ptr(loss_out) if loss_out is not None else None,
                                                 _stream_handle(stream)))
+
+    def shuffle_dataset(self, data: GBuffer, target: torch.Tensor, seed: int, out: tuple = None, stream=None):
+        """A shuffled copy (GBuffer, target) of a training dataset in one pass
+        on the device (fabric_shuffle_dataset): every field of point p is
+        point pi(p) of the input, pi the permutation of [0, n) that `seed`
+        selects.  out: optional (GBuffer, target) to write into (not
+        overlapping the input)."""
+        target = target.contiguous()
+        if out is None:
+            out = (GBuffer(*(torch.empty_like(getattr(data, k)) for k in ("u", "v", "radius", "wi", "wo", "material"))),
+                   torch.empty_like(target))
+        og, ot = out
+        tb = FabricTrainBatch(data.struct(), target.data_ptr())
+        do = FabricDatasetOut(*(getattr(og, k).data_ptr() for k in ("u", "v", "radius", "wi", "wo", "material")),
+                              ot.data_ptr())
+        self._check(self.lib.fabric_shuffle_dataset(self.h, ctypes.byref(tb), ctypes.byref(do),
+                                                    ctypes.c_uint64(seed & (2 ** 64 - 1)), _stream_handle(stream)))
+        return og, ot
 
     def error_stats(self, a: torch.Tensor, b: torch.Tensor, weights: torch.Tensor = None, group: int = 1,
                     weight_stride: int = 1, out=None, stream=None) -> torch.Tensor:

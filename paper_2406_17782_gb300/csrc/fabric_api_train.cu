@@ -196,6 +196,27 @@ fabric_status fabric_train_steps(fabric_ctx *ctx, const fabric_train_batch *data
   return FABRIC_OK;
 }
 
+fabric_status fabric_shuffle_dataset(fabric_ctx *ctx, const fabric_train_batch *src, const fabric_dataset_out *dst,
+                                     uint64_t seed, void *stream) {
+  FAB_CHECK_CTX(ctx);
+  if (!src || !dst) return fail(ctx, FABRIC_ERR_INVALID_ARG, "dataset is NULL");
+  const fabric_gbuffer &g = src->queries;
+  if (!check_gbuffer(ctx, &g)) return FABRIC_ERR_INVALID_ARG;
+  if (g.n < 1 || g.n > (1ll << 31)) return fail(ctx, FABRIC_ERR_INVALID_ARG, "dataset size must be 1..2^31");
+  if (!dst->u || !dst->v || !dst->radius || !dst->wi || !dst->wo || !dst->material)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "output array is NULL");
+  if (!src->target != !dst->target)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "targets must be given on both sides or on neither");
+  const void *f[] = {dst->u, dst->v, dst->radius, dst->wi, dst->wo, dst->target, src->target};
+  for (const void *p : f)
+    if (reinterpret_cast<uintptr_t>(p) & 3u) return fail(ctx, FABRIC_ERR_INVALID_ARG, "arrays must be float-aligned");
+  if (reinterpret_cast<uintptr_t>(dst->material) & 1u)
+    return fail(ctx, FABRIC_ERR_INVALID_ARG, "material array must be 2-byte aligned");
+  FAB_CUDA(ctx, launch_shuffle_dataset(*src, *dst, seed, ctx->sm_count, static_cast<cudaStream_t>(stream)),
+           "dataset shuffle");
+  return FABRIC_OK;
+}
+
 fabric_status fabric_decoder_forward(fabric_ctx *ctx, const fabric_gbuffer *g, const float *latents_dev, int n_lat,
                                      const float *dec_dev, float *y_dev, void *stream) {
   FAB_CHECK_CTX(ctx);

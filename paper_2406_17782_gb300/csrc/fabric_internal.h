@@ -308,6 +308,9 @@ cudaError_t launch_selftest_mn(const float *a, const float *b, int n, int k, flo
 cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                             const float *target, int loss_mode, void *blob, float *partial, double *loss_partial,
                             float *dlat_rows, int sm_count, int *status, cudaStream_t s);
+// dst[p] = src[pi(p)] for the dataset's fields (fabric_shuffle_dataset).
+cudaError_t launch_shuffle_dataset(const fabric_train_batch &src, const fabric_dataset_out &dst, uint64_t seed,
+                                   int sm_count, cudaStream_t s);
 cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const float *grad, float *m, float *v, float lr,
                         int64_t step, cudaStream_t s);
 // The paper's decoder structure (paper_decoder.cu): K of its first layer for

@@ -6,6 +6,8 @@
 // then a fixed-order sum over CTAs), so repeated runs are bitwise identical.
 #include <cmath>
 
+#include <algorithm>
+
 #include "fabric_internal.h"
 #include "train_common.cuh"
 
@@ -1389,6 +1391,67 @@ cudaError_t launch_adam(float *p0, int64_t n0, float *p1, int64_t n1, const floa
   float bc1, bc2;
   adam_bias(step, &bc1, &bc2);
   launch_dependent(adam_kernel, (unsigned)((n0 + n1 + 255) / 256), 256, 0, s, p0, n0, p1, n1, grad, m, v, lr, bc1, bc2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Dataset shuffle: a pseudo-random permutation of [0, n) from a four-round
+// Feistel network on [0, 4^k) (balanced halves of k bits, 4^k >= n) with
+// the SplitMix64 finaliser of (seed, round, half) as round function; values
+// at or past n are walked along their cycle (the network is a bijection of
+// [0, 4^k), so the walk returns to [0, n)).
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ uint64_t shuffle_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t feistel(uint64_t x, int k, uint64_t seed) {
+  const uint64_t mask = (1ull << k) - 1ull;
+  uint64_t l = x >> k, r = x & mask;
+#pragma unroll
+  for (int round = 0; round < 4; ++round) {
+    const uint64_t f = shuffle_mix(seed + 0x9E3779B97F4A7C15ull * (uint64_t)(round + 1) + r) & mask;
+    const uint64_t t = l ^ f;
+    l = r;
+    r = t;
+  }
+  return (l << k) | r;
+}
+
+__global__ void shuffle_dataset_kernel(const fabric_train_batch src, const fabric_dataset_out dst, int k,
+                                       uint64_t seed) {
+  const int64_t n = src.queries.n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t j = feistel((uint64_t)p, k, seed);
+    while (j >= (uint64_t)n) j = feistel(j, k, seed);
+    const fabric_gbuffer &g = src.queries;
+    dst.u[p] = g.u[j];
+    dst.v[p] = g.v[j];
+    dst.radius[p] = g.radius[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dst.wi[3 * p + c] = g.wi[3 * j + c];
+      dst.wo[3 * p + c] = g.wo[3 * j + c];
+    }
+    dst.material[p] = g.material[j];
+    if (dst.target) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst.target[4 * p + c] = src.target[4 * j + c];
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_shuffle_dataset(const fabric_train_batch &src, const fabric_dataset_out &dst, uint64_t seed,
+                                   int sm_count, cudaStream_t s) {
+  const int64_t n = src.queries.n;
+  int k = 1;
+  while ((1ll << (2 * k)) < n) ++k;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)(sm_count > 0 ? sm_count : 148) * 8);
+  shuffle_dataset_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, k, seed);
   return cudaGetLastError();
 }
 

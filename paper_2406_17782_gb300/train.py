@@ -59,11 +59,9 @@ def generate_dataset(fab: Fabric, mats, n_queries: int, spp=(64, 32), seed: int 
     return g, target
 
 
-def shuffled(g: GBuffer, target: torch.Tensor, gen: torch.Generator):
-    perm = torch.randperm(g.n, device=target.device, generator=gen)
-    return (GBuffer(*(getattr(g, k).index_select(0, perm).contiguous()
-                      for k in ("u", "v", "radius", "wi", "wo", "material"))),
-            target.index_select(0, perm).contiguous())
+def epoch_seed(seed: int, epoch: int) -> int:
+    """The permutation seed of one epoch's shuffle."""
+    return (seed << 32) + epoch
 
 
 def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch: int = 65536,
@@ -74,14 +72,14 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
     (fabric_paper_train_step) instead of the workload's network."""
     step_fn = fab.paper_train_step if paper else fab.train_step
     fab.set_train_materials(mats)
-    gen = torch.Generator(device=fab.device)
-    gen.manual_seed(seed)
     per_epoch = g.n // batch
     if per_epoch < 1:
         raise ValueError(f"the dataset ({g.n} points) is smaller than one batch ({batch})")
     losses = []
     t0 = time.time()
-    gs, ts = shuffled(g, target, gen)
+    # each epoch a shuffled copy of the dataset (fabric_shuffle_dataset),
+    # written over the previous epoch's in stream order
+    gs, ts = fab.shuffle_dataset(g, target, epoch_seed(seed, 0))
     if not paper:
         # one native call per epoch (fabric_train_steps: the same steps,
         # learning rates and results as the per-step loop below)
@@ -89,7 +87,7 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
         step = 0
         while step < steps:
             if step > 0:
-                gs, ts = shuffled(g, target, gen)
+                gs, ts = fab.shuffle_dataset(g, target, epoch_seed(seed, step // per_epoch), out=(gs, ts))
             n = min(per_epoch, steps - step)
             fab.train_steps(gs, ts, batch, n, step, max(1, steps), lr0, lr1, loss_out=all_loss[step:step + n])
             for m in range((step // log_every + 1) * log_every, step + n + 1, log_every):
@@ -105,7 +103,7 @@ def train(fab: Fabric, mats, g: GBuffer, target: torch.Tensor, steps: int, batch
     for step in range(steps):
         k = step % per_epoch
         if k == 0 and step > 0:
-            gs, ts = shuffled(g, target, gen)
+            gs, ts = fab.shuffle_dataset(g, target, epoch_seed(seed, step // per_epoch), out=(gs, ts))
         sl = slice(k * batch, (k + 1) * batch)
         bg = GBuffer(*(getattr(gs, f)[sl] for f in ("u", "v", "radius", "wi", "wo", "material")))
         lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * step / max(1, steps)))

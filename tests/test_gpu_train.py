@@ -243,3 +243,28 @@ def test_train_steps_equal_single_steps(fab, prec):
     for bad in [(0, 1, 0, 1), (n + 1, 1, 0, 1), (bsz, -1, 0, 1), (bsz, 1, 0, 0), (bsz, 1, -1, 1)]:
         with pytest.raises(FabricError):
             fab.train_steps(gd, tt, bad[0], bad[1], bad[2], bad[3], lr0, lr1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 100003])
+def test_shuffle_dataset_is_a_permutation(fab, n):
+    """fabric_shuffle_dataset moves every field of a point together, and the
+    output is a permutation of the input that the seed alone selects."""
+    idx = torch.arange(n, dtype=torch.float32, device="cuda")
+    g = GBuffer(u=idx.clone(), v=idx + 0.5, radius=2.0 * idx, wi=torch.stack([idx, idx + 1, idx + 2], 1),
+                wo=torch.stack([-idx, -idx - 1, -idx - 2], 1),
+                material=(torch.arange(n, device="cuda") % 65536).to(torch.int32).to(torch.int16))
+    target = torch.stack([idx, 2 * idx, 3 * idx, 4 * idx], 1)
+    og, ot = fab.shuffle_dataset(g, target, 12345)
+    og2, ot2 = fab.shuffle_dataset(g, target, 12345)
+    og3, _ = fab.shuffle_dataset(g, target, 54321)
+    torch.cuda.synchronize()
+    u = og.u
+    assert torch.equal(torch.sort(u).values, idx)
+    assert torch.equal(og.v, u + 0.5) and torch.equal(og.radius, 2.0 * u)
+    assert torch.equal(og.wi, torch.stack([u, u + 1, u + 2], 1)) and torch.equal(og.wo, torch.stack([-u, -u - 1, -u - 2], 1))
+    assert torch.equal(og.material.to(torch.int64) & 0xFFFF, u.to(torch.int64) % 65536)
+    assert torch.equal(ot, torch.stack([u, 2 * u, 3 * u, 4 * u], 1))
+    assert torch.equal(og2.u, u) and torch.equal(ot2, ot)
+    if n >= 100:
+        assert not torch.equal(og3.u, u)
+        assert (u != idx).float().mean() > 0.99   # few points stay in place
