@@ -965,9 +965,15 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
 // which halves the arithmetic instruction count of the error-free
 // transformations; used when a and b are 8-byte aligned.  Lane 0 of every
 // packed value carries the even element of a pair, lane 1 the odd one; each
-// lane has its own double-float run sums.  An element outside the fast
-// range enters its lane as zeros (an exact no-op) and is added by the FP64
-// pass as in err_partial_kernel.
+// lane has its own double-float run sums.
+// No element is range-checked in the main loop.  Where the FP32 pairs cannot
+// carry a term exactly, the thread's results show it: a square or sum that
+// overflows (or a non-finite input) makes its FP64 sums non-finite, and a
+// square whose low part falls below the normal range loses at most 2^-149
+// absolutely, which is below 2^-49 of the thread's sum unless its largest
+// |w(a-b)| (or |w b|) is under sqrt(elements) 2^-50.  A thread in either
+// case (or with an exactly zero largest value, whose sums are then exact)
+// redoes its whole share in FP64 instead.
 constexpr int kErrRun2 = 16;    // pairs per run
 constexpr int kErrBatch2 = 4;   // pair loads in flight per thread
 constexpr int kErrPerSm2 = 4;   // resident CTAs per SM
@@ -1028,8 +1034,7 @@ __global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(c
   const Idx start = (Idx)blockIdx.x * kErrThreads + threadIdx.x;
   const uint64_t two = pk2(2.0f, 2.0f);
   double e2 = 0.0, b2s = 0.0;
-  float mh = -1.0f, ml = 0.0f;
-  bool slow = false;
+  float mh = -1.0f, ml = 0.0f, bmax = 0.0f;
   for (Idx j0 = start; j0 < np; j0 += kErrRun2 * stride) {
     uint64_t EH = 0, EL = 0, BH = 0, BL = 0;
 #pragma unroll 1
@@ -1066,33 +1071,18 @@ __global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(c
         float dh0, dh1, bh0, bh1;
         upk2(D, dh0, dh1);
         upk2(Bh, bh0, bh1);
-        bool ok0 = err_fast(dh0) && err_fast(bh0), ok1 = err_fast(dh1) && err_fast(bh1);
-        if (W) {
-          float w0, w1;
-          upk2(wv[q], w0, w1);
-          ok0 = ok0 && err_fast(w0);
-          ok1 = ok1 && err_fast(w1);
-        }
-        uint64_t PP = mul2(D, D);
-        uint64_t X = fma2(mul2(D, two), E, fma2(D, D, PP ^ kSign2));
-        uint64_t QQ = mul2(Bh, Bh);
-        uint64_t Y = fma2(mul2(Bh, two), Bl, fma2(Bh, Bh, QQ ^ kSign2));
-        if (!(ok0 && ok1)) {
-          slow = true;
-          const uint64_t keep = (ok0 ? 0xFFFFFFFFull : 0ull) | (ok1 ? 0xFFFFFFFF00000000ull : 0ull);
-          PP &= keep;
-          X &= keep;
-          QQ &= keep;
-          Y &= keep;
-        }
+        const uint64_t PP = mul2(D, D);
+        const uint64_t X = fma2(mul2(D, two), E, fma2(D, D, PP ^ kSign2));
+        const uint64_t QQ = mul2(Bh, Bh);
+        const uint64_t Y = W ? fma2(mul2(Bh, two), Bl, fma2(Bh, Bh, QQ ^ kSign2)) : fma2(Bh, Bh, QQ ^ kSign2);
         dadd2(EH, EL, PP, X);
         dadd2(BH, BL, QQ, Y);
+        bmax = fmaxf(bmax, fmaxf(fabsf(bh0), fabsf(bh1)));
         float dl0, dl1;
         upk2(E, dl0, dl1);
 #pragma unroll
         for (int lane = 0; lane < 2; ++lane) {
           const float dh = lane ? dh1 : dh0, dl = lane ? dl1 : dl0;
-          if (!(lane ? ok1 : ok0)) continue;
           const float sh = fabsf(dh);
           if (sh >= mh) {
             const float sl = dh < 0.0f ? -dl : dl;
@@ -1113,15 +1103,19 @@ __global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(c
     b2s += ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
   }
   double mx = mh < 0.0f ? 0.0 : (double)mh + (double)ml;
-  const bool odd_tail = (n & 1) && blockIdx.x == 0 && threadIdx.x == 0;
-  if (slow || odd_tail) {
-    // elements outside the fast range (and the odd last element) in FP64
-    auto fp64 = [&](Idx i, bool force) {
+  {
+    const double pairs = (double)((np - (start < np ? start : np) + stride - 1) / stride);   // this thread's pairs
+    const double floor_v = sqrt(2.0 * pairs) * 0x1p-50;
+    const bool slow = !isfinite(e2) || !isfinite(b2s) || (mh > 0.0f && (double)mh < floor_v) ||
+                      (bmax > 0.0f && (double)bmax < floor_v);
+    if (slow) {   // the thread's whole share again, in FP64
+      e2 = 0.0;
+      b2s = 0.0;
+      mx = 0.0;
+    }
+    auto fp64 = [&](Idx i) {
       const float ai = a[i], bi = b[i];
-      const float wv = W ? w[(int64_t)(i / group) * w_stride] : 1.0f;
-      float dh, dl, bh, bl;
-      if (!force && err_pairs<W>(ai, bi, wv, dh, dl, bh, bl)) return;
-      const double wi = (double)wv;
+      const double wi = W ? (double)w[(int64_t)(i / group) * w_stride] : 1.0;
       const double d = ((double)ai - (double)bi) * wi;
       const double bb = (double)bi * wi;
       e2 += d * d;
@@ -1130,10 +1124,10 @@ __global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(c
     };
     if (slow)
       for (Idx j = start; j < np; j += stride) {
-        fp64(2 * j, false);
-        fp64(2 * j + 1, false);
+        fp64(2 * j);
+        fp64(2 * j + 1);
       }
-    if (odd_tail) fp64(n - 1, true);
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) fp64(n - 1);   // the odd last element
   }
   s0[threadIdx.x] = e2;
   s1[threadIdx.x] = b2s;
