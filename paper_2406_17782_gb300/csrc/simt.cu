@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
 // case (or with an exactly zero largest value, whose sums are then exact)
 // redoes its whole share in FP64 instead.
 constexpr int kErrRun2 = 16;    // pairs per run
-constexpr int kErrBatch2 = 4;   // pair loads in flight per thread
+constexpr int kErrBatch2 = 4;   // pair loads in flight per thread (eight without weights)
 constexpr int kErrPerSm2 = 4;   // resident CTAs per SM
 constexpr int kErrBlocks2 = 152 * kErrPerSm2;   // one wave on 152 SMs
 
@@ -1038,10 +1038,11 @@ __global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(c
   for (Idx j0 = start; j0 < np; j0 += kErrRun2 * stride) {
     uint64_t EH = 0, EL = 0, BH = 0, BL = 0;
 #pragma unroll 1
-    for (int r0 = 0; r0 < kErrRun2; r0 += kErrBatch2) {
-      uint64_t av[kErrBatch2], bv[kErrBatch2], wv[kErrBatch2];
+    constexpr int NB = W ? kErrBatch2 : 2 * kErrBatch2;
+    for (int r0 = 0; r0 < kErrRun2; r0 += NB) {
+      uint64_t av[NB], bv[NB], wv[NB];
 #pragma unroll
-      for (int q = 0; q < kErrBatch2; ++q) {
+      for (int q = 0; q < NB; ++q) {
         const Idx j = j0 + (Idx)(r0 + q) * stride;
         const bool in = j < np;
         av[q] = in ? __ldg(a2 + j) : 0ull;
@@ -1053,7 +1054,7 @@ __global__ void __launch_bounds__(kErrThreads, kErrPerSm2) err_partial2_kernel(c
         }
       }
 #pragma unroll
-      for (int q = 0; q < kErrBatch2; ++q) {
+      for (int q = 0; q < NB; ++q) {
         // w (a - b) as D + E exactly (TwoSum, then the FMA TwoProduct by w)
         uint64_t D = sub2(av[q], bv[q]);
         const uint64_t BV = sub2(D, av[q]);
