@@ -20,10 +20,13 @@
 // gradient products, which nothing reads until the tile loop ends: each dW
 // chain is waited for only before the shared-memory operand it reads is
 // rewritten (the da operands alternate between two buffers for this).
-// At the end each CTA writes its gradient partials; the fixed-order
-// reduction over CTAs, the encoder backward and Adam are shared with the FP32
-// path.  Tensor-memory columns: D [0, 64), A [64, 104), dW1^T [128, 192),
-// dW2^T [192, 256), dW3^T [256, 320), dW4^T [320, 336).
+// At the end each CTA writes its gradient partials (and, for up to 1588
+// materials, its per-material latent sums); fixed-order reductions over the
+// CTAs follow in other kernels, the decoder's together with its Adam update
+// beside the encoder's gradients.  Tensor-memory columns: D [0, 64),
+// A [64, 104), dW1^T [128, 192), dW2^T [192, 256), dW3^T [256, 320),
+// dW4^T [320, 336), and the latent-gradient rows of up to five tiles
+// [336, 496).
 #include <cuda_bf16.h>
 
 #include "fabric_internal.h"
