@@ -110,6 +110,12 @@ __device__ __forceinline__ float ld_pinned(const float *p) {
   return v;
 }
 
+__device__ __forceinline__ float4 ld_pinned4(const float *p) {   // p 16-byte aligned
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+
 __device__ __forceinline__ int ld_pinned_u16(const uint16_t *p) {
   unsigned short v;
   asm volatile("ld.global.u16 %0, [%1];" : "=h"(v) : "l"(p));
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(256) train_pack_kernel(const float *__restrict
 
 struct TrainTcArgs {
   fabric_gbuffer g;
-  const float *latents;   // [n_lat][32]
+  const float *latents;   // [n_lat][32], 16-byte aligned
   int n_lat;
   const uint8_t *blob;
   const float *target;    // [n][4]
@@ -366,14 +372,31 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
       }
     }
   };
-  auto load_late = [&](int64_t t) {   // half 0: latent row, targets, <wi.n_s>
+  // half 0: latent row (16-byte loads: the rows of different queries are
+  // different lines, so wider loads mean fewer of them), targets, <wi.n_s>
+  const bool target_v4 = (reinterpret_cast<uintptr_t>(a.target) & 15u) == 0;
+  auto load_late = [&](int64_t t) {
     const int64_t q = t * kRows + r;
     const int m = nxt_mat;
     if (m >= 0) {
 #pragma unroll
-      for (int i = 0; i < kLatent; ++i) in_v[i] = ld_pinned(a.latents + (int64_t)m * kLatent + i);
+      for (int i = 0; i < kLatent / 4; ++i) {
+        const float4 z4 = ld_pinned4(a.latents + (int64_t)m * kLatent + 4 * i);
+        in_v[4 * i] = z4.x;
+        in_v[4 * i + 1] = z4.y;
+        in_v[4 * i + 2] = z4.z;
+        in_v[4 * i + 3] = z4.w;
+      }
+      if (target_v4) {
+        const float4 t4 = ld_pinned4(a.target + 4 * q);
+        in_tg[0] = t4.x;
+        in_tg[1] = t4.y;
+        in_tg[2] = t4.z;
+        in_tg[3] = t4.w;
+      } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) in_tg[k] = ld_pinned(a.target + 4 * q + k);
+        for (int k = 0; k < 4; ++k) in_tg[k] = ld_pinned(a.target + 4 * q + k);
+      }
       in_wz = ld_pinned(a.g.wi + 3 * q + 2);
     } else {
 #pragma unroll
@@ -740,6 +763,7 @@ int train_tc_grid(int64_t n, int sm_count) {
 cudaError_t launch_train_tc(const fabric_gbuffer &g, const float *latents, int n_lat, const float *dec,
                             const float *target, int loss_mode, void *blob, float *partial, double *loss_partial,
                             float *dlat_rows, int sm_count, int *status, cudaStream_t s) {
+  if (reinterpret_cast<uintptr_t>(latents) & 15u) return cudaErrorInvalidValue;   // rows read as float4
   {
     const cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void *>(train_tc_kernel), (int)kDynSmem);
     if (e != cudaSuccess) return e;
