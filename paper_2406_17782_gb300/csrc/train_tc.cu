@@ -297,10 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) train_tc_kernel(const TrainTcArgs
   // A tile's global inputs are loaded ahead, so that no wait for them falls
   // on the tile's critical path.  When a tile starts, every thread issues the
   // load of the next tile's material id, and half 1 those of its G-buffer
-  // record.  Half 1 encodes the record while the forward rounds' products
-  // run (the octaves of u, of v, then the rest), when it has nothing else to
-  // do; half 0 issues the latent row, target and <wi.n_s> loads after the
-  // loss, in flight during the backward pass.
+  // record.  Half 1 encodes the record in four pieces when it has nothing
+  // else to do: during the products of layers 2 and 3 and of the head, and
+  // while half 0 evaluates the loss; half 0 then issues the latent row,
+  // target and <wi.n_s> loads, in flight during the backward pass.
   int nxt_raw = -1;       // the next tile's raw material id
   int nxt_mat = -1;       // resolved: -1 for no query or a material out of range
   float in_v[kLatent];    // half 0: the latent row; half 1: the G-buffer record (9 used)
