@@ -972,8 +972,8 @@ __global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const float *_
 // square whose low part falls below the normal range loses at most 2^-149
 // absolutely, which is below 2^-49 of the thread's sum unless its largest
 // |w(a-b)| (or |w b|) is under sqrt(elements) 2^-50.  A thread in either
-// case (or with an exactly zero largest value, whose sums are then exact)
-// redoes its whole share in FP64 instead.
+// case redoes its whole share in FP64 instead; one whose largest value is
+// exactly zero does not, since its sums are then exact.
 constexpr int kErrRun2 = 16;    // pairs per run
 constexpr int kErrBatch2 = 4;   // pair loads in flight per thread (eight without weights)
 constexpr int kErrPerSm2 = 4;   // resident CTAs per SM
